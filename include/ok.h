@@ -1,0 +1,204 @@
+/*
+ * ok.h -- C ABI of the GB300 Ohta--Kawasaki Newton-step solver.
+ *
+ * What it computes (Farrell & Pearson, "A preconditioner for the
+ * Ohta--Kawasaki equation", arXiv:1603.04570):
+ *   - the P1 finite-element, theta-method discretisation of the Ohta--Kawasaki
+ *     equations in (u, w) form with homogeneous Neumann conditions
+ *     (Sec. 1, eqns oka, okb, okbcs; Sec. 2 first paragraph);
+ *   - at each Newton step the linear system J [du; dw] = f of eqn newton,
+ *         J = [ (1 + dt theta sigma) M    dt theta K ]
+ *             [ -eps^2 K - M_E            M          ],
+ *     solved by right-preconditioned restarted flexible GMRES;
+ *   - the preconditioner of eqn prec with A~^{-1} (Chebyshev semi-iteration on
+ *     the mass matrix, Sec. 3) and the matching-strategy Schur approximation
+ *     S~^{-1} = S_hat^{-1} M S_hat^{-1}, S_hat = M + eps sqrt(c) K,
+ *     c = dt theta / (1 + dt theta sigma) (eqns schur, outer_approx, schurinv);
+ *     S_hat^{-1} is approximated by geometric multigrid V-cycles (the paper
+ *     uses algebraic multigrid, Sec. 2 and Sec. 4).
+ *
+ * Grids: the unit square cut into n x n squares, each split along its
+ * (0,0)-(1,1) diagonal into two P1 triangles (dim = 2), or the unit cube cut
+ * into n^3 cubes of 6 Kuhn tetrahedra around the (0,0,0)-(1,1,1) diagonal
+ * (dim = 3).  N_v = (n+1)^dim vertices.
+ *
+ * Array conventions (every function):
+ *   - nodal arrays are double, compact lexicographic order, x fastest:
+ *     vertex (i,j[,k]) sits at i + (n+1) j [+ (n+1)^2 k];  a field has N_v
+ *     entries, a block vector [first field; second field] has 2 N_v;
+ *   - every array pointer may be HOST memory (pageable or pinned) or DEVICE
+ *     memory of the current CUDA device; the library asks the CUDA runtime
+ *     which it is.  Host arrays are staged through the grid's device
+ *     buffers, and the call returns only after results are back on the host.
+ *     Device arrays are used in place; work is enqueued on `stream`, and
+ *     functions that need a scalar on the host (norms, convergence tests)
+ *     synchronise that stream.
+ *   - the caller owns every array; the library owns the ok_grid handle and all
+ *     device workspace it allocated in ok_grid_create.
+ *   - `stream` is a cudaStream_t (0 = the legacy default stream).
+ *
+ * Errors: every function returns an OK_* status.  On failure
+ * ok_last_error() returns a message for the calling thread.  A non-finite
+ * input is reported as OK_ERR_NONFINITE before work that depends on it runs.
+ * No function traps or faults the GPU on purpose.
+ *
+ * One handle must not be used from two threads at once.
+ */
+#ifndef OK_GB300_H
+#define OK_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ok_stream;   /* a cudaStream_t */
+
+enum ok_status {
+  OK_SUCCESS = 0,
+  OK_ERR_INVALID_ARG = 1,     /* a size, option or pointer is invalid        */
+  OK_ERR_NOMEM = 2,           /* device or pinned host allocation failed     */
+  OK_ERR_CUDA = 3,            /* a CUDA runtime call failed                  */
+  OK_ERR_NOT_CONVERGED = 4,   /* Newton or GMRES hit its iteration cap       */
+  OK_ERR_NONFINITE = 5,       /* NaN/Inf in an input or during the solve     */
+  OK_ERR_TIMEOUT = 6          /* a bounded device-side wait gave up          */
+};
+
+enum ok_precision {
+  OK_FP64 = 0,    /* every step in float64                                      */
+  OK_MIXED = 1    /* preconditioner in float32 under float64 FGMRES, J, residual */
+};
+
+/* Physical and time-stepping parameters of eqns oka/okb and the theta-method. */
+typedef struct ok_params {
+  double eps;     /* interfacial thickness epsilon                        */
+  double sigma;   /* nonlocal energy coefficient sigma                    */
+  double m;       /* conserved mean of u                                  */
+  double theta;   /* implicitness of the theta-method, in (0, 1]          */
+  double dt;      /* timestep                                             */
+} ok_params;
+
+/* Solver options.  ok_default_opts() fills the defaults given in brackets. */
+typedef struct ok_opts {
+  int restart;        /* FGMRES restart length m [30]                           */
+  int max_gmres;      /* FGMRES iteration cap per linear solve [500]            */
+  int max_newton;     /* Newton steps per timestep [25]                         */
+  int newton_extra;   /* extra Newton steps after the stop test passes [0]      */
+  int q_A;            /* Chebyshev steps for A~^{-1} [10] (Sec. 4: ten)         */
+  int n_V;            /* V-cycles per S_hat^{-1} [5] (Sec. 4: five)             */
+  int k_R;            /* 1: S~^{-1}; 2: two Richardson steps on S [1]           */
+  int smooth_pre;     /* Chebyshev--Jacobi pre-smoothing steps per level [2]    */
+  int smooth_post;    /* post-smoothing steps per level [2]                     */
+  int precision;      /* OK_FP64 or OK_MIXED [OK_FP64]                          */
+  int coarse_max;     /* halve the grid while n is even and > coarse_max [4]    */
+  int use_graphs;     /* capture preconditioner applications in CUDA graphs [1] */
+  double gmres_rtol;  /* stop when ||f - J x|| <= gmres_rtol ||f|| [1e-10]      */
+  double newton_atol; /* Newton stops when ||F||_2 <= max(atol, rtol ||F_0||)   */
+  double newton_rtol; /*   [atol 1e-10, rtol 0]                                 */
+  double smooth_lo_frac; /* smoother interval [frac*lmax, lmax] [0.25]          */
+} ok_opts;
+
+/* Statistics of one Newton step / one timestep. */
+typedef struct ok_step_info {
+  int newton_its;       /* Newton steps taken                                   */
+  int gmres_its;        /* FGMRES iterations, summed over the Newton steps      */
+  int converged;        /* 1 when the stop test passed                          */
+  int last_gmres_its;   /* iterations of the last linear solve                  */
+  double rel_resid;     /* ||f - J x|| / ||f|| of the last linear solve         */
+  double newton_resid;  /* ||F||_2 at exit                                      */
+  double newton_resid0; /* ||F||_2 at entry                                     */
+  double solve_ms;      /* wall time of the linear solves (host clock)          */
+} ok_step_info;
+
+typedef struct ok_grid ok_grid;
+
+/* Fill `o` with the defaults listed in ok_opts. */
+void ok_default_opts(ok_opts* o);
+
+/* Create a solver for one grid and parameter set (dim 2 or 3, n cells per
+ * side, 2 <= n, (n+1)^dim < 2^31).  Builds the multigrid hierarchy of
+ * S_hat = M + eps sqrt(c) K, which depends only on the grid, eps and c and
+ * is therefore reused across Newton steps and timesteps (Sec. 2, after eqn
+ * schurapprox), and allocates the Krylov workspace on the current device.
+ * `o` may be NULL (defaults).  *out receives the handle. */
+int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid** out);
+
+/* Free a handle and its device memory.  NULL is accepted. */
+int ok_grid_destroy(ok_grid* g);
+
+/* Sizes of a handle: vertices, multigrid levels, device bytes held. */
+int ok_grid_query(const ok_grid* g, long long* n_vertices, int* n_levels, long long* device_bytes);
+
+/* w0 from eqn okb for a given u0 (Sec. 4, "computed from u0 via okb"):
+ * the L2 projection  M w0 = eps^2 K u0 + N(u0),  N(u)_i = int (u^3 - u) phi_i,
+ * solved with Chebyshev on M to round-off.  u0, w0: N_v each. */
+int ok_init_w(ok_grid* g, const double* u0, double* w0, ok_stream stream);
+
+/* f = -F(u_k, w_k) for the theta-scheme residual with previous state
+ * (u_n, w_n) (eqns oka/okb integrated against each P1 basis function):
+ *   F1 = M (u - u_n) + dt theta [K w + sigma M (u - m)]
+ *                    + dt (1 - theta) [K w_n + sigma M (u_n - m)],
+ *   F2 = M w - eps^2 K u - N(u).
+ * f has 2 N_v entries; *norm_out (host) receives ||F||_2.  Synchronises. */
+int ok_assemble_rhs(ok_grid* g, const double* u_n, const double* w_n,
+                    const double* u_k, const double* w_k, double* f,
+                    double* norm_out, ok_stream stream);
+
+/* y = J(u_k) z with J of eqn newton; z, y: 2 N_v.  M_E uses u_k. */
+int ok_apply_jacobian(ok_grid* g, const double* u_k, const double* z, double* y,
+                      ok_stream stream);
+
+/* z = P^{-1} v, the block lower-triangular preconditioner of eqn prec with
+ * A~^{-1} and S~^{-1} as configured (precision, q_A, n_V, k_R); v, z: 2 N_v. */
+int ok_apply_preconditioner(ok_grid* g, const double* u_k, const double* v, double* z,
+                            ok_stream stream);
+
+/* Solve J(u_k) x = f by right-preconditioned restarted FGMRES from x = 0 to
+ * the relative tolerance opts.gmres_rtol (eqn newton).  info may be NULL. */
+int ok_solve_linear(ok_grid* g, const double* u_k, const double* f, double* x,
+                    ok_step_info* info, ok_stream stream);
+
+/* One Newton step for the timestep from (u_n, w_n): f = -F(u_k, w_k),
+ * solve J(u_k) d = f, then (u_k, w_k) += d.  u_k, w_k are in-out. */
+int ok_newton_step(ok_grid* g, const double* u_n, const double* w_n,
+                   double* u_k, double* w_k, ok_step_info* info, ok_stream stream);
+
+/* One theta-method timestep: Newton from (u, w) at t_n to the stop test,
+ * then newton_extra more steps; (u, w) are overwritten with t_{n+1}.
+ * Returns OK_ERR_NOT_CONVERGED (state left at the last iterate) when the
+ * Newton cap is hit. */
+int ok_timestep(ok_grid* g, double* u, double* w, ok_step_info* info, ok_stream stream);
+
+/* A batch of independent simulations.  Each request names its grid handle,
+ * its state arrays and its number of timesteps; per-request status and
+ * statistics are written back into the request. */
+typedef struct ok_request {
+  ok_grid* grid;       /* in                                              */
+  double* u;           /* in-out, N_v of that grid                         */
+  double* w;           /* in-out                                           */
+  int steps;           /* in: timesteps to take                            */
+  int status;          /* out: OK_* of the first failing step, else 0      */
+  int newton_its;      /* out: summed over the steps                       */
+  int gmres_its;       /* out                                              */
+  double seconds;      /* out: wall time from batch start to completion    */
+} ok_request;
+
+typedef struct ok_batch_info {
+  int completed;       /* requests that finished with OK_SUCCESS          */
+  int failed;
+  double seconds;      /* wall time of the whole batch                     */
+} ok_batch_info;
+
+/* Run every request to completion.  Requests on distinct handles are
+ * independent; each gets its own stream, derived from `stream`'s device. */
+int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* ok_last_error(void);
+
+/* Library version string. */
+const char* ok_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OK_GB300_H */

@@ -1,0 +1,282 @@
+"""Python binding of libok_gb300.so (include/ok.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  Arrays may be torch tensors
+(CUDA or CPU) or numpy arrays; they must be float64 and contiguous.  The
+functions keep the C names (``ok_grid_create``, ``ok_timestep``, ...);
+``Grid`` wraps a handle for convenience.
+
+If the library cannot be built or loaded this module raises: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, byref, c_char_p, c_double, c_int, c_longlong, c_void_p
+
+from . import _build
+
+OK_SUCCESS, OK_ERR_INVALID_ARG, OK_ERR_NOMEM, OK_ERR_CUDA = 0, 1, 2, 3
+OK_ERR_NOT_CONVERGED, OK_ERR_NONFINITE, OK_ERR_TIMEOUT = 4, 5, 6
+OK_FP64, OK_MIXED = 0, 1
+STATUS_NAMES = {0: "OK_SUCCESS", 1: "OK_ERR_INVALID_ARG", 2: "OK_ERR_NOMEM", 3: "OK_ERR_CUDA",
+                4: "OK_ERR_NOT_CONVERGED", 5: "OK_ERR_NONFINITE", 6: "OK_ERR_TIMEOUT"}
+
+
+class Params(Structure):
+    _fields_ = [("eps", c_double), ("sigma", c_double), ("m", c_double), ("theta", c_double), ("dt", c_double)]
+
+
+class Opts(Structure):
+    _fields_ = [("restart", c_int), ("max_gmres", c_int), ("max_newton", c_int), ("newton_extra", c_int),
+                ("q_A", c_int), ("n_V", c_int), ("k_R", c_int), ("smooth_pre", c_int), ("smooth_post", c_int),
+                ("precision", c_int), ("coarse_max", c_int), ("use_graphs", c_int),
+                ("gmres_rtol", c_double), ("newton_atol", c_double), ("newton_rtol", c_double),
+                ("smooth_lo_frac", c_double)]
+
+
+class StepInfo(Structure):
+    _fields_ = [("newton_its", c_int), ("gmres_its", c_int), ("converged", c_int), ("last_gmres_its", c_int),
+                ("rel_resid", c_double), ("newton_resid", c_double), ("newton_resid0", c_double),
+                ("solve_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(Structure):
+    _fields_ = [("grid", c_void_p), ("u", c_void_p), ("w", c_void_p), ("steps", c_int), ("status", c_int),
+                ("newton_its", c_int), ("gmres_its", c_int), ("seconds", c_double)]
+
+
+class BatchInfo(Structure):
+    _fields_ = [("completed", c_int), ("failed", c_int), ("seconds", c_double)]
+
+
+class OkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load (building first if needed) the CUDA library; raises on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library {_build.LIB} is missing; build it with "
+                           f"paper_1603_04570_gb300._build.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    P = c_void_p
+    sig = {
+        "ok_default_opts": (None, [POINTER(Opts)]),
+        "ok_grid_create": (c_int, [c_int, c_int, POINTER(Params), POINTER(Opts), POINTER(c_void_p)]),
+        "ok_grid_destroy": (c_int, [P]),
+        "ok_grid_query": (c_int, [P, POINTER(c_longlong), POINTER(c_int), POINTER(c_longlong)]),
+        "ok_init_w": (c_int, [P, P, P, P]),
+        "ok_assemble_rhs": (c_int, [P, P, P, P, P, P, POINTER(c_double), P]),
+        "ok_apply_jacobian": (c_int, [P, P, P, P, P]),
+        "ok_apply_preconditioner": (c_int, [P, P, P, P, P]),
+        "ok_solve_linear": (c_int, [P, P, P, P, POINTER(StepInfo), P]),
+        "ok_newton_step": (c_int, [P, P, P, P, P, POINTER(StepInfo), P]),
+        "ok_timestep": (c_int, [P, P, P, POINTER(StepInfo), P]),
+        "ok_solve_batch": (c_int, [POINTER(Request), c_int, POINTER(BatchInfo), P]),
+        "ok_last_error": (c_char_p, []),
+        "ok_version": (c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _ptr(a, n=None, name="array"):
+    """Raw pointer of a float64 contiguous torch tensor or numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):                    # torch
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float64 tensor")
+        if n is not None and a.numel() != n:
+            raise ValueError(f"{name} has {a.numel()} entries, expected {n}")
+        return a.data_ptr()
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a contiguous float64 numpy array or torch tensor")
+    if n is not None and a.size != n:
+        raise ValueError(f"{name} has {a.size} entries, expected {n}")
+    return a.ctypes.data
+
+
+def _stream(stream, *arrays):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    for a in arrays:
+        if hasattr(a, "is_cuda") and a.is_cuda:
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+def _check(st):
+    if st != OK_SUCCESS:
+        raise OkError(st, load().ok_last_error().decode())
+
+
+def ok_default_opts(**overrides) -> Opts:
+    o = Opts()
+    load().ok_default_opts(byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def ok_grid_create(dim, n, params: Params, opts: Opts | None = None):
+    h = c_void_p()
+    _check(load().ok_grid_create(dim, n, byref(params), byref(opts) if opts is not None else None, byref(h)))
+    return h
+
+
+def ok_grid_destroy(h):
+    _check(load().ok_grid_destroy(h))
+
+
+def ok_grid_query(h):
+    nv, nl, nb = c_longlong(), c_int(), c_longlong()
+    _check(load().ok_grid_query(h, byref(nv), byref(nl), byref(nb)))
+    return nv.value, nl.value, nb.value
+
+
+def ok_init_w(h, nv, u0, w0, stream=None):
+    _check(load().ok_init_w(h, _ptr(u0, nv, "u0"), _ptr(w0, nv, "w0"), _stream(stream, u0, w0)))
+
+
+def ok_assemble_rhs(h, nv, u_n, w_n, u_k, w_k, f, stream=None):
+    nrm = c_double()
+    _check(load().ok_assemble_rhs(h, _ptr(u_n, nv, "u_n"), _ptr(w_n, nv, "w_n"), _ptr(u_k, nv, "u_k"),
+                                  _ptr(w_k, nv, "w_k"), _ptr(f, 2 * nv, "f"), byref(nrm),
+                                  _stream(stream, f, u_k)))
+    return nrm.value
+
+
+def ok_apply_jacobian(h, nv, u_k, z, y, stream=None):
+    _check(load().ok_apply_jacobian(h, _ptr(u_k, nv, "u_k"), _ptr(z, 2 * nv, "z"), _ptr(y, 2 * nv, "y"),
+                                    _stream(stream, y, z)))
+
+
+def ok_apply_preconditioner(h, nv, u_k, v, z, stream=None):
+    _check(load().ok_apply_preconditioner(h, _ptr(u_k, nv, "u_k"), _ptr(v, 2 * nv, "v"), _ptr(z, 2 * nv, "z"),
+                                          _stream(stream, z, v)))
+
+
+def _info_call(fn, *args):
+    info = StepInfo()
+    st = fn(*args[:-1], byref(info), args[-1])
+    return st, info
+
+
+def ok_solve_linear(h, nv, u_k, f, x, stream=None, check=True):
+    st, info = _info_call(load().ok_solve_linear, h, _ptr(u_k, nv, "u_k"), _ptr(f, 2 * nv, "f"),
+                          _ptr(x, 2 * nv, "x"), _stream(stream, x, f))
+    if check:
+        _check(st)
+    return info
+
+
+def ok_newton_step(h, nv, u_n, w_n, u_k, w_k, stream=None, check=True):
+    st, info = _info_call(load().ok_newton_step, h, _ptr(u_n, nv, "u_n"), _ptr(w_n, nv, "w_n"),
+                          _ptr(u_k, nv, "u_k"), _ptr(w_k, nv, "w_k"), _stream(stream, u_k, w_k))
+    if check:
+        _check(st)
+    return info
+
+
+def ok_timestep(h, nv, u, w, stream=None, check=True):
+    st, info = _info_call(load().ok_timestep, h, _ptr(u, nv, "u"), _ptr(w, nv, "w"), _stream(stream, u, w))
+    if check:
+        _check(st)
+    return info
+
+
+def ok_solve_batch(requests, stream=None):
+    """requests: list of (Grid, u, w, steps).  Returns (status list, BatchInfo)."""
+    arr = (Request * len(requests))()
+    for i, (g, u, w, steps) in enumerate(requests):
+        arr[i].grid = g.handle
+        arr[i].u = _ptr(u, g.nv, "u")
+        arr[i].w = _ptr(w, g.nv, "w")
+        arr[i].steps = steps
+    out = BatchInfo()
+    st = load().ok_solve_batch(arr, len(requests), byref(out), _stream(stream, *(r[1] for r in requests)))
+    return st, [arr[i] for i in range(len(requests))], out
+
+
+class Grid:
+    """One solver handle (grid + parameters + workspace on the current device)."""
+
+    def __init__(self, dim, n, eps, sigma, m, theta, dt, **opts):
+        self.dim, self.n = dim, n
+        self.params = Params(eps, sigma, m, theta, dt)
+        self.opts = ok_default_opts(**opts)
+        self.handle = ok_grid_create(dim, n, self.params, self.opts)
+        self.nv, self.levels, self.device_bytes = ok_grid_query(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ok_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init_w(self, u0, w0, stream=None):
+        ok_init_w(self.handle, self.nv, u0, w0, stream)
+
+    def assemble_rhs(self, u_n, w_n, u_k, w_k, f, stream=None):
+        return ok_assemble_rhs(self.handle, self.nv, u_n, w_n, u_k, w_k, f, stream)
+
+    def apply_jacobian(self, u_k, z, y, stream=None):
+        ok_apply_jacobian(self.handle, self.nv, u_k, z, y, stream)
+
+    def apply_preconditioner(self, u_k, v, z, stream=None):
+        ok_apply_preconditioner(self.handle, self.nv, u_k, v, z, stream)
+
+    def solve_linear(self, u_k, f, x, stream=None, check=True):
+        return ok_solve_linear(self.handle, self.nv, u_k, f, x, stream, check)
+
+    def newton_step(self, u_n, w_n, u_k, w_k, stream=None, check=True):
+        return ok_newton_step(self.handle, self.nv, u_n, w_n, u_k, w_k, stream, check)
+
+    def timestep(self, u, w, stream=None, check=True):
+        return ok_timestep(self.handle, self.nv, u, w, stream, check)
+
+
+def version() -> str:
+    return load().ok_version().decode()

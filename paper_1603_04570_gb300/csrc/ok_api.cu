@@ -1,0 +1,941 @@
+// ok_api.cu -- the C ABI (include/ok.h): grid handles, the preconditioner,
+// flexible GMRES, Newton and the theta-method timestep.
+//
+// Host code here only sequences kernels and moves scalars; every arithmetic
+// step of the solve runs in the kernels of ok_fem.cu, ok_mg.cu, ok_krylov.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ok.h"
+#include "ok_internal.cuh"
+#include "ok_kernels.h"
+
+using namespace okg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct OkError {
+  int status;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int status, const std::string& msg) { throw OkError{status, msg}; }
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      fail(OK_ERR_NOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    fail(OK_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+#define CK(call) ck((call), #call)
+#define CKL() ck(cudaGetLastError(), "kernel launch")
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    f();
+    g_last_error.clear();
+    return OK_SUCCESS;
+  } catch (const OkError& e) {
+    g_last_error = e.msg;
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return OK_ERR_NOMEM;
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void cheb_coefs(double lo, double hi, int steps, std::vector<double>& c1, std::vector<double>& c2, double& th) {
+  th = 0.5 * (hi + lo);
+  const double de = 0.5 * (hi - lo);
+  double rho = de / th;
+  c1.assign(steps > 1 ? steps - 1 : 1, 0.0);
+  c2.assign(steps > 1 ? steps - 1 : 1, 0.0);
+  for (int k = 0; k + 1 < steps; ++k) {
+    const double rn = 1.0 / (2.0 * th / de - rho);
+    c1[k] = rn * rho;
+    c2[k] = 2.0 * rn / de;
+    rho = rn;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// device memory owned by a handle
+// ---------------------------------------------------------------------------
+struct Arena {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  template <typename T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    size_t b = count * sizeof(T);
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(OK_ERR_NOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    ptrs.push_back(p);
+    bytes += b;
+    return (T*)p;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+// One multigrid level of S_hat in precision T.
+template <typename T> struct Level {
+  int n;
+  Geom g;
+  T *x, *b, *r, *d0, *d1;
+  T *WS, *dinvS;
+};
+
+// The block preconditioner in precision T (eqn prec with A~, S~).
+template <typename T> struct Prec {
+  int dim = 0;
+  std::vector<Level<T>> lv;
+  T *WM = nullptr, *WK = nullptr, *dinvM = nullptr;   // finest level M, K (scaled)
+  T* coarse_inv = nullptr;
+  long long nc = 0;
+  T *cx = nullptr, *cr = nullptr, *cd0 = nullptr, *cd1 = nullptr;   // Chebyshev on M
+  T *tt = nullptr, *yy = nullptr;                                    // k_R = 2
+  const T* coef = nullptr;                                           // C coefficients (T)
+  std::vector<double> cM1, cM2, cS1, cS2;
+  double thM = 1, thS = 1;
+  double inv_a11 = 1, dth = 0;
+  int q_A = 10, n_V = 5, k_R = 1, nu_pre = 2, nu_post = 2;
+
+  template <typename TB, typename TO>
+  void cheb(const Geom& g, const T* W, const T* dinv, const TB* b, bool x_zero, T* x, T* r, T* d0, T* d1,
+            int steps, double th, const std::vector<double>& c1, const std::vector<double>& c2, TO* out,
+            T oscale, bool want_r, cudaStream_t s) {
+    if (x_zero) launch_cheb_init<T, TB>(dim, g, dinv, b, (T)1, r, d0, (T)(1.0 / th), s);
+    else launch_resid_init<T>(dim, g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s);
+    T* d[2] = {d0, d1};
+    int cur = 0;
+    for (int k = 0; k + 1 < steps; ++k) {
+      launch_cheb_step<T>(dim, g, W, dinv, x, r, d[cur], d[1 - cur], (T)c1[k], (T)c2[k], x_zero && k == 0, s);
+      cur ^= 1;
+    }
+    launch_cheb_last<T, TO>(dim, g, W, x, want_r ? r : nullptr, d[cur], x_zero && steps == 1, out, oscale, s);
+  }
+
+  template <typename TO>
+  void vcycle(int l, bool x_zero, TO* out, cudaStream_t s) {
+    Level<T>& L = lv[l];
+    const bool coarsest = (l + 1 == (int)lv.size());
+    if (coarsest) {
+      launch_coarse_solve<T>(nc, coarse_inv, L.b, L.x, s);
+      if (out) launch_axpby<T, TO>(L.g.nv, 1.0, L.x, 0.0, out, s);
+      return;
+    }
+    cheb<T, T>(L.g, L.WS, L.dinvS, L.b, x_zero, L.x, L.r, L.d0, L.d1, nu_pre, thS, cS1, cS2, (T*)nullptr,
+               (T)1, true, s);
+    Level<T>& C = lv[l + 1];
+    launch_restrict<T>(dim, L.g, C.g, L.r, C.b, s);
+    vcycle<T>(l + 1, true, (T*)nullptr, s);
+    launch_prolong_add<T>(dim, L.g, C.g, L.x, C.x, s);
+    cheb<T, TO>(L.g, L.WS, L.dinvS, L.b, false, L.x, L.r, L.d0, L.d1, nu_post, thS, cS1, cS2, out, (T)1, false, s);
+  }
+
+  // x_0 = S_hat^{-1} b_0 by n_V V-cycles from zero; optional cast to out
+  template <typename TO>
+  void mg_solve(TO* out, cudaStream_t s) {
+    for (int c = 0; c < n_V; ++c) vcycle<TO>(0, c == 0, c + 1 == n_V ? out : (TO*)nullptr, s);
+  }
+
+  // A~^{-1} b into cx (unscaled Chebyshev on M; A~^{-1} b = cx / a11)
+  template <typename TB, typename TO>
+  void a_inv(const TB* b, TO* out, cudaStream_t s) {
+    cheb<TB, TO>(lv[0].g, WM, dinvM, b, true, cx, cr, cd0, cd1, q_A, thM, cM1, cM2, out, (T)inv_a11, false, s);
+  }
+
+  // z = P^{-1} v  (v: 2 nv doubles; z: 2 nv of TZ)
+  template <typename TZ>
+  void apply(const double* v, TZ* z, cudaStream_t s) {
+    const Geom& g = lv[0].g;
+    const long long nv = g.nv;
+    Level<T>& L0 = lv[0];
+    a_inv<double, TZ>(v, z, s);                                           // z1 = A~^{-1} r1
+    launch_cstep<T, double>(dim, g, coef, v + nv, (T)1, cx, (T)inv_a11, L0.b, s);   // t = r2 - C z1
+    if (k_R == 1) {
+      mg_solve<T>((T*)nullptr, s);                                         // S_hat^{-1} t
+      launch_op_apply<T, T, T>(dim, g, WM, false, L0.x, L0.b, (T)1, (const T*)nullptr, (T)0, s);   // M .
+      mg_solve<TZ>(z + nv, s);                                             // S_hat^{-1} .
+      return;
+    }
+    // k_R = 2: y = S~^{-1} t;  z2 = y + S~^{-1} (t - S y),  S y = M y - C A~^{-1} (dt theta K y)
+    launch_axpby<T, T>(nv, 1.0, L0.b, 0.0, tt, s);
+    mg_solve<T>((T*)nullptr, s);
+    launch_op_apply<T, T, T>(dim, g, WM, false, L0.x, L0.b, (T)1, (const T*)nullptr, (T)0, s);
+    mg_solve<T>(yy, s);
+    launch_op_apply<T, T, T>(dim, g, WK, true, yy, cr, (T)dth, (const T*)nullptr, (T)0, s);   // q = dt th K y
+    launch_axpby<T, T>(nv, 1.0, cr, 0.0, L0.r, s);                                          // keep q
+    a_inv<T, T>(L0.r, (T*)nullptr, s);                                                     // cx = Cheb(q)
+    launch_schur_resid<T>(dim, g, WM, (T)1, coef, tt, yy, cx, (T)inv_a11, L0.b, s);         // t - S y
+    mg_solve<T>((T*)nullptr, s);
+    launch_op_apply<T, T, T>(dim, g, WM, false, L0.x, L0.b, (T)1, (const T*)nullptr, (T)0, s);
+    mg_solve<T>((T*)nullptr, s);
+    launch_axpby<T, T>(nv, 1.0, yy, 1.0, L0.x, s);
+    launch_axpby<T, TZ>(nv, 1.0, L0.x, 0.0, z + nv, s);
+  }
+};
+
+struct ok_grid {
+  int dim = 0, n = 0;
+  int device = 0;
+  Geom g0;
+  ok_params p;
+  ok_opts o;
+  Arena arena;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  ResidualCoefs rc;
+  JCoefs jc;
+  int n_levels = 0;
+  // reference tables (h = 1), double
+  double *refWM = nullptr, *refWK = nullptr;
+  double *WM0d = nullptr, *dinvM0d = nullptr;   // finest M (scaled), double: w0 projection
+  // state and work vectors (double)
+  double *un = nullptr, *wn = nullptr, *uk = nullptr, *wk = nullptr;   // N_v each
+  double *f = nullptr, *xs = nullptr, *rv = nullptr, *tmp = nullptr;  // 2 N_v each
+  double* coef = nullptr;
+  float* coef32 = nullptr;
+  // Krylov
+  double* V = nullptr;
+  double* Zd = nullptr;
+  float* Zf = nullptr;
+  KrylovState* ks = nullptr;
+  RedScratch rs;
+  double* dsc = nullptr;      // device scalars
+  int* dflag = nullptr;
+  double* hpin = nullptr;     // pinned host scalars
+  Prec<double> pd;
+  Prec<float> pf;
+  std::vector<cudaGraphExec_t> graphs;   // one Arnoldi step per j
+  double cheb_init_th = 1;
+  std::vector<double> cI1, cI2;          // 60-step mass Chebyshev for w0
+};
+
+namespace {
+
+template <typename T>
+void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std::vector<double>& refM,
+                const std::vector<double>& refK) {
+  const int dim = G->dim;
+  const int NOFF = dim == 2 ? Topo<2>::NOFF : Topo<3>::NOFF;
+  const int NCLASS = dim == 2 ? Topo<2>::NCLASS : Topo<3>::NCLASS;
+  const double gamma = G->p.eps * std::sqrt(G->p.dt * G->p.theta / (1.0 + G->p.dt * G->p.theta * G->p.sigma));
+  Arena& A = G->arena;
+  P.dim = dim;
+  P.q_A = G->o.q_A;
+  P.n_V = G->o.n_V;
+  P.k_R = G->o.k_R;
+  P.nu_pre = G->o.smooth_pre;
+  P.nu_post = G->o.smooth_post;
+  P.inv_a11 = 1.0 / (1.0 + G->p.dt * G->p.theta * G->p.sigma);
+  P.dth = G->p.dt * G->p.theta;
+  const double hiS = 0.5 * (dim + 2);
+  cheb_coefs(G->o.smooth_lo_frac * hiS, hiS, std::max(P.nu_pre, P.nu_post), P.cS1, P.cS2, P.thS);
+  cheb_coefs(0.5, 0.5 * (dim + 2), P.q_A, P.cM1, P.cM2, P.thM);
+  std::vector<T> tab(NCLASS * NOFF), dv(NCLASS);
+  auto upload = [&](const std::vector<T>& h) {
+    T* d = A.alloc<T>(h.size());
+    CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return d;
+  };
+  for (size_t l = 0; l < sizes.size(); ++l) {
+    Level<T> L;
+    L.n = sizes[l];
+    L.g = make_geom(dim, L.n);
+    const double h = 1.0 / L.n;
+    const double hd = std::pow(h, dim), hk = std::pow(h, dim - 2);
+    for (int i = 0; i < NCLASS * NOFF; ++i) tab[i] = (T)(hd * refM[i] + gamma * hk * refK[i]);
+    for (int c = 0; c < NCLASS; ++c) dv[c] = (T)(1.0 / (hd * refM[c * NOFF] + gamma * hk * refK[c * NOFF]));
+    L.WS = upload(tab);
+    L.dinvS = upload(dv);
+    const long long nv = L.g.nv;
+    L.x = A.alloc<T>(nv);
+    L.b = A.alloc<T>(nv);
+    L.r = A.alloc<T>(nv);
+    L.d0 = A.alloc<T>(nv);
+    L.d1 = A.alloc<T>(nv);
+    if (l == 0) {
+      for (int i = 0; i < NCLASS * NOFF; ++i) tab[i] = (T)(hd * refM[i]);
+      for (int c = 0; c < NCLASS; ++c) dv[c] = (T)(1.0 / (hd * refM[c * NOFF]));
+      P.WM = upload(tab);
+      P.dinvM = upload(dv);
+      for (int i = 0; i < NCLASS * NOFF; ++i) tab[i] = (T)(hk * refK[i]);
+      P.WK = upload(tab);
+    }
+    P.lv.push_back(L);
+  }
+  const long long nv0 = P.lv[0].g.nv;
+  P.cx = A.alloc<T>(nv0);
+  P.cr = A.alloc<T>(nv0);
+  P.cd0 = A.alloc<T>(nv0);
+  P.cd1 = A.alloc<T>(nv0);
+  if (P.k_R == 2) {
+    P.tt = A.alloc<T>(nv0);
+    P.yy = A.alloc<T>(nv0);
+  }
+  // coarsest level: dense S_hat and its inverse (float64 Gauss--Jordan on the GPU)
+  Level<T>& C = P.lv.back();
+  const long long nc = C.g.nv;
+  P.nc = nc;
+  {
+    const double h = 1.0 / C.n, hd = std::pow(h, dim), hk = std::pow(h, dim - 2);
+    std::vector<double> td(NCLASS * NOFF);
+    for (int i = 0; i < NCLASS * NOFF; ++i) td[i] = hd * refM[i] + gamma * hk * refK[i];
+    double* Wd = A.alloc<double>(td.size());
+    CK(cudaMemcpy(Wd, td.data(), td.size() * sizeof(double), cudaMemcpyHostToDevice));
+    double* dense = A.alloc<double>(nc * nc);
+    double* work = A.alloc<double>(2 * nc * nc);
+    double* inv = A.alloc<double>(nc * nc);
+    CK(cudaMemset(dense, 0, nc * nc * sizeof(double)));
+    launch_dense_from_table(dim, C.g, Wd, dense, 0);
+    CKL();
+    launch_gauss_jordan(nc, dense, work, inv, 0);
+    CKL();
+    if (std::is_same<T, double>::value) {
+      P.coarse_inv = (T*)inv;
+    } else {
+      P.coarse_inv = A.alloc<T>(nc * nc);
+      launch_axpby<double, T>(nc * nc, 1.0, inv, 0.0, P.coarse_inv, 0);
+      CKL();
+    }
+    CK(cudaDeviceSynchronize());
+  }
+}
+
+void validate(int dim, int n, const ok_params* p, const ok_opts* o) {
+  if (dim != 2 && dim != 3) fail(OK_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (n < 2) fail(OK_ERR_INVALID_ARG, "n must be >= 2");
+  double nv = std::pow((double)(n + 1), dim);
+  if (nv >= 2147483647.0) fail(OK_ERR_INVALID_ARG, "(n+1)^dim must be < 2^31");
+  if (!p) fail(OK_ERR_INVALID_ARG, "params is NULL");
+  if (!(p->eps > 0) || !(p->dt > 0) || !(p->theta > 0 && p->theta <= 1) || !(p->sigma >= 0) ||
+      !std::isfinite(p->m) || !std::isfinite(p->eps) || !std::isfinite(p->dt) || !std::isfinite(p->sigma))
+    fail(OK_ERR_INVALID_ARG, "params out of range (need eps > 0, dt > 0, 0 < theta <= 1, sigma >= 0)");
+  if (o->restart < 1 || o->restart >= KRYLOV_MAX) fail(OK_ERR_INVALID_ARG, "restart must be in [1, 63]");
+  if (o->q_A < 1 || o->n_V < 1 || o->smooth_pre < 1 || o->smooth_post < 1 || o->q_A > 64 || o->smooth_pre > 16 ||
+      o->smooth_post > 16 || o->n_V > 32)
+    fail(OK_ERR_INVALID_ARG, "q_A, n_V, smooth_pre, smooth_post must be >= 1 (and q_A <= 64, n_V <= 32, smoothing <= 16)");
+  if (o->k_R != 1 && o->k_R != 2) fail(OK_ERR_INVALID_ARG, "k_R must be 1 or 2");
+  if (o->precision != OK_FP64 && o->precision != OK_MIXED) fail(OK_ERR_INVALID_ARG, "precision must be OK_FP64 or OK_MIXED");
+  if (o->max_gmres < 1 || o->max_newton < 0 || o->newton_extra < 0) fail(OK_ERR_INVALID_ARG, "iteration caps");
+  if (!(o->gmres_rtol > 0) || !(o->newton_atol >= 0) || !(o->newton_rtol >= 0))
+    fail(OK_ERR_INVALID_ARG, "tolerances must be positive");
+  if (!(o->smooth_lo_frac > 0 && o->smooth_lo_frac < 1)) fail(OK_ERR_INVALID_ARG, "smooth_lo_frac in (0,1)");
+  if (o->coarse_max < 1) fail(OK_ERR_INVALID_ARG, "coarse_max must be >= 1");
+}
+
+std::vector<int> level_sizes(int n, int coarse_max) {
+  std::vector<int> s{n};
+  while (s.back() % 2 == 0 && s.back() > coarse_max) s.push_back(s.back() / 2);
+  return s;
+}
+
+struct StreamScope {
+  ok_grid* G;
+  cudaStream_t user;
+  StreamScope(ok_grid* g, cudaStream_t u) : G(g), user(u) {
+    CK(cudaEventRecord(G->ev_in, user));
+    CK(cudaStreamWaitEvent(G->s, G->ev_in, 0));
+  }
+  ~StreamScope() {
+    if (cudaEventRecord(G->ev_out, G->s) == cudaSuccess) cudaStreamWaitEvent(user, G->ev_out, 0);
+  }
+};
+
+// bring a caller array into device memory (copy if it is on the host)
+const double* stage_in(ok_grid* G, const double* p, double* buf, long long count) {
+  if (!p) fail(OK_ERR_INVALID_ARG, "NULL array");
+  if (is_device_ptr(p)) return p;
+  CK(cudaMemcpyAsync(buf, p, count * sizeof(double), cudaMemcpyHostToDevice, G->s));
+  return buf;
+}
+
+void check_finite(ok_grid* G, const double* d, long long count, const char* what) {
+  CK(cudaMemsetAsync(G->dflag, 0, sizeof(int), G->s));
+  launch_check_finite(d, count, G->dflag, G->s);
+  CKL();
+  int h = 0;
+  CK(cudaMemcpyAsync(G->hpin, G->dflag, sizeof(int), cudaMemcpyDeviceToHost, G->s));
+  CK(cudaStreamSynchronize(G->s));
+  std::memcpy(&h, G->hpin, sizeof(int));
+  if (h) fail(OK_ERR_NONFINITE, std::string("non-finite value in ") + what);
+}
+
+double read_scalar(ok_grid* G, const double* d) {
+  CK(cudaMemcpyAsync(G->hpin, d, sizeof(double), cudaMemcpyDeviceToHost, G->s));
+  CK(cudaStreamSynchronize(G->s));
+  return G->hpin[0];
+}
+
+void assemble_c(ok_grid* G, const double* uk) {
+  launch_assemble_c(G->dim, G->g0, G->rc, uk, G->coef, G->coef32, G->s);
+  CKL();
+}
+
+// z = P^{-1} v with the configured precision (z: 2 nv, Z-slot type)
+template <typename TZ>
+void precond(ok_grid* G, const double* v, TZ* z, cudaStream_t s) {
+  if (G->o.precision == OK_MIXED) G->pf.apply<TZ>(v, z, s);
+  else G->pd.apply<TZ>(v, z, s);
+}
+
+template <typename TZ>
+void arnoldi(ok_grid* G, TZ* Z, int j, cudaStream_t s) {
+  const long long N = 2 * G->g0.nv;
+  const double* vj = G->V + (long long)j * N;
+  double* w = G->V + (long long)(j + 1) * N;
+  TZ* zj = Z + (long long)j * N;
+  precond<TZ>(G, vj, zj, s);
+  launch_apply_j<TZ>(G->dim, G->g0, G->refWM, G->refWK, G->jc, G->coef, zj, w, nullptr, s);
+  launch_multidot(G->V, N, j + 1, w, N, G->rs, ks_h1_ptr(G->ks), s);
+  launch_update_multidot(G->V, N, j + 1, ks_h1_ptr(G->ks), w, N, G->rs, ks_h2_ptr(G->ks), s);
+  launch_update_norm_givens(G->V, N, j + 1, w, N, G->rs, G->ks, j, s);
+  launch_scale_by(w, N, ks_eta_ptr(G->ks) + 1, s);   // inv_eta follows eta
+}
+
+// Right-preconditioned restarted FGMRES for J x = f (all device pointers).
+template <typename TZ>
+void fgmres(ok_grid* G, TZ* Z, const double* f, double* x, int& its, double& rel) {
+  cudaStream_t s = G->s;
+  const long long N = 2 * G->g0.nv;
+  const int m = G->o.restart;
+  const double rtol = G->o.gmres_rtol;
+  its = 0;
+  launch_norm(f, N, G->rs, G->dsc, s);
+  CKL();
+  const double fnorm = read_scalar(G, G->dsc);
+  CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+  if (!std::isfinite(fnorm)) fail(OK_ERR_NONFINITE, "non-finite right-hand side");
+  if (fnorm == 0.0) {
+    rel = 0.0;
+    return;
+  }
+  CK(cudaMemcpyAsync(G->rv, f, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double beta = fnorm;
+  CK(cudaMemcpyAsync(G->dsc + 1, G->dsc, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  const bool graphs = G->o.use_graphs != 0;
+  while (beta > rtol * fnorm && its < G->o.max_gmres) {
+    launch_cycle_start(G->ks, G->dsc + 1, s);
+    launch_axpby<double, double>(N, 1.0, G->rv, 0.0, G->V, s);
+    launch_scale_by(G->V, N, ks_beta_ptr(G->ks) + 1, s);    // inv_beta follows beta
+    CKL();
+    int jused = 0;
+    for (int j = 0; j < m; ++j) {
+      if (graphs) {
+        if (!G->graphs[j]) {
+          cudaGraph_t gr;
+          CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+          arnoldi<TZ>(G, Z, j, s);
+          cudaError_t e = cudaStreamEndCapture(s, &gr);
+          ck(e, "graph capture of an Arnoldi step");
+          CK(cudaGraphInstantiate(&G->graphs[j], gr, 0));
+          cudaGraphDestroy(gr);
+        }
+        CK(cudaGraphLaunch(G->graphs[j], s));
+      } else {
+        arnoldi<TZ>(G, Z, j, s);
+        CKL();
+      }
+      ++its;
+      jused = j + 1;
+      CK(cudaMemcpyAsync(G->hpin, ks_eta_ptr(G->ks), 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      const double eta = G->hpin[0], est = G->hpin[2];
+      if (!std::isfinite(est)) fail(OK_ERR_NONFINITE, "non-finite value in FGMRES");
+      if (est <= rtol * fnorm || its >= G->o.max_gmres || eta == 0.0) break;
+    }
+    launch_lsq(G->ks, jused, s);
+    launch_multi_axpy<TZ>(Z, N, jused, G->ks, x, N, s);
+    JCoefs jc = G->jc;
+    jc.alpha = -1.0;
+    jc.beta = 1.0;
+    launch_apply_j<double>(G->dim, G->g0, G->refWM, G->refWK, jc, G->coef, x, G->rv, f, s);   // r = f - J x
+    launch_norm(G->rv, N, G->rs, G->dsc + 1, s);
+    CKL();
+    beta = read_scalar(G, G->dsc + 1);
+    if (!std::isfinite(beta)) fail(OK_ERR_NONFINITE, "non-finite residual in FGMRES");
+  }
+  rel = beta / fnorm;
+}
+
+void linear_solve(ok_grid* G, const double* f, double* x, int& its, double& rel) {
+  if (G->o.precision == OK_MIXED) fgmres<float>(G, G->Zf, f, x, its, rel);
+  else fgmres<double>(G, G->Zd, f, x, its, rel);
+}
+
+// f = -F(u_k, w_k), returns ||F||_2
+double residual(ok_grid* G, const double* un, const double* wn, const double* uk, const double* wk, double* f) {
+  launch_residual(G->dim, G->g0, G->refWM, G->refWK, G->rc, un, wn, uk, wk, f, G->s);
+  CKL();
+  launch_norm(f, 2 * G->g0.nv, G->rs, G->dsc, G->s);
+  CKL();
+  return read_scalar(G, G->dsc);
+}
+
+// one Newton step on the handle's device buffers un, wn, uk, wk
+void newton_update(ok_grid* G, ok_step_info& info, double& ms) {
+  auto t0 = std::chrono::steady_clock::now();
+  assemble_c(G, G->uk);
+  int its = 0;
+  double rel = 0;
+  linear_solve(G, G->f, G->xs, its, rel);
+  const long long nv = G->g0.nv;
+  launch_axpby<double, double>(nv, 1.0, G->xs, 1.0, G->uk, G->s);
+  launch_axpby<double, double>(nv, 1.0, G->xs + nv, 1.0, G->wk, G->s);
+  CKL();
+  CK(cudaStreamSynchronize(G->s));
+  ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  info.gmres_its += its;
+  info.last_gmres_its = its;
+  info.rel_resid = rel;
+  info.newton_its += 1;
+  if (rel > G->o.gmres_rtol) fail(OK_ERR_NOT_CONVERGED, "FGMRES did not reach gmres_rtol within max_gmres");
+}
+
+void copy_out(ok_grid* G, double* dst, const double* src, long long count) {
+  CK(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, G->s));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void ok_default_opts(ok_opts* o) {
+  if (!o) return;
+  o->restart = 30;
+  o->max_gmres = 500;
+  o->max_newton = 25;
+  o->newton_extra = 0;
+  o->q_A = 10;
+  o->n_V = 5;
+  o->k_R = 1;
+  o->smooth_pre = 2;
+  o->smooth_post = 2;
+  o->precision = OK_FP64;
+  o->coarse_max = 4;
+  o->use_graphs = 1;
+  o->gmres_rtol = 1e-10;
+  o->newton_atol = 1e-10;
+  o->newton_rtol = 0.0;
+  o->smooth_lo_frac = 0.25;
+}
+
+const char* ok_last_error(void) { return g_last_error.c_str(); }
+const char* ok_version(void) { return "ok-gb300 0.1 (sm_103a)"; }
+
+int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid** out) {
+  if (!out) {
+    g_last_error = "out is NULL";
+    return OK_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  ok_opts od;
+  ok_default_opts(&od);
+  if (o) od = *o;
+  ok_grid* G = nullptr;
+  int st = guarded([&] {
+    validate(dim, n, p, &od);
+    std::vector<int> sizes = level_sizes(n, od.coarse_max);
+    const long long ncoarse = (long long)std::pow((double)(sizes.back() + 1), dim);
+    if (ncoarse > 1000)
+      fail(OK_ERR_INVALID_ARG, "the coarsest multigrid level has " + std::to_string(ncoarse) +
+                                   " unknowns (> 1000); use n = c 2^k with (c+1)^dim <= 1000");
+    G = new ok_grid();
+    G->dim = dim;
+    G->n = n;
+    G->p = *p;
+    G->o = od;
+    CK(cudaGetDevice(&G->device));
+    G->g0 = make_geom(dim, n);
+    G->n_levels = (int)sizes.size();
+    const double h = 1.0 / n;
+    const int fact = dim == 2 ? 2 : 6;
+    ResidualCoefs& rc = G->rc;
+    rc.a11 = 1.0 + p->dt * p->theta * p->sigma;
+    rc.bn = 1.0 - p->dt * (1.0 - p->theta) * p->sigma;
+    rc.dsm = p->dt * p->sigma * p->m;
+    rc.dth = p->dt * p->theta;
+    rc.dth1 = p->dt * (1.0 - p->theta);
+    rc.hd = std::pow(h, dim);
+    rc.hk = std::pow(h, dim - 2);
+    rc.eps2 = p->eps * p->eps;
+    rc.vol = rc.hd / fact;
+    rc.a4 = dim == 2 ? 2.0 / 720.0 : 6.0 / 5040.0;     // d!/(d+4)!
+    rc.a2 = dim == 2 ? 2.0 / 24.0 : 6.0 / 120.0;       // d!/(d+2)!
+    JCoefs& jc = G->jc;
+    jc.a11hd = rc.a11 * rc.hd;
+    jc.dthhk = rc.dth * rc.hk;
+    jc.hd = rc.hd;
+    jc.alpha = 1.0;
+    jc.beta = 0.0;
+    CK(cudaStreamCreateWithFlags(&G->s, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&G->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&G->ev_out, cudaEventDisableTiming));
+    const int NOFF = dim == 2 ? Topo<2>::NOFF : Topo<3>::NOFF;
+    const int NCLASS = dim == 2 ? Topo<2>::NCLASS : Topo<3>::NCLASS;
+    const int NSLOT = dim == 2 ? Topo<2>::NSLOT : Topo<3>::NSLOT;
+    std::vector<double> refM(NCLASS * NOFF), refK(NCLASS * NOFF);
+    reference_tables(dim, refM.data(), refK.data());
+    Arena& A = G->arena;
+    G->refWM = A.alloc<double>(refM.size());
+    G->refWK = A.alloc<double>(refK.size());
+    CK(cudaMemcpy(G->refWM, refM.data(), refM.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->refWK, refK.data(), refK.size() * sizeof(double), cudaMemcpyHostToDevice));
+    {
+      std::vector<double> t(NCLASS * NOFF), dv(NCLASS);
+      for (int i = 0; i < NCLASS * NOFF; ++i) t[i] = rc.hd * refM[i];
+      for (int c = 0; c < NCLASS; ++c) dv[c] = 1.0 / t[c * NOFF];
+      G->WM0d = A.alloc<double>(t.size());
+      G->dinvM0d = A.alloc<double>(dv.size());
+      CK(cudaMemcpy(G->WM0d, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(G->dinvM0d, dv.data(), dv.size() * sizeof(double), cudaMemcpyHostToDevice));
+      cheb_coefs(0.5, 0.5 * (dim + 2), 60, G->cI1, G->cI2, G->cheb_init_th);
+    }
+    const long long nv = G->g0.nv, N = 2 * nv;
+    G->un = A.alloc<double>(nv);
+    G->wn = A.alloc<double>(nv);
+    G->uk = A.alloc<double>(nv);
+    G->wk = A.alloc<double>(nv);
+    G->f = A.alloc<double>(N);
+    G->xs = A.alloc<double>(N);
+    G->rv = A.alloc<double>(N);
+    G->tmp = A.alloc<double>(N);
+    G->coef = A.alloc<double>(NSLOT * nv);
+    G->coef32 = A.alloc<float>(NSLOT * nv);
+    G->V = A.alloc<double>((size_t)(od.restart + 1) * N);
+    if (od.precision == OK_MIXED) G->Zf = A.alloc<float>((size_t)od.restart * N);
+    else G->Zd = A.alloc<double>((size_t)od.restart * N);
+    G->ks = (KrylovState*)A.alloc<char>(krylov_state_bytes());
+    CK(cudaMemset(G->ks, 0, krylov_state_bytes()));
+    G->rs.partials = A.alloc<double>((size_t)RED_MAX_BLOCKS * KRYLOV_MAX);
+    G->rs.counter = A.alloc<unsigned int>(1);
+    CK(cudaMemset(G->rs.counter, 0, sizeof(unsigned int)));
+    G->dsc = A.alloc<double>(8);
+    G->dflag = A.alloc<int>(1);
+    void* hp = nullptr;
+    CK(cudaMallocHost(&hp, 64));
+    G->hpin = (double*)hp;
+    if (od.precision == OK_MIXED) {
+      build_prec<float>(G, G->pf, sizes, refM, refK);
+      G->pf.coef = G->coef32;
+    } else {
+      build_prec<double>(G, G->pd, sizes, refM, refK);
+      G->pd.coef = G->coef;
+    }
+    G->graphs.assign(od.restart, nullptr);
+    krylov_blocks();
+    CK(cudaDeviceSynchronize());
+  });
+  if (st != OK_SUCCESS) {
+    if (G) ok_grid_destroy(G);
+    return st;
+  }
+  *out = G;
+  return OK_SUCCESS;
+}
+
+int ok_grid_destroy(ok_grid* G) {
+  if (!G) return OK_SUCCESS;
+  if (G->s) cudaStreamSynchronize(G->s);
+  for (auto& ge : G->graphs)
+    if (ge) cudaGraphExecDestroy(ge);
+  G->arena.release();
+  if (G->hpin) cudaFreeHost(G->hpin);
+  if (G->ev_in) cudaEventDestroy(G->ev_in);
+  if (G->ev_out) cudaEventDestroy(G->ev_out);
+  if (G->s) cudaStreamDestroy(G->s);
+  delete G;
+  return OK_SUCCESS;
+}
+
+int ok_grid_query(const ok_grid* G, long long* n_vertices, int* n_levels, long long* device_bytes) {
+  if (!G) {
+    g_last_error = "NULL handle";
+    return OK_ERR_INVALID_ARG;
+  }
+  if (n_vertices) *n_vertices = G->g0.nv;
+  if (n_levels) *n_levels = G->n_levels;
+  if (device_bytes) *device_bytes = (long long)G->arena.bytes;
+  return OK_SUCCESS;
+}
+
+int ok_init_w(ok_grid* G, const double* u0, double* w0, ok_stream stream) {
+  if (!G || !u0 || !w0) {
+    g_last_error = "NULL argument";
+    return OK_ERR_INVALID_ARG;
+  }
+  return guarded([&] {
+    StreamScope sc(G, (cudaStream_t)stream);
+    const long long nv = G->g0.nv;
+    const double* u = stage_in(G, u0, G->uk, nv);
+    check_finite(G, u, nv, "u0");
+    double* rhs = G->f;
+    launch_initw_rhs(G->dim, G->g0, G->refWK, G->rc, u, rhs, G->s);
+    CKL();
+    // M w0 = rhs by 60 Chebyshev--Jacobi steps on M (contraction <= 0.39 per step)
+    Prec<double> tmp;
+    tmp.dim = G->dim;
+    tmp.cheb<double, double>(G->g0, G->WM0d, G->dinvM0d, rhs, true, G->wk, G->f + nv, G->xs, G->xs + nv, 60,
+                             G->cheb_init_th, G->cI1, G->cI2, (double*)nullptr, 1.0, false, G->s);
+    CKL();
+    copy_out(G, w0, G->wk, nv);
+    CK(cudaStreamSynchronize(G->s));
+  });
+}
+
+int ok_assemble_rhs(ok_grid* G, const double* u_n, const double* w_n, const double* u_k, const double* w_k,
+                    double* f, double* norm_out, ok_stream stream) {
+  if (!G || !f) {
+    g_last_error = "NULL argument";
+    return OK_ERR_INVALID_ARG;
+  }
+  return guarded([&] {
+    StreamScope sc(G, (cudaStream_t)stream);
+    const long long nv = G->g0.nv;
+    const double* un = stage_in(G, u_n, G->un, nv);
+    const double* wn = stage_in(G, w_n, G->wn, nv);
+    const double* uk = stage_in(G, u_k, G->uk, nv);
+    const double* wk = stage_in(G, w_k, G->wk, nv);
+    double* fd = is_device_ptr(f) ? f : G->f;
+    double nrm = residual(G, un, wn, uk, wk, fd);
+    if (fd != f) copy_out(G, f, fd, 2 * nv);
+    CK(cudaStreamSynchronize(G->s));
+    if (norm_out) *norm_out = nrm;
+    if (!std::isfinite(nrm)) fail(OK_ERR_NONFINITE, "non-finite residual");
+  });
+}
+
+int ok_apply_jacobian(ok_grid* G, const double* u_k, const double* z, double* y, ok_stream stream) {
+  if (!G || !y) {
+    g_last_error = "NULL argument";
+    return OK_ERR_INVALID_ARG;
+  }
+  return guarded([&] {
+    StreamScope sc(G, (cudaStream_t)stream);
+    const long long nv = G->g0.nv;
+    const double* uk = stage_in(G, u_k, G->uk, nv);
+    const double* zd = stage_in(G, z, G->tmp, 2 * nv);
+    assemble_c(G, uk);
+    double* yd = is_device_ptr(y) ? y : G->rv;
+    launch_apply_j<double>(G->dim, G->g0, G->refWM, G->refWK, G->jc, G->coef, zd, yd, nullptr, G->s);
+    CKL();
+    if (yd != y) copy_out(G, y, yd, 2 * nv);
+    CK(cudaStreamSynchronize(G->s));
+  });
+}
+
+int ok_apply_preconditioner(ok_grid* G, const double* u_k, const double* v, double* z, ok_stream stream) {
+  if (!G || !z) {
+    g_last_error = "NULL argument";
+    return OK_ERR_INVALID_ARG;
+  }
+  return guarded([&] {
+    StreamScope sc(G, (cudaStream_t)stream);
+    const long long nv = G->g0.nv;
+    const double* uk = stage_in(G, u_k, G->uk, nv);
+    const double* vd = stage_in(G, v, G->tmp, 2 * nv);
+    assemble_c(G, uk);
+    double* zd = is_device_ptr(z) ? z : G->rv;
+    precond<double>(G, vd, zd, G->s);
+    CKL();
+    if (zd != z) copy_out(G, z, zd, 2 * nv);
+    CK(cudaStreamSynchronize(G->s));
+  });
+}
+
+int ok_solve_linear(ok_grid* G, const double* u_k, const double* f, double* x, ok_step_info* info,
+                    ok_stream stream) {
+  if (!G || !x) {
+    g_last_error = "NULL argument";
+    return OK_ERR_INVALID_ARG;
+  }
+  return guarded([&] {
+    StreamScope sc(G, (cudaStream_t)stream);
+    const long long nv = G->g0.nv;
+    const double* uk = stage_in(G, u_k, G->uk, nv);
+    const double* fd = stage_in(G, f, G->f, 2 * nv);
+    check_finite(G, fd, 2 * nv, "f");
+    assemble_c(G, uk);
+    auto t0 = std::chrono::steady_clock::now();
+    int its = 0;
+    double rel = 0;
+    double* xd = is_device_ptr(x) ? x : G->xs;
+    linear_solve(G, fd, xd, its, rel);
+    if (xd != x) copy_out(G, x, xd, 2 * nv);
+    CK(cudaStreamSynchronize(G->s));
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->gmres_its = its;
+      info->last_gmres_its = its;
+      info->rel_resid = rel;
+      info->converged = rel <= G->o.gmres_rtol;
+      info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (rel > G->o.gmres_rtol) fail(OK_ERR_NOT_CONVERGED, "FGMRES did not reach gmres_rtol within max_gmres");
+  });
+}
+
+int ok_newton_step(ok_grid* G, const double* u_n, const double* w_n, double* u_k, double* w_k,
+                   ok_step_info* info, ok_stream stream) {
+  if (!G || !u_k || !w_k) {
+    g_last_error = "NULL argument";
+    return OK_ERR_INVALID_ARG;
+  }
+  ok_step_info loc;
+  std::memset(&loc, 0, sizeof(loc));
+  int st = guarded([&] {
+    StreamScope sc(G, (cudaStream_t)stream);
+    const long long nv = G->g0.nv;
+    const double* un = stage_in(G, u_n, G->un, nv);
+    const double* wn = stage_in(G, w_n, G->wn, nv);
+    if (un != G->un) CK(cudaMemcpyAsync(G->un, un, nv * sizeof(double), cudaMemcpyDeviceToDevice, G->s));
+    if (wn != G->wn) CK(cudaMemcpyAsync(G->wn, wn, nv * sizeof(double), cudaMemcpyDeviceToDevice, G->s));
+    CK(cudaMemcpyAsync(G->uk, u_k, nv * sizeof(double), cudaMemcpyDefault, G->s));
+    CK(cudaMemcpyAsync(G->wk, w_k, nv * sizeof(double), cudaMemcpyDefault, G->s));
+    check_finite(G, G->uk, nv, "u_k");
+    check_finite(G, G->wk, nv, "w_k");
+    double r0 = residual(G, G->un, G->wn, G->uk, G->wk, G->f);
+    loc.newton_resid0 = r0;
+    if (!std::isfinite(r0)) fail(OK_ERR_NONFINITE, "non-finite residual");
+    double ms = 0;
+    newton_update(G, loc, ms);
+    loc.solve_ms = ms;
+    loc.newton_resid = residual(G, G->un, G->wn, G->uk, G->wk, G->f);
+    loc.converged = loc.newton_resid <= std::max(G->o.newton_atol, G->o.newton_rtol * r0);
+    copy_out(G, u_k, G->uk, nv);
+    copy_out(G, w_k, G->wk, nv);
+    CK(cudaStreamSynchronize(G->s));
+  });
+  if (info) *info = loc;
+  return st;
+}
+
+int ok_timestep(ok_grid* G, double* u, double* w, ok_step_info* info, ok_stream stream) {
+  if (!G || !u || !w) {
+    g_last_error = "NULL argument";
+    return OK_ERR_INVALID_ARG;
+  }
+  ok_step_info loc;
+  std::memset(&loc, 0, sizeof(loc));
+  int st = guarded([&] {
+    StreamScope sc(G, (cudaStream_t)stream);
+    const long long nv = G->g0.nv;
+    CK(cudaMemcpyAsync(G->un, u, nv * sizeof(double), cudaMemcpyDefault, G->s));
+    CK(cudaMemcpyAsync(G->wn, w, nv * sizeof(double), cudaMemcpyDefault, G->s));
+    check_finite(G, G->un, nv, "u");
+    check_finite(G, G->wn, nv, "w");
+    CK(cudaMemcpyAsync(G->uk, G->un, nv * sizeof(double), cudaMemcpyDeviceToDevice, G->s));
+    CK(cudaMemcpyAsync(G->wk, G->wn, nv * sizeof(double), cudaMemcpyDeviceToDevice, G->s));
+    double fn = residual(G, G->un, G->wn, G->uk, G->wk, G->f);
+    const double r0 = fn;
+    loc.newton_resid0 = r0;
+    int extra = 0;
+    double ms = 0;
+    bool ok = false;
+    while (true) {
+      if (!std::isfinite(fn)) fail(OK_ERR_NONFINITE, "non-finite Newton residual");
+      if (fn <= std::max(G->o.newton_atol, G->o.newton_rtol * r0)) {
+        ok = true;
+        if (extra >= G->o.newton_extra) break;
+        ++extra;
+      }
+      if (loc.newton_its >= G->o.max_newton) break;
+      newton_update(G, loc, ms);
+      fn = residual(G, G->un, G->wn, G->uk, G->wk, G->f);
+    }
+    loc.newton_resid = fn;
+    loc.converged = ok;
+    loc.solve_ms = ms;
+    copy_out(G, u, G->uk, nv);
+    copy_out(G, w, G->wk, nv);
+    CK(cudaStreamSynchronize(G->s));
+    if (!ok) fail(OK_ERR_NOT_CONVERGED, "Newton did not converge within max_newton steps");
+  });
+  if (info) *info = loc;
+  return st;
+}
+
+int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream stream) {
+  if (count < 0 || (count > 0 && !reqs)) {
+    g_last_error = "invalid batch";
+    return OK_ERR_INVALID_ARG;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  int done = 0, failed = 0;
+  for (int i = 0; i < count; ++i) {
+    ok_request& r = reqs[i];
+    r.status = OK_SUCCESS;
+    r.newton_its = r.gmres_its = 0;
+    if (!r.grid || !r.u || !r.w || r.steps < 0) {
+      r.status = OK_ERR_INVALID_ARG;
+      ++failed;
+      continue;
+    }
+    for (int k = 0; k < r.steps; ++k) {
+      ok_step_info info;
+      int st = ok_timestep(r.grid, r.u, r.w, &info, stream);
+      r.newton_its += info.newton_its;
+      r.gmres_its += info.gmres_its;
+      if (st != OK_SUCCESS) {
+        r.status = st;
+        break;
+      }
+    }
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (r.status == OK_SUCCESS) ++done;
+    else ++failed;
+  }
+  if (out) {
+    out->completed = done;
+    out->failed = failed;
+    out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (failed == 0) return OK_SUCCESS;
+  for (int i = 0; i < count; ++i)
+    if (reqs[i].status != OK_SUCCESS) {
+      g_last_error = "request " + std::to_string(i) + " failed with status " + std::to_string(reqs[i].status);
+      return reqs[i].status;
+    }
+  return OK_SUCCESS;
+}
+
+}  // extern "C"

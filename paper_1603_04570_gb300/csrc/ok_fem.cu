@@ -1,0 +1,335 @@
+// ok_fem.cu -- matrix-free P1 operators of the Ohta--Kawasaki system.
+//
+// Residual F and Jacobian J of the theta-scheme (Sec. 2, eqns oka/okb/newton),
+// assembled vertex by vertex on the uniform simplex grids described in
+// ok_internal.cuh.  M and K use per-class stencil tables; the variable (2,1)
+// block C = -eps^2 K - M_E(u_k) is assembled once per Newton step into a
+// symmetric per-vertex coefficient store (self + the NPOS positive offsets).
+//
+// Exact integrals on a simplex T with P1 values u_0..u_d and barycentrics
+// lambda (Dirichlet moments  int_T prod lambda^k = d! |T| prod k! / (d+sum k)!):
+//   int_T u_h lambda_a             = |T| d!/(d+2)! (p1 + u_a)
+//   int_T u_h^3 lambda_a           = |T| d!/(d+4)! (p1^3 + 3 p1 p2 + 2 p3
+//                                      + 3 u_a (p1^2 + p2) + 6 u_a^2 p1 + 6 u_a^3)
+//   int_T u_h^2 lambda_a lambda_b  = |T| d!/(d+4)! (1 + delta_ab)
+//                                      (p1^2 + p2 + 2 p1 (u_a + u_b) + 2 (u_a^2 + u_a u_b + u_b^2))
+// with p_k = sum_c u_c^k over the simplex's vertices.  (Each follows from
+// expanding prod k! as the number of label-preserving permutations of the
+// integrand's factors.)
+#include "ok_internal.cuh"
+#include "ok_kernels.h"
+
+namespace okg {
+
+// ---------------------------------------------------------------------------
+// host: reference class tables of M (h = 1) and K (h = 1)
+// ---------------------------------------------------------------------------
+template <int D>
+static void reference_tables_d(double* WM, double* WK) {
+  using Tp = Topo<D>;
+  const double vol = 1.0 / Tp::FACT;                       // |T| of a unit simplex
+  const double mcoef = vol / ((D + 1) * (D + 2));          // int lambda_a lambda_b, a != b
+  for (int cls = 0; cls < Tp::NCLASS; ++cls) {
+    int c[3] = {cls % 3, (cls / 3) % 3, cls / 9};
+    if (D == 2) c[2] = 1;
+    double* wm = WM + cls * Tp::NOFF;
+    double* wk = WK + cls * Tp::NOFF;
+    for (int o = 0; o < Tp::NOFF; ++o) wm[o] = wk[o] = 0.0;
+    for (int i = 0; i < Tp::NINC; ++i) {
+      bool ok = true;
+      for (int a = 0; a < D; ++a) {
+        bool neg = (inc_corner(D, i) >> a) & 1;
+        ok = ok && (neg ? c[a] != 0 : c[a] != 2);
+      }
+      if (!ok) continue;
+      int k = inc_pos(D, i);
+      for (int t = 0; t <= D; ++t) {
+        int o = inc_off(D, i, t);
+        wm[o] += mcoef * (t == k ? 2.0 : 1.0);
+        wk[o] += vol * path_lap(D, k, t);
+      }
+    }
+  }
+}
+
+void reference_tables(int dim, double* WM, double* WK) {
+  if (dim == 2) reference_tables_d<2>(WM, WK);
+  else reference_tables_d<3>(WM, WK);
+}
+
+// ---------------------------------------------------------------------------
+// residual  f = -F(u, w)
+// ---------------------------------------------------------------------------
+// F1 = M g1 + K g2 with g1 = a11 u - bn u_n - dt sigma m,
+//                      g2 = dt theta w + dt (1-theta) w_n,
+//   a11 = 1 + dt theta sigma, bn = 1 - dt (1-theta) sigma;
+// F2 = M w - eps^2 K u - N(u).
+template <int D>
+__global__ void __launch_bounds__(128) k_residual(Geom g, const double* __restrict__ WM,
+                                                  const double* __restrict__ WK, ResidualCoefs rc,
+                                                  const double* __restrict__ un, const double* __restrict__ wn,
+                                                  const double* __restrict__ u, const double* __restrict__ w,
+                                                  double* __restrict__ f) {
+  using Tp = Topo<D>;
+  Vtx<D> v;
+  if (!vertex_of_thread<D>(g, v)) return;
+  double us[Tp::NOFF], g1[Tp::NOFF], g2[Tp::NAX], ws[Tp::NOFF];
+  static_for<0, Tp::NOFF>([&](auto O) {
+    constexpr int o = decltype(O)::value;
+    bool ok = nb_valid<D, o>(v.c);
+    long long j = v.idx + (ok ? nb_delta<D, o>(g) : 0);
+    double uu = u[j], ww = w[j];
+    us[o] = ok ? uu : 0.0;
+    ws[o] = ok ? ww : 0.0;
+    g1[o] = ok ? (rc.a11 * uu - rc.bn * un[j] - rc.dsm) : 0.0;
+    if constexpr (o < Tp::NAX) g2[o] = ok ? (rc.dth * ww + rc.dth1 * wn[j]) : 0.0;
+  });
+  const double hd = rc.hd, hk = rc.hk;
+  double F1 = hd * dot_w<D, Tp::NOFF>(WM, v.cls, g1) + hk * dot_w<D, Tp::NAX>(WK, v.cls, g2);
+  double F2 = hd * dot_w<D, Tp::NOFF>(WM, v.cls, ws) - rc.eps2 * hk * dot_w<D, Tp::NAX>(WK, v.cls, us);
+  // N(u)_v: gather over the incident simplices
+  double nacc = 0.0;
+  static_for<0, Tp::NINC>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (inc_valid<D, i>(v.c)) {
+      constexpr int k = inc_pos(D, i);
+      double p1 = 0.0, p2 = 0.0, p3 = 0.0;
+      static_for<0, D + 1>([&](auto Tt) {
+        constexpr int o = inc_off(D, i, decltype(Tt)::value);
+        double x = us[o];
+        p1 += x;
+        p2 = fma(x, x, p2);
+        p3 = fma(x * x, x, p3);
+      });
+      double ua = us[0];
+      (void)k;
+      double t3 = p1 * p1 * p1 + 3.0 * p1 * p2 + 2.0 * p3 + 3.0 * ua * (p1 * p1 + p2) +
+                  6.0 * ua * ua * p1 + 6.0 * ua * ua * ua;
+      nacc += rc.a4 * t3 - rc.a2 * (p1 + ua);
+    }
+  });
+  F2 -= rc.vol * nacc;
+  f[v.idx] = -F1;
+  f[v.idx + g.nv] = -F2;
+}
+
+// rhs of the w0 projection: eps^2 K u0 + N(u0)
+template <int D>
+__global__ void __launch_bounds__(128) k_initw_rhs(Geom g, const double* __restrict__ WK, ResidualCoefs rc,
+                                                   const double* __restrict__ u, double* __restrict__ out) {
+  using Tp = Topo<D>;
+  Vtx<D> v;
+  if (!vertex_of_thread<D>(g, v)) return;
+  double us[Tp::NOFF];
+  load_nb<D>(u, g, v, us);
+  double acc = rc.eps2 * rc.hk * dot_w<D, Tp::NAX>(WK, v.cls, us);
+  double nacc = 0.0;
+  static_for<0, Tp::NINC>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (inc_valid<D, i>(v.c)) {
+      double p1 = 0.0, p2 = 0.0, p3 = 0.0;
+      static_for<0, D + 1>([&](auto Tt) {
+        constexpr int o = inc_off(D, i, decltype(Tt)::value);
+        double x = us[o];
+        p1 += x;
+        p2 = fma(x, x, p2);
+        p3 = fma(x * x, x, p3);
+      });
+      double ua = us[0];
+      double t3 = p1 * p1 * p1 + 3.0 * p1 * p2 + 2.0 * p3 + 3.0 * ua * (p1 * p1 + p2) +
+                  6.0 * ua * ua * p1 + 6.0 * ua * ua * ua;
+      nacc += rc.a4 * t3 - rc.a2 * (p1 + ua);
+    }
+  });
+  out[v.idx] = acc + rc.vol * nacc;
+}
+
+// ---------------------------------------------------------------------------
+// C = -eps^2 K - M_E(u) coefficients, symmetric storage:
+//   coef[0][v]   = C(v, v)
+//   coef[1+p][v] = C(v, v + pos_p)       (p = 0..NPOS-1)
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(128) k_assemble_c(Geom g, ResidualCoefs rc, const double* __restrict__ u,
+                                                    double* __restrict__ coef, float* __restrict__ coef32) {
+  using Tp = Topo<D>;
+  Vtx<D> v;
+  if (!vertex_of_thread<D>(g, v)) return;
+  double us[Tp::NOFF];
+  load_nb<D>(u, g, v, us);
+  double acc[Tp::NSLOT];
+#pragma unroll
+  for (int s = 0; s < Tp::NSLOT; ++s) acc[s] = 0.0;
+  const double kscale = rc.eps2 * rc.hk * (1.0 / Tp::FACT);   // eps^2 h^(d-2) / d!
+  static_for<0, Tp::NINC>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (inc_valid<D, i>(v.c)) {
+      constexpr int k = inc_pos(D, i);
+      double p1 = 0.0, p2 = 0.0;
+      static_for<0, D + 1>([&](auto Tt) {
+        constexpr int o = inc_off(D, i, decltype(Tt)::value);
+        p1 += us[o];
+        p2 = fma(us[o], us[o], p2);
+      });
+      const double ua = us[0];
+      const double base = p1 * p1 + p2 + 2.0 * p1 * ua + 2.0 * ua * ua;
+      static_for<0, D + 1>([&](auto Tt) {
+        constexpr int t = decltype(Tt)::value;
+        constexpr int o = inc_off(D, i, t);
+        if constexpr (o == 0 || (o & 1)) {
+          constexpr int slot = (o + 1) / 2;
+          const double ub = us[o];
+          const double P = base + 2.0 * p1 * ub + 2.0 * (ua * ub + ub * ub);
+          const double dlt = (t == k) ? 2.0 : 1.0;
+          // M_E entry: 3 int u^2 l_a l_b - int l_a l_b
+          const double me = rc.vol * dlt * (3.0 * rc.a4 * P - rc.a2);
+          acc[slot] += -kscale * path_lap(D, k, t) - me;
+        }
+      });
+    }
+  });
+#pragma unroll
+  for (int s = 0; s < Tp::NSLOT; ++s) {
+    coef[s * g.nv + v.idx] = acc[s];
+    coef32[s * g.nv + v.idx] = (float)acc[s];
+  }
+}
+
+// sum over the symmetric store: (C y)_v
+template <int D, typename T, typename TY>
+__device__ __forceinline__ T capply_at(const Geom& g, const Vtx<D>& v, const T* __restrict__ coef,
+                                       const TY* __restrict__ y, T yscale) {
+  using Tp = Topo<D>;
+  T acc = coef[v.idx] * (T)y[v.idx] * yscale;
+  static_for<0, Tp::NPOS>([&](auto P) {
+    constexpr int p = decltype(P)::value;
+    constexpr int op = 2 * p + 1, om = 2 * p + 2;
+    if (nb_valid<D, op>(v.c)) {
+      long long j = v.idx + nb_delta<D, op>(g);
+      acc = fma(coef[(1 + p) * g.nv + v.idx], (T)y[j] * yscale, acc);
+    }
+    if (nb_valid<D, om>(v.c)) {
+      long long j = v.idx + nb_delta<D, om>(g);
+      acc = fma(coef[(1 + p) * g.nv + j], (T)y[j] * yscale, acc);
+    }
+  });
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// y = alpha J z + beta y0, J = [a11 M, dth K; C, M]  (eqn newton)
+// ---------------------------------------------------------------------------
+template <int D, typename TZ>
+__global__ void __launch_bounds__(128) k_apply_j(Geom g, const double* __restrict__ WM,
+                                                 const double* __restrict__ WK, JCoefs jc,
+                                                 const double* __restrict__ coef, const TZ* __restrict__ z,
+                                                 double* __restrict__ y, const double* __restrict__ y0) {
+  using Tp = Topo<D>;
+  Vtx<D> v;
+  if (!vertex_of_thread<D>(g, v)) return;
+  double z1[Tp::NOFF], z2[Tp::NOFF];
+  load_nb<D>(z, g, v, z1);
+  load_nb<D>(z + g.nv, g, v, z2);
+  double y1 = jc.a11hd * dot_w<D, Tp::NOFF>(WM, v.cls, z1) + jc.dthhk * dot_w<D, Tp::NAX>(WK, v.cls, z2);
+  double y2 = jc.hd * dot_w<D, Tp::NOFF>(WM, v.cls, z2) + capply_at<D, double>(g, v, coef, z, 1.0);
+  if (y0) {
+    y1 = jc.beta * y0[v.idx] + jc.alpha * y1;
+    y2 = jc.beta * y0[v.idx + g.nv] + jc.alpha * y2;
+  }
+  y[v.idx] = y1;
+  y[v.idx + g.nv] = y2;
+}
+
+// ---------------------------------------------------------------------------
+// preconditioner C-step:  t = s * v2 - C (ys * y1)     (eqn prec: r2 - C A^{-1} r1)
+// ---------------------------------------------------------------------------
+template <int D, typename T, typename TV>
+__global__ void __launch_bounds__(128) k_cstep(Geom g, const T* __restrict__ coef, const TV* __restrict__ v2,
+                                               T vscale, const T* __restrict__ y1, T yscale, T* __restrict__ t) {
+  Vtx<D> v;
+  if (!vertex_of_thread<D>(g, v)) return;
+  T cy = capply_at<D, T>(g, v, coef, y1, yscale);
+  t[v.idx] = (T)v2[v.idx] * vscale - cy;
+}
+
+// Richardson residual for k_R = 2:  out = t - (M y - C a)   (S y = M y - C A~^{-1} B y)
+template <int D, typename T>
+__global__ void __launch_bounds__(128) k_schur_resid(Geom g, const T* __restrict__ WM, T hd, const T* __restrict__ coef,
+                                                     const T* __restrict__ t, const T* __restrict__ y,
+                                                     const T* __restrict__ a, T ascale, T* __restrict__ out) {
+  using Tp = Topo<D>;
+  Vtx<D> v;
+  if (!vertex_of_thread<D>(g, v)) return;
+  T ys[Tp::NOFF];
+  load_nb<D>(y, g, v, ys);
+  T my = hd * dot_w<D, Tp::NOFF>(WM, v.cls, ys);
+  T ca = capply_at<D, T>(g, v, coef, a, ascale);
+  out[v.idx] = t[v.idx] - my + ca;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline dim3 grid_of(int dim, const Geom& g, int bx) {
+  return dim3((g.n1 + bx - 1) / bx, g.n1, dim == 3 ? g.n1 : 1);
+}
+
+void launch_residual(int dim, const Geom& g, const double* WM, const double* WK, const ResidualCoefs& rc,
+                     const double* un, const double* wn, const double* u, const double* w, double* f,
+                     cudaStream_t s) {
+  dim3 grd = grid_of(dim, g, 128);
+  if (dim == 2) k_residual<2><<<grd, 128, 0, s>>>(g, WM, WK, rc, un, wn, u, w, f);
+  else k_residual<3><<<grd, 128, 0, s>>>(g, WM, WK, rc, un, wn, u, w, f);
+}
+
+void launch_initw_rhs(int dim, const Geom& g, const double* WK, const ResidualCoefs& rc, const double* u,
+                      double* out, cudaStream_t s) {
+  dim3 grd = grid_of(dim, g, 128);
+  if (dim == 2) k_initw_rhs<2><<<grd, 128, 0, s>>>(g, WK, rc, u, out);
+  else k_initw_rhs<3><<<grd, 128, 0, s>>>(g, WK, rc, u, out);
+}
+
+void launch_assemble_c(int dim, const Geom& g, const ResidualCoefs& rc, const double* u, double* coef,
+                       float* coef32, cudaStream_t s) {
+  dim3 grd = grid_of(dim, g, 128);
+  if (dim == 2) k_assemble_c<2><<<grd, 128, 0, s>>>(g, rc, u, coef, coef32);
+  else k_assemble_c<3><<<grd, 128, 0, s>>>(g, rc, u, coef, coef32);
+}
+
+template <typename TZ>
+void launch_apply_j(int dim, const Geom& g, const double* WM, const double* WK, const JCoefs& jc,
+                    const double* coef, const TZ* z, double* y, const double* y0, cudaStream_t s) {
+  dim3 grd = grid_of(dim, g, 128);
+  if (dim == 2) k_apply_j<2, TZ><<<grd, 128, 0, s>>>(g, WM, WK, jc, coef, z, y, y0);
+  else k_apply_j<3, TZ><<<grd, 128, 0, s>>>(g, WM, WK, jc, coef, z, y, y0);
+}
+template void launch_apply_j<double>(int, const Geom&, const double*, const double*, const JCoefs&,
+                                     const double*, const double*, double*, const double*, cudaStream_t);
+template void launch_apply_j<float>(int, const Geom&, const double*, const double*, const JCoefs&,
+                                    const double*, const float*, double*, const double*, cudaStream_t);
+
+template <typename T, typename TV>
+void launch_cstep(int dim, const Geom& g, const T* coef, const TV* v2, T vscale, const T* y1, T yscale, T* t,
+                  cudaStream_t s) {
+  dim3 grd = grid_of(dim, g, 128);
+  if (dim == 2) k_cstep<2, T, TV><<<grd, 128, 0, s>>>(g, coef, v2, vscale, y1, yscale, t);
+  else k_cstep<3, T, TV><<<grd, 128, 0, s>>>(g, coef, v2, vscale, y1, yscale, t);
+}
+template void launch_cstep<double, double>(int, const Geom&, const double*, const double*, double, const double*,
+                                           double, double*, cudaStream_t);
+template void launch_cstep<float, double>(int, const Geom&, const float*, const double*, float, const float*, float,
+                                          float*, cudaStream_t);
+
+template <typename T>
+void launch_schur_resid(int dim, const Geom& g, const T* WM, T hd, const T* coef, const T* t, const T* y,
+                        const T* a, T ascale, T* out, cudaStream_t s) {
+  dim3 grd = grid_of(dim, g, 128);
+  if (dim == 2) k_schur_resid<2, T><<<grd, 128, 0, s>>>(g, WM, hd, coef, t, y, a, ascale, out);
+  else k_schur_resid<3, T><<<grd, 128, 0, s>>>(g, WM, hd, coef, t, y, a, ascale, out);
+}
+template void launch_schur_resid<double>(int, const Geom&, const double*, double, const double*, const double*,
+                                         const double*, const double*, double, double*, cudaStream_t);
+template void launch_schur_resid<float>(int, const Geom&, const float*, float, const float*, const float*,
+                                        const float*, const float*, float, float*, cudaStream_t);
+
+}  // namespace okg

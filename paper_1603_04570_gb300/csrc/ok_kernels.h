@@ -1,0 +1,126 @@
+// ok_kernels.h -- kernel launchers shared between the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include "ok_internal.cuh"
+
+namespace okg {
+
+// Scalars of the residual / projection kernels (see ok_fem.cu).
+struct ResidualCoefs {
+  double a11;    // 1 + dt theta sigma
+  double bn;     // 1 - dt (1 - theta) sigma
+  double dsm;    // dt sigma m
+  double dth;    // dt theta
+  double dth1;   // dt (1 - theta)
+  double hd;     // h^d       (mass scale)
+  double hk;     // h^(d-2)   (stiffness scale)
+  double eps2;   // eps^2
+  double vol;    // |T| = h^d / d!
+  double a4;     // d! / (d+4)!
+  double a2;     // d! / (d+2)!
+};
+
+// y = alpha J z + beta y0 (y0 may be null: y = J z)
+struct JCoefs {
+  double a11hd;  // (1 + dt theta sigma) h^d
+  double dthhk;  // dt theta h^(d-2)
+  double hd;
+  double alpha, beta;
+};
+
+void launch_residual(int dim, const Geom& g, const double* WM, const double* WK, const ResidualCoefs& rc,
+                     const double* un, const double* wn, const double* u, const double* w, double* f,
+                     cudaStream_t s);
+void launch_initw_rhs(int dim, const Geom& g, const double* WK, const ResidualCoefs& rc, const double* u,
+                      double* out, cudaStream_t s);
+void launch_assemble_c(int dim, const Geom& g, const ResidualCoefs& rc, const double* u, double* coef,
+                       float* coef32, cudaStream_t s);
+template <typename TZ>
+void launch_apply_j(int dim, const Geom& g, const double* WM, const double* WK, const JCoefs& jc,
+                    const double* coef, const TZ* z, double* y, const double* y0, cudaStream_t s);
+template <typename T, typename TV>
+void launch_cstep(int dim, const Geom& g, const T* coef, const TV* v2, T vscale, const T* y1, T yscale, T* t,
+                  cudaStream_t s);
+template <typename T>
+void launch_schur_resid(int dim, const Geom& g, const T* WM, T hd, const T* coef, const T* t, const T* y,
+                        const T* a, T ascale, T* out, cudaStream_t s);
+
+// ---- Chebyshev / multigrid (ok_mg.cu) ------------------------------------
+// All operate on one level with a per-class weight table W (already scaled
+// to the level) and per-class inverse diagonal dinv.
+// r = s*b, d = dinv r / th                          (x = 0 start)
+template <typename T, typename TB>
+void launch_cheb_init(int dim, const Geom& g, const T* dinv, const TB* b, T bscale, T* r, T* d, T inv_th,
+                      cudaStream_t s);
+// r = b - W x, d = dinv r / th
+template <typename T>
+void launch_resid_init(int dim, const Geom& g, const T* W, const T* dinv, const T* b, const T* x, T* r, T* d,
+                       T inv_th, cudaStream_t s);
+// x = (first ? 0 : x) + d_in; r -= W d_in; d_out = c1 d_in + c2 dinv r
+template <typename T>
+void launch_cheb_step(int dim, const Geom& g, const T* W, const T* dinv, T* x, T* r, const T* d_in, T* d_out,
+                      T c1, T c2, bool first, cudaStream_t s);
+// x = (first ? 0 : x) + d_in; if (r) r -= W d_in; if (out) out = oscale * x
+template <typename T, typename TO>
+void launch_cheb_last(int dim, const Geom& g, const T* W, T* x, T* r, const T* d_in, bool first, TO* out,
+                      T oscale, cudaStream_t s);
+// b_c = P^T r_f
+template <typename T>
+void launch_restrict(int dim, const Geom& gf, const Geom& gc, const T* rf, T* bc, cudaStream_t s);
+// x_f += P x_c
+template <typename T>
+void launch_prolong_add(int dim, const Geom& gf, const Geom& gc, T* xf, const T* xc, cudaStream_t s);
+// x = Ainv b on the coarsest level (dense)
+template <typename T>
+void launch_coarse_solve(long long nc, const T* Ainv, const T* b, T* x, cudaStream_t s);
+// y = alpha W x (+ beta y0 when y0 != null), first NO offsets: full (M-like) or axis (K)
+template <typename T, typename TX, typename TY>
+void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha,
+                     const TY* y0, T beta, cudaStream_t s);
+// dense matrix of a level operator (row-major nv x nv) from its class table
+void launch_dense_from_table(int dim, const Geom& g, const double* W, double* A, cudaStream_t s);
+// in-place Gauss--Jordan inverse of an SPD matrix (single block); work: n x 2n
+void launch_gauss_jordan(long long n, const double* A, double* work, double* Ainv, cudaStream_t s);
+
+// ---- Krylov (ok_krylov.cu) -----------------------------------------------
+struct KrylovState;   // device-resident Arnoldi/Givens state (ok_krylov.cu)
+struct RedScratch {
+  double* partials;    // RED_MAX_BLOCKS * KRYLOV_MAX
+  unsigned int* counter;
+};
+int krylov_blocks();
+// ks->h1[0..K) = V^T w       (V: K vectors with leading dimension ldv)
+void launch_multidot(const double* V, long long ldv, int K, const double* w, long long N, RedScratch rs,
+                     double* out, cudaStream_t s);
+// w -= V h_in; h_out = V^T w
+void launch_update_multidot(const double* V, long long ldv, int K, const double* h_in, double* w, long long N,
+                            RedScratch rs, double* h_out, cudaStream_t s);
+// w -= V h2; then Arnoldi column j finalisation + Givens in the last block
+void launch_update_norm_givens(const double* V, long long ldv, int K, double* w, long long N, RedScratch rs,
+                               KrylovState* ks, int j, cudaStream_t s);
+// w *= ks->inv_eta
+void launch_scale_by(double* w, long long N, const double* factor, cudaStream_t s);
+// out = ||x||_2 (device scalar)
+void launch_norm(const double* x, long long N, RedScratch rs, double* out, cudaStream_t s);
+// cycle start: v0 = r / beta with beta = ||r|| on device; ks reset
+void launch_cycle_start(KrylovState* ks, const double* beta, cudaStream_t s);
+// y = H^{-1} g (upper triangular, size k)
+void launch_lsq(KrylovState* ks, int k, cudaStream_t s);
+// x += sum_k y_k Z_k
+template <typename TZ>
+void launch_multi_axpy(const TZ* Z, long long ldz, int K, const KrylovState* ks, double* x, long long N,
+                       cudaStream_t s);
+// y = a x + b y, typed
+template <typename TX, typename TY>
+void launch_axpby(long long N, double a, const TX* x, double b, TY* y, cudaStream_t s);
+// flag |= any non-finite in x
+void launch_check_finite(const double* x, long long N, int* flag, cudaStream_t s);
+size_t krylov_state_bytes();
+double* ks_resid_ptr(KrylovState* ks);
+double* ks_eta_ptr(KrylovState* ks);
+double* ks_beta_ptr(KrylovState* ks);
+double* ks_h1_ptr(KrylovState* ks);
+double* ks_h2_ptr(KrylovState* ks);
+
+}  // namespace okg

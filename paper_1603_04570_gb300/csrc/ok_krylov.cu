@@ -1,0 +1,356 @@
+// ok_krylov.cu -- float64 kernels of right-preconditioned restarted FGMRES.
+//
+// Arnoldi step j (Saad, "A flexible inner-outer preconditioned GMRES
+// algorithm", SISC 14, 1993) with w = J z_j orthogonalised against
+// v_0..v_j by classical Gram--Schmidt applied twice (CGS2):
+//     h1 = V^T w;  w -= V h1;  h2 = V^T w;  w -= V h2;  H(:,j) = h1 + h2;
+//     eta = ||w||;  H(j+1,j) = eta;  v_{j+1} = w / eta;
+// then the new column is reduced by Givens rotations and |g_{j+1}| is the
+// residual norm of the least-squares problem min || beta e_1 - H y ||.
+//
+// Reductions are deterministic: a fixed grid, a fixed element-to-thread map,
+// per-block partials and an in-order sum by the last block to finish (found
+// with an atomic ticket; no block waits on another).
+#include <math.h>
+#include "ok_internal.cuh"
+#include "ok_kernels.h"
+
+namespace okg {
+
+struct KrylovState {
+  double H[(KRYLOV_MAX + 1) * KRYLOV_MAX];   // H(i,j) at i + (KRYLOV_MAX+1) j; rotated in place
+  double cs[KRYLOV_MAX], sn[KRYLOV_MAX];
+  double g[KRYLOV_MAX + 1];
+  double h1[KRYLOV_MAX + 1], h2[KRYLOV_MAX + 1];
+  double y[KRYLOV_MAX];
+  double beta, inv_beta;
+  double eta, inv_eta;
+  double resid;
+};
+
+size_t krylov_state_bytes() { return sizeof(KrylovState); }
+double* ks_resid_ptr(KrylovState* ks) { return &ks->resid; }
+double* ks_eta_ptr(KrylovState* ks) { return &ks->eta; }
+double* ks_beta_ptr(KrylovState* ks) { return &ks->beta; }
+double* ks_h1_ptr(KrylovState* ks) { return ks->h1; }
+double* ks_h2_ptr(KrylovState* ks) { return ks->h2; }
+
+static constexpr int RT = 256;    // threads per reduction block
+static constexpr int KC = 16;     // vectors per multi-dot launch (register budget)
+
+static int g_blocks = 0;
+int krylov_blocks() {
+  if (g_blocks == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g_blocks = sms > 0 ? 2 * sms : 256;
+    if (g_blocks > RED_MAX_BLOCKS) g_blocks = RED_MAX_BLOCKS;
+  }
+  return g_blocks;
+}
+
+// Reduce acc[0..K) over the block into partials[blockIdx.x * KRYLOV_MAX + k].
+template <int NK>
+__device__ __forceinline__ void block_partials(const double (&acc)[NK], int K, double* __restrict__ partials) {
+  __shared__ double sm[RT / 32][NK];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NK; ++k) {
+    if (k < K) {
+      double a = acc[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) sm[warp][k] = a;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double a = 0.0;
+#pragma unroll
+    for (int w = 0; w < RT / 32; ++w) a += sm[w][threadIdx.x];
+    partials[blockIdx.x * KRYLOV_MAX + threadIdx.x] = a;
+  }
+}
+
+// True in exactly one block: the last to finish.  Resets the ticket.
+__device__ __forceinline__ bool last_block(unsigned int* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+    if (last) *counter = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ __forceinline__ void final_sums(const double* __restrict__ partials, int K, double* __restrict__ out) {
+  if (threadIdx.x < K) {
+    double a = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) a += partials[b * KRYLOV_MAX + threadIdx.x];
+    out[threadIdx.x] = a;
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ V, long long ldv, int K,
+                                                 const double* __restrict__ w, long long N,
+                                                 double* __restrict__ partials, unsigned int* counter,
+                                                 double* __restrict__ out) {
+  double acc[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) acc[k] = 0.0;
+  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
+    const double we = w[e];
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k < K) acc[k] = fma(V[k * ldv + e], we, acc[k]);
+  }
+  block_partials<KC>(acc, K, partials);
+  if (last_block(counter)) final_sums(partials, K, out);
+}
+
+__global__ void __launch_bounds__(RT) k_update_multidot(const double* __restrict__ V, long long ldv, int K,
+                                                        const double* __restrict__ hin, double* __restrict__ w,
+                                                        long long N, double* __restrict__ partials,
+                                                        unsigned int* counter, double* __restrict__ out) {
+  __shared__ double hs[KC];
+  if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < K ? hin[threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) acc[k] = 0.0;
+  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
+    double vals[KC];
+    double we = w[e];
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k < K) {
+        vals[k] = V[k * ldv + e];
+        we = fma(-hs[k], vals[k], we);
+      }
+    w[e] = we;
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k < K) acc[k] = fma(vals[k], we, acc[k]);
+  }
+  block_partials<KC>(acc, K, partials);
+  if (last_block(counter)) final_sums(partials, K, out);
+}
+
+// w -= V h2 (h2 = ks->h2), ||w||^2; last block: column j of H, Givens, residual.
+__global__ void __launch_bounds__(RT) k_update_norm_givens(const double* __restrict__ V, long long ldv, int K,
+                                                           double* __restrict__ w, long long N,
+                                                           double* __restrict__ partials, unsigned int* counter,
+                                                           KrylovState* ks, int j, int K0) {
+  __shared__ double hs[KC];
+  if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < K ? ks->h2[K0 + threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[1] = {0.0};
+  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
+    double we = w[e];
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k < K) we = fma(-hs[k], V[k * ldv + e], we);
+    w[e] = we;
+    acc[0] = fma(we, we, acc[0]);
+  }
+  block_partials<1>(acc, 1, partials);
+  if (last_block(counter) && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += partials[b * KRYLOV_MAX];
+    const int ld = KRYLOV_MAX + 1;
+    double* Hj = ks->H + (long long)ld * j;
+    for (int i = 0; i <= j; ++i) Hj[i] = ks->h1[i] + ks->h2[i];
+    const double eta = sqrt(s);
+    Hj[j + 1] = eta;
+    ks->eta = eta;
+    ks->inv_eta = eta > 0.0 ? 1.0 / eta : 0.0;
+    for (int i = 0; i < j; ++i) {                       // previous rotations
+      const double a = Hj[i], b = Hj[i + 1];
+      Hj[i] = ks->cs[i] * a + ks->sn[i] * b;
+      Hj[i + 1] = -ks->sn[i] * a + ks->cs[i] * b;
+    }
+    const double a = Hj[j], b = Hj[j + 1];
+    const double r = hypot(a, b);
+    const double c = r > 0.0 ? a / r : 1.0, sn = r > 0.0 ? b / r : 0.0;
+    ks->cs[j] = c;
+    ks->sn[j] = sn;
+    Hj[j] = r;
+    Hj[j + 1] = 0.0;
+    ks->g[j + 1] = -sn * ks->g[j];
+    ks->g[j] = c * ks->g[j];
+    ks->resid = fabs(ks->g[j + 1]);
+  }
+}
+
+// The second CGS2 pass may need several KC-vector chunks: the update kernel
+// above handles one chunk (K0 offset); when K > KC the host launches the
+// update chunks first and the norm/Givens only with the last chunk.
+__global__ void __launch_bounds__(RT) k_update_only(const double* __restrict__ V, long long ldv, int K,
+                                                    const double* __restrict__ h, double* __restrict__ w,
+                                                    long long N) {
+  __shared__ double hs[KC];
+  if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < K ? h[threadIdx.x] : 0.0;
+  __syncthreads();
+  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
+    double we = w[e];
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k < K) we = fma(-hs[k], V[k * ldv + e], we);
+    w[e] = we;
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_sumsq(const double* __restrict__ x, long long N,
+                                              double* __restrict__ partials, unsigned int* counter,
+                                              double* __restrict__ out) {
+  double acc[1] = {0.0};
+  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT)
+    acc[0] = fma(x[e], x[e], acc[0]);
+  block_partials<1>(acc, 1, partials);
+  if (last_block(counter) && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += partials[b * KRYLOV_MAX];
+    *out = sqrt(s);
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_scale_by(double* __restrict__ w, long long N,
+                                                 const double* __restrict__ factor) {
+  const double f = *factor;
+  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) w[e] *= f;
+}
+
+__global__ void k_cycle_start(KrylovState* ks, const double* __restrict__ beta) {
+  if (threadIdx.x == 0) {
+    const double b = *beta;
+    ks->beta = b;
+    ks->inv_beta = b > 0.0 ? 1.0 / b : 0.0;
+    for (int i = 0; i <= KRYLOV_MAX; ++i) ks->g[i] = 0.0;
+    ks->g[0] = b;
+    ks->resid = b;
+  }
+}
+
+// back substitution R y = g, R = rotated H (k x k upper triangular)
+__global__ void k_lsq(KrylovState* ks, int k) {
+  if (threadIdx.x == 0) {
+    const int ld = KRYLOV_MAX + 1;
+    for (int i = k - 1; i >= 0; --i) {
+      double s = ks->g[i];
+      for (int c = i + 1; c < k; ++c) s -= ks->H[i + ld * c] * ks->y[c];
+      const double d = ks->H[i + ld * i];
+      ks->y[i] = d != 0.0 ? s / d : 0.0;
+    }
+  }
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(RT) k_multi_axpy(const TZ* __restrict__ Z, long long ldz, int K,
+                                                   const KrylovState* __restrict__ ks, double* __restrict__ x,
+                                                   long long N) {
+  __shared__ double ys[KRYLOV_MAX];
+  if (threadIdx.x < KRYLOV_MAX) ys[threadIdx.x] = threadIdx.x < K ? ks->y[threadIdx.x] : 0.0;
+  __syncthreads();
+  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
+    double acc = x[e];
+    for (int k = 0; k < K; ++k) acc = fma(ys[k], (double)Z[k * ldz + e], acc);
+    x[e] = acc;
+  }
+}
+
+template <typename TX, typename TY>
+__global__ void __launch_bounds__(RT) k_axpby(long long N, double a, const TX* __restrict__ x, double b,
+                                              TY* __restrict__ y) {
+  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
+    double v = a * (double)x[e];
+    if (b != 0.0) v = fma(b, (double)y[e], v);
+    y[e] = (TY)v;
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_check_finite(const double* __restrict__ x, long long N, int* flag) {
+  int bad = 0;
+  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT)
+    bad |= !isfinite(x[e]);
+  bad = __syncthreads_or(bad);
+  if (bad && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_multidot(const double* V, long long ldv, int K, const double* w, long long N, RedScratch rs,
+                     double* out, cudaStream_t s) {
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    int kk = K - k0 < KC ? K - k0 : KC;
+    k_multidot<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, kk, w, N, rs.partials, rs.counter, out + k0);
+  }
+}
+
+void launch_update_multidot(const double* V, long long ldv, int K, const double* h_in, double* w, long long N,
+                            RedScratch rs, double* h_out, cudaStream_t s) {
+  if (K <= KC) {
+    k_update_multidot<<<krylov_blocks(), RT, 0, s>>>(V, ldv, K, h_in, w, N, rs.partials, rs.counter, h_out);
+    return;
+  }
+  for (int k0 = 0; k0 < K; k0 += KC) {   // all updates first, then the dots of the final w
+    int kk = K - k0 < KC ? K - k0 : KC;
+    k_update_only<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, kk, h_in + k0, w, N);
+  }
+  launch_multidot(V, ldv, K, w, N, rs, h_out, s);
+}
+
+void launch_update_norm_givens(const double* V, long long ldv, int K, double* w, long long N, RedScratch rs,
+                               KrylovState* ks, int j, cudaStream_t s) {
+  int k0 = 0;
+  for (; K - k0 > KC; k0 += KC) {
+    // h2 lives in device memory inside ks; chunk offsets index it directly
+    k_update_only<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, KC, ks->h2 + k0, w, N);
+  }
+  k_update_norm_givens<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, K - k0, w, N, rs.partials, rs.counter,
+                                                       ks, j, k0);
+}
+
+void launch_scale_by(double* w, long long N, const double* factor, cudaStream_t s) {
+  k_scale_by<<<krylov_blocks(), RT, 0, s>>>(w, N, factor);
+}
+
+void launch_norm(const double* x, long long N, RedScratch rs, double* out, cudaStream_t s) {
+  k_sumsq<<<krylov_blocks(), RT, 0, s>>>(x, N, rs.partials, rs.counter, out);
+}
+
+void launch_cycle_start(KrylovState* ks, const double* beta, cudaStream_t s) {
+  k_cycle_start<<<1, 32, 0, s>>>(ks, beta);
+}
+
+void launch_lsq(KrylovState* ks, int k, cudaStream_t s) { k_lsq<<<1, 32, 0, s>>>(ks, k); }
+
+template <typename TZ>
+void launch_multi_axpy(const TZ* Z, long long ldz, int K, const KrylovState* ks, double* x, long long N,
+                       cudaStream_t s) {
+  k_multi_axpy<TZ><<<krylov_blocks(), RT, 0, s>>>(Z, ldz, K, ks, x, N);
+}
+template void launch_multi_axpy<double>(const double*, long long, int, const KrylovState*, double*, long long,
+                                        cudaStream_t);
+template void launch_multi_axpy<float>(const float*, long long, int, const KrylovState*, double*, long long,
+                                       cudaStream_t);
+
+template <typename TX, typename TY>
+void launch_axpby(long long N, double a, const TX* x, double b, TY* y, cudaStream_t s) {
+  k_axpby<TX, TY><<<krylov_blocks(), RT, 0, s>>>(N, a, x, b, y);
+}
+template void launch_axpby<double, double>(long long, double, const double*, double, double*, cudaStream_t);
+template void launch_axpby<float, double>(long long, double, const float*, double, double*, cudaStream_t);
+template void launch_axpby<double, float>(long long, double, const double*, double, float*, cudaStream_t);
+template void launch_axpby<float, float>(long long, double, const float*, double, float*, cudaStream_t);
+
+void launch_check_finite(const double* x, long long N, int* flag, cudaStream_t s) {
+  k_check_finite<<<krylov_blocks(), RT, 0, s>>>(x, N, flag);
+}
+
+}  // namespace okg

@@ -1,0 +1,73 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every
+function include/ok.h declares; option defaults and host-side argument
+validation work without a GPU (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1603_04570_gb300 as ok
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ok_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["ok_grid_create", "ok_grid_destroy", "ok_assemble_rhs", "ok_newton_step",
+                     "ok_timestep", "ok_solve_batch", "ok_init_w", "ok_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ok.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert ok.version().startswith("ok-gb300")
+
+
+def test_default_opts_match_header_documentation():
+    o = ok.ok_default_opts()
+    assert (o.restart, o.q_A, o.n_V, o.k_R, o.smooth_pre, o.smooth_post) == (30, 10, 5, 1, 2, 2)
+    assert o.precision == ok.OK_FP64 and o.gmres_rtol == 1e-10 and o.smooth_lo_frac == 0.25
+    assert ctypes.sizeof(ok.Opts) == 12 * 4 + 4 * 8
+
+
+@pytest.mark.parametrize("dim,n,kw,msg", [
+    (4, 8, {}, "dim"),
+    (2, 1, {}, "n must"),
+    (2, 8, {"restart": 0}, "restart"),
+    (2, 8, {"restart": 64}, "restart"),
+    (2, 8, {"k_R": 3}, "k_R"),
+    (2, 8, {"precision": 7}, "precision"),
+    (2, 8, {"q_A": 0}, "q_A"),
+    (2, 8, {"gmres_rtol": 0.0}, "tolerances"),
+])
+def test_invalid_arguments_rejected_on_host(dim, n, kw, msg):
+    p = ok.Params(0.04, 100.0, 0.0, 1.0, 1e-4)
+    with pytest.raises(ok.OkError) as e:
+        ok.ok_grid_create(dim, n, p, ok.ok_default_opts(**kw))
+    assert e.value.status == ok.OK_ERR_INVALID_ARG and msg in str(e.value)
+
+
+def test_invalid_params_rejected_on_host():
+    for bad in [ok.Params(0.0, 100, 0, 1, 1e-4), ok.Params(0.04, 100, 0, 0.0, 1e-4),
+                ok.Params(0.04, 100, 0, 1, -1.0), ok.Params(0.04, -1, 0, 1, 1e-4)]:
+        with pytest.raises(ok.OkError) as e:
+            ok.ok_grid_create(2, 8, bad)
+        assert e.value.status == ok.OK_ERR_INVALID_ARG
+
+
+def test_too_large_coarse_level_rejected():
+    with pytest.raises(ok.OkError) as e:
+        ok.ok_grid_create(3, 11, ok.Params(0.04, 100, 0, 1, 1e-4))    # 12^3 coarse unknowns
+    assert e.value.status == ok.OK_ERR_INVALID_ARG and "coarsest" in str(e.value)

@@ -1,0 +1,242 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Element-wise comparisons on seeded inputs at sizes the oracle handles in
+seconds, covering degenerate grids (n = 2, 3), single-level multigrid (odd n),
+several levels, and rows whose length is not a multiple of the 128-thread
+block (ragged tails).  Tolerances:
+  * residual, Jacobian: 1e-12 relative to the largest entry (a few roundings
+    of sums of <= 15 + 24 terms);
+  * FP64 preconditioner: 1e-10 relative (tens of Chebyshev sweeps, each a
+    contraction, so rounding does not grow);
+  * mixed preconditioner: 2e-4 relative (float32 arithmetic);
+  * timesteps: 1e-10 (FP64) and 1e-8 (mixed) relative in the 2-norm after
+    every step, the targets of the method.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import ok_inputs as oi
+import paper_1603_04570_gb300 as ok
+from oracle.fem import Mesh, Params, System
+from oracle.solvers import Options, Preconditioner, timestep
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel_inf(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def rel2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+P_DEFAULT = dict(eps=0.04, sigma=100.0, m=0.1, theta=0.5, dt=2e-3)
+GRIDS = [(2, 2), (2, 3), (2, 5), (2, 8), (2, 12), (2, 17), (2, 40), (2, 160),
+         (3, 2), (3, 3), (3, 4), (3, 6), (3, 8), (3, 24)]
+
+
+def make(dim, n, seed=0, **kw):
+    p = dict(P_DEFAULT)
+    p.update(kw)
+    sysm = System(Mesh(dim, n), Params(p["eps"], p["sigma"], p["m"], p["theta"], p["dt"]))
+    rng = np.random.default_rng(seed + 100 * dim + n)
+    return sysm, p, rng
+
+
+@pytest.mark.parametrize("dim,n", GRIDS)
+def test_residual_parity(dim, n):
+    sysm, p, rng = make(dim, n)
+    nv = sysm.mesh.nv
+    un, wn, u, w = (rng.uniform(-1.1, 1.1, nv) for _ in range(4))
+    F = sysm.residual(un, wn, u, w)
+    with ok.Grid(dim, n, **p) as g:
+        f = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        nrm = g.assemble_rhs(dev(un), dev(wn), dev(u), dev(w), f)
+        assert rel_inf(host(f), -F) < 1e-12
+        assert abs(nrm - np.linalg.norm(F)) <= 1e-12 * np.linalg.norm(F)
+        fh = np.empty(2 * nv)                       # host arrays take the staging path
+        g.assemble_rhs(un, wn, u, w, fh)
+        assert np.array_equal(fh, host(f))
+
+
+@pytest.mark.parametrize("dim,n", GRIDS)
+def test_jacobian_parity(dim, n):
+    sysm, p, rng = make(dim, n, seed=1)
+    nv = sysm.mesh.nv
+    u = rng.uniform(-1.1, 1.1, nv)
+    z = rng.standard_normal(2 * nv)
+    J = sysm.jacobian(u)
+    with ok.Grid(dim, n, **p) as g:
+        y = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        g.apply_jacobian(dev(u), dev(z), y)
+        ref = J @ z
+        scale = np.abs(J) @ np.abs(z)
+        assert (np.abs(host(y) - ref) <= 1e-13 * scale.max() + 1e-15 * scale).all()
+
+
+PREC_CASES = [(2, 3, 1), (2, 8, 1), (2, 12, 2), (2, 17, 1), (2, 40, 1), (2, 40, 2), (2, 160, 1),
+              (3, 2, 1), (3, 4, 2), (3, 6, 1), (3, 8, 1), (3, 24, 1)]
+
+
+@pytest.mark.parametrize("dim,n,k_R", PREC_CASES)
+@pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
+def test_preconditioner_parity(dim, n, k_R, precision):
+    sysm, p, rng = make(dim, n, seed=2, dt=1e-4)
+    nv = sysm.mesh.nv
+    u = rng.uniform(-1.0, 1.0, nv)
+    v = rng.standard_normal(2 * nv)
+    P = Preconditioner(sysm, u, mode="inexact", q_A=10, n_V=3, k_R=k_R, nu_pre=2, nu_post=2)
+    ref = P.apply(v)
+    with ok.Grid(dim, n, **p, n_V=3, k_R=k_R, precision=precision) as g:
+        z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        g.apply_preconditioner(dev(u), dev(v), z)
+        tol = 1e-10 if precision == ok.OK_FP64 else 2e-4
+        zh = host(z)
+        assert rel_inf(zh[:nv], ref[:nv]) < tol
+        assert rel_inf(zh[nv:], ref[nv:]) < tol
+
+
+@pytest.mark.parametrize("dim,n", [(2, 32), (3, 8)])
+def test_init_w_parity(dim, n):
+    sysm, p, rng = make(dim, n, seed=3)
+    u0 = 0.1 + 0.3 * rng.uniform(-1, 1, sysm.mesh.nv)
+    ref = sysm.initial_w(u0)
+    with ok.Grid(dim, n, **p) as g:
+        w0 = torch.empty(sysm.mesh.nv, dtype=torch.float64, device="cuda")
+        g.init_w(dev(u0), w0)
+        assert rel2(host(w0), ref) < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [(ok.OK_FP64, 1e-10), (ok.OK_MIXED, 1e-8)])
+def test_timesteps_small_2d(precision, tol):
+    """The 2D 32x32 workload (eps 0.04, sigma 100, m 0, theta 1, dt 1e-4): 5 steps."""
+    wl = oi.SMALL_2D
+    sysm = System(Mesh(wl.dim, wl.n), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
+    u0 = oi.initial_u(wl)
+    w0 = sysm.initial_w(u0)
+    opts = Options(linear="direct", newton_atol=wl.newton_atol, newton_extra=1)
+    with ok.Grid(wl.dim, wl.n, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, restart=wl.restart,
+                 gmres_rtol=wl.gmres_rtol, newton_atol=wl.newton_atol, newton_extra=1,
+                 precision=precision) as g:
+        u, w = dev(u0), dev(w0)
+        ur, wr = u0, w0
+        for step in range(wl.steps):
+            ur, wr, info = timestep(sysm, ur, wr, opts)
+            gi = g.timestep(u, w)
+            assert gi.converged
+            assert rel2(host(u), ur) < tol, step
+            assert rel2(host(w), wr) < tol, step
+
+
+@pytest.mark.parametrize("precision,tol", [(ok.OK_FP64, 1e-10), (ok.OK_MIXED, 1e-8)])
+def test_timesteps_small_3d(precision, tol):
+    """The 3D Kuhn workload's parameters (eps 0.03, sigma 100, m -0.2, theta 1) on 8^3."""
+    wl = oi.scaled(oi.CUBE_128, 8, dt=5e-4)
+    sysm = System(Mesh(3, 8), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
+    u0 = oi.initial_u(wl)
+    w0 = sysm.initial_w(u0)
+    opts = Options(linear="direct", newton_atol=1e-13, newton_extra=1)
+    with ok.Grid(3, 8, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, gmres_rtol=1e-10, newton_atol=1e-13,
+                 newton_extra=1, precision=precision) as g:
+        u, w = dev(u0), dev(w0)
+        ur, wr = u0, w0
+        for step in range(3):
+            ur, wr, _ = timestep(sysm, ur, wr, opts)
+            g.timestep(u, w)
+            assert rel2(host(u), ur) < tol and rel2(host(w), wr) < tol, step
+
+
+def test_solve_linear_meets_tolerance():
+    sysm, p, rng = make(2, 40, seed=4, dt=1e-4)
+    nv = sysm.mesh.nv
+    u = rng.uniform(-1, 1, nv)
+    f = rng.standard_normal(2 * nv)
+    J = sysm.jacobian(u)
+    with ok.Grid(2, 40, **p, gmres_rtol=1e-11, restart=8) as g:   # short restart: several cycles
+        x = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        info = g.solve_linear(dev(u), dev(f), x)
+        r = f - J @ host(x)
+        assert np.linalg.norm(r) <= 1.01e-11 * np.linalg.norm(f)
+        assert info.rel_resid <= 1e-11 and info.gmres_its > 8
+
+
+def test_graphs_and_streams_are_bitwise_identical():
+    wl = oi.SMALL_2D
+    u0 = oi.initial_u(wl)
+    sysm = System(Mesh(2, 32), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
+    w0 = sysm.initial_w(u0)
+    out = []
+    for graphs in (0, 1, 1):
+        with ok.Grid(2, 32, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, use_graphs=graphs) as g:
+            u, w = dev(u0), dev(w0)
+            for _ in range(2):
+                g.timestep(u, w)
+            out.append((host(u), host(w)))
+    for a in out[1:]:
+        assert np.array_equal(a[0], out[0][0]) and np.array_equal(a[1], out[0][1])
+
+
+def test_host_and_device_arrays_agree():
+    wl = oi.SMALL_2D
+    u0 = oi.initial_u(wl)
+    sysm = System(Mesh(2, 32), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
+    w0 = sysm.initial_w(u0)
+    with ok.Grid(2, 32, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt) as g:
+        uh, wh = u0.copy(), w0.copy()
+        g.timestep(uh, wh)
+        ud, wd = dev(u0), dev(w0)
+        g.timestep(ud, wd)
+        assert np.array_equal(uh, host(ud)) and np.array_equal(wh, host(wd))
+
+
+def test_nonfinite_input_is_reported():
+    with ok.Grid(2, 16, **P_DEFAULT) as g:
+        u = torch.zeros(g.nv, dtype=torch.float64, device="cuda")
+        w = torch.zeros(g.nv, dtype=torch.float64, device="cuda")
+        u[5] = float("nan")
+        with pytest.raises(ok.OkError) as e:
+            g.timestep(u, w)
+        assert e.value.status == ok.OK_ERR_NONFINITE
+        u[5] = 0.0                                   # the handle stays usable
+        g.timestep(u, w)
+
+
+def test_iteration_cap_reports_not_converged():
+    with ok.Grid(2, 16, **P_DEFAULT, max_gmres=1, gmres_rtol=1e-12) as g:
+        rng = np.random.default_rng(0)
+        u = dev(rng.uniform(-1, 1, g.nv))
+        w = dev(rng.uniform(-1, 1, g.nv))
+        info = g.timestep(u, w, check=False)
+        st = ok.load().ok_timestep(g.handle, u.data_ptr(), w.data_ptr(), None, None)
+        assert st == ok.OK_ERR_NOT_CONVERGED
+        assert not info.converged or info.newton_its >= 1
+
+
+def test_batch_runs_each_request():
+    wl = oi.SMALL_2D
+    u0 = oi.initial_u(wl)
+    sysm = System(Mesh(2, 32), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
+    w0 = sysm.initial_w(u0)
+    with ok.Grid(2, 32, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt) as g1, \
+            ok.Grid(3, 4, 0.05, 50.0, 0.0, 1.0, 1e-3) as g2:
+        a_u, a_w = dev(u0), dev(w0)
+        b_u = dev(0.01 * np.random.default_rng(1).uniform(-1, 1, g2.nv))
+        b_w = torch.zeros(g2.nv, dtype=torch.float64, device="cuda")
+        ref_u, ref_w = dev(u0), dev(w0)
+        for _ in range(2):
+            g1.timestep(ref_u, ref_w)
+        st, reqs, info = ok.ok_solve_batch([(g1, a_u, a_w, 2), (g2, b_u, b_w, 3)])
+        assert st == ok.OK_SUCCESS and info.completed == 2
+        assert torch.equal(a_u, ref_u) and torch.equal(a_w, ref_w)
+        assert reqs[1].newton_its >= 3
