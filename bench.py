@@ -1,0 +1,441 @@
+#!/usr/bin/env python3
+"""Benchmark of the Ohta--Kawasaki Newton-step solver on one GB300.
+
+Metric: FGMRES DoF x iterations per second (DoF = 2 N_v, the u and w nodal
+values), mixed precision (float32 preconditioner under float64 FGMRES) as the
+headline and float64 beside it, at FGMRES relative tolerance 1e-8, with
+p50/p99 latency of the timesteps and of the Newton linear solves.
+
+Workload (default): the unit square cut into 1024 x 1024 squares, each split
+into two P1 triangles (1,050,625 vertices, 2,101,250 DoF); eps 0.02,
+sigma 200, m 0.1, theta 0.5, dt 2e-5; u0 = m + 0.05 N(0,1) (seeded); FGMRES(30)
+to 1e-8; 9 multigrid levels.  A "step" is one theta-method timestep (Newton
+to its stop test, every Newton step one preconditioned FGMRES solve).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ok|reference]
+Under torchrun each rank runs an independent replica (the method has no
+exchange step on one grid); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import ok_inputs as oi  # noqa: E402
+
+METRIC = "GMRES DoF*iter/s, mixed vs FP64 @1e-8 rel. resid; p50/p99 solve latency"
+UNIT = "DoF*iter/s"
+FLUSH_BYTES = 512 << 20          # > 129 MB L2
+FP64_PEAK_TFLOPS = 1.259         # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ok", "reference"], default="ok")
+    ap.add_argument("--workload", default="2d_n1024", choices=sorted(oi.WORKLOADS))
+    ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-out", default=None, help="write per-kernel samples as JSON")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def reduce_across(values: dict, op: str):
+    """max/sum of float scalars over ranks (identity when not distributed)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return dict(values)
+    import torch
+    keys = sorted(values)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(values[k]) for k in keys], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return {k: float(v) for k, v in zip(keys, t.cpu().tolist())}
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes / flops per launch of the sampled kernel classes
+# ---------------------------------------------------------------------------
+def kernel_model(tag, wl, precision):
+    """(bytes, flops, bound) per launch from the kernel contracts.
+
+    apply_j: reads z (2 fields, float64 or float32 Z slot), the C coefficients
+             (1 + NPOS float64 per vertex), writes y (2 float64); flops:
+             M z1, K z2, M z2, C z1 (NOFF, 2d+1, NOFF, NOFF FMAs) + 3 per vertex.
+    mg_smooth_l0: one Chebyshev step on the finest level: reads d, x, r,
+             writes x, r, d' (6 values of the preconditioner type); NOFF FMAs + 4.
+    cheb_mass_step: the same on M.
+    """
+    nv = wl.n_vertices
+    d = wl.dim
+    noff = 7 if d == 2 else 15
+    npos = 3 if d == 2 else 7
+    nax = 2 * d + 1
+    bz = 4 if precision == "mixed" else 8
+    bp = 4 if precision == "mixed" else 8
+    if tag == "apply_j":
+        by = nv * (2 * bz + 8 * (npos + 1) + 16)
+        fl = nv * 2 * (noff + nax + noff + noff + 3)
+        return by, fl, "alu"
+    if tag in ("mg_smooth_l0", "cheb_mass_step"):
+        return nv * 6 * bp, nv * 2 * (noff + 4), "hbm"
+    return None, None, None
+
+
+def launches_per_iteration(tag, opts):
+    if tag == "apply_j":
+        return 1
+    if tag == "mg_smooth_l0":
+        k = 2 if opts.get("k_R", 1) == 1 else 4
+        return k * opts["n_V"] * ((opts["smooth_pre"] - 1) + (opts["smooth_post"] - 1))
+    if tag == "cheb_mass_step":
+        return (opts["q_A"] - 1) * (1 if opts.get("k_R", 1) == 1 else 2)
+    return None
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1603_04570_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(tag, workload, precision):
+    """DRAM bytes per launch from a committed ncu summary, if it matches these sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 5 and not line.startswith("#"):
+            t, wk, pr, by, hs = parts
+            if t == tag and wk == workload and pr == precision and hs == want:
+                return float(by)
+    return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+def grid_opts(wl, precision):
+    atol, rtol = wl.newton_tols
+    return dict(restart=wl.restart, gmres_rtol=wl.gmres_rtol, newton_atol=atol, newton_rtol=rtol,
+                precision=precision, q_A=10, n_V=5, k_R=1, smooth_pre=2, smooth_post=2, use_graphs=1)
+
+
+def run_precision(ok, torch, wl, precision_name, steps, warmup, rank, profile, flush):
+    precision = ok.OK_MIXED if precision_name == "mixed" else ok.OK_FP64
+    opts = grid_opts(wl, precision)
+    g = ok.Grid(wl.dim, wl.n, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, **opts)
+    wl_r = dataclasses.replace(wl, seed=wl.seed + rank)
+    u = torch.from_numpy(oi.initial_u(wl_r)).cuda()
+    w = torch.empty_like(u)
+    g.init_w(u, w)
+    if profile:
+        ok.ok_profile(g.handle, True)
+    for _ in range(warmup):
+        g.timestep(u, w)
+    if profile:
+        ok.ok_profile(g.handle, True)          # clear warm-up samples (graphs already captured)
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    infos = []
+    torch.cuda.synchronize()
+    barrier()
+    l0 = ok.ok_launch_count()
+    t_wall = time.perf_counter()
+    for k in range(steps):
+        flush.zero_()                          # L2 flushed before every timed step
+        evs[k][0].record(stream)
+        infos.append(g.timestep(u, w))
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = ok.ok_launch_count() - l0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    prof = ok.ok_profile_read(g.handle) if profile else {}
+    its = sum(i.gmres_its for i in infos)
+    newton = sum(i.newton_its for i in infos)
+    solve_lat = [i.solve_ms / max(i.newton_its, 1) for i in infos]
+    res = dict(g=g, u=u, w=w, step_ms=step_ms, its=its, newton=newton, infos=infos, launches=launches,
+               wall_s=t_wall, prof=prof, opts=opts, solve_lat=solve_lat)
+    return res
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q
+    lo, hi = math.floor(k), math.ceil(k)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def e2e_run(ok, torch, res, wl, steps, flush):
+    """Same metric through the C ABI with pinned host buffers (copies inside)."""
+    g = res["g"]
+    uh = torch.empty(g.nv, dtype=torch.float64, pin_memory=True)
+    wh = torch.empty(g.nv, dtype=torch.float64, pin_memory=True)
+    uh.copy_(res["u"])
+    wh.copy_(res["w"])
+    torch.cuda.synchronize()
+    its, total = 0, 0.0
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = g.timestep(uh.numpy(), wh.numpy())
+        total += time.perf_counter() - t0
+        its += info.gmres_its
+    nbytes = 2 * g.nv * 8
+    return {"value": 2 * g.nv * its / total, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "ms_per_step": 1e3 * total / steps,
+            "api": "ok_timestep with pinned host arrays"}
+
+
+def cpu_baseline(wl, iters=3):
+    """The oracle's preconditioned FGMRES on the same workload: first `iters`
+    iterations of the first Newton linear solve (plain numpy/scipy, 1 thread)."""
+    from oracle.fem import Mesh, Params, System
+    from oracle.solvers import Preconditioner, fgmres
+    sysm = System(Mesh(wl.dim, wl.n), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
+    u0 = oi.initial_u(wl)
+    w0 = sysm.initial_w(u0)
+    F = sysm.residual(u0, w0, u0, w0)
+    J = sysm.jacobian(u0)
+    P = Preconditioner(sysm, u0, mode="inexact", q_A=10, n_V=5, k_R=1)
+    t0 = time.perf_counter()
+    _, its, _ = fgmres(lambda z: J @ z, P.apply, -F, restart=wl.restart, rtol=wl.gmres_rtol, max_its=iters)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * sysm.mesh.nv * its / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {its} FGMRES iterations of the first Newton solve of {wl.name} "
+                      f"({2 * sysm.mesh.nv} DoF), scipy CSR operators, {dt:.1f} s",
+            "seconds": dt}
+
+
+def main_ok(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    import paper_1603_04570_gb300 as ok
+    ok.load()
+    wl = oi.WORKLOADS[args.workload]
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(local)
+    clocks.start()
+    mixed = run_precision(ok, torch, wl, "mixed", args.steps, args.warmup, rank, True, flush)
+    clk = clocks.stop()
+    fp64 = None if args.no_fp64 else run_precision(ok, torch, wl, "fp64", args.steps, args.warmup, rank, True,
+                                                   flush)
+    e2e = e2e_run(ok, torch, mixed, wl, args.steps, flush)
+    dof = 2 * wl.n_vertices
+    total_ms = sum(mixed["step_ms"])
+    agg = reduce_across({"ms": total_ms}, "max")
+    units = reduce_across({"u": dof * mixed["its"]}, "sum")["u"]
+    value = units / (agg["ms"] / 1e3)
+    # dominant sampled kernel: largest estimated share of the step
+    peaks, peak_kind = measured_peaks()
+    best = None
+    for tag, (n, tot) in mixed["prof"].items():
+        lpi = launches_per_iteration(tag, mixed["opts"])
+        if n == 0 or lpi is None:
+            continue
+        share = tot / n * lpi * mixed["its"]
+        if best is None or share > best[1]:
+            best = (tag, share, tot / n, n)
+    roof = None
+    if best:
+        tag, share, avg_ms, n = best
+        by, fl, bound = kernel_model(tag, wl, "mixed")
+        if bound == "hbm":
+            ach = by / (avg_ms * 1e-3) / 1e9
+            peak = peaks["hbm_gbs"]
+            unit = "GB/s"
+        else:
+            ach = fl / (avg_ms * 1e-3) / 1e12
+            peak = FP64_PEAK_TFLOPS
+            unit = "TFLOP/s"
+        tr = recorded_traffic(tag, wl.name, "mixed")
+        roof = {"kernel": tag, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "traffic": tr, "algorithmic_bytes_per_launch": by, "flops_per_launch": fl,
+                "avg_launch_ms": avg_ms, "samples": n, "share_of_timed_region": share / total_ms,
+                "peak_source": (f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})" if bound == "hbm" else
+                                "FP64 nominal: 152 SMs x 2 FMA/clk x 2.07 GHz")}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": agg["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32 (mixed)", "data": "synthetic",
+        "config": {"workload": wl.name, "dim": wl.dim, "n": wl.n, "vertices": wl.n_vertices, "dofs": dof,
+                   "eps": wl.eps, "sigma": wl.sigma, "m": wl.m, "theta": wl.theta, "dt": wl.dt,
+                   "restart": wl.restart, "gmres_rtol": wl.gmres_rtol, "mg_levels": mixed["g"].levels,
+                   "precision": "mixed (float32 preconditioner, float64 FGMRES/J/residual)",
+                   "l2": "flushed by a 512 MB write before every timed step", "parallelism": f"replicas x{world}"},
+        "gmres_its": mixed["its"], "newton_its": mixed["newton"],
+        "its_per_newton": mixed["its"] / max(mixed["newton"], 1),
+        "latency": {"step_p50_ms": pct(mixed["step_ms"], 0.5), "step_p99_ms": pct(mixed["step_ms"], 0.99),
+                    "newton_solve_p50_ms": pct(mixed["solve_lat"], 0.5),
+                    "newton_solve_p99_ms": pct(mixed["solve_lat"], 0.99)},
+        "roofline": roof, "e2e": e2e, "gpu_launches": mixed["launches"], "clocks": clk,
+        "kernel_samples": {k: {"samples": n, "avg_ms": (t / n if n else None)} for k, (n, t) in mixed["prof"].items()},
+    }
+    if fp64 is not None:
+        fms = sum(fp64["step_ms"])
+        du = float(torch.linalg.norm(mixed["u"] - fp64["u"]) / torch.linalg.norm(fp64["u"]))
+        dw = float(torch.linalg.norm(mixed["w"] - fp64["w"]) / torch.linalg.norm(fp64["w"]))
+        out["fp64"] = {"value": dof * fp64["its"] / (fms / 1e3), "ms_per_step": fms / args.steps,
+                       "gmres_its": fp64["its"], "newton_its": fp64["newton"],
+                       "step_p50_ms": pct(fp64["step_ms"], 0.5), "step_p99_ms": pct(fp64["step_ms"], 0.99),
+                       "kernel_samples": {k: {"samples": n, "avg_ms": (t / n if n else None)}
+                                          for k, (n, t) in fp64["prof"].items()}}
+        out["mixed_vs_fp64"] = {"speedup": out["value"] / out["fp64"]["value"], "rel_diff_u": du,
+                                "rel_diff_w": dw}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    if args.profile_out and rank == 0:
+        json.dump(out, open(args.profile_out, "w"), indent=1, default=str)
+    if rank == 0:
+        print(json.dumps(out, default=lambda o: None))
+    mixed["g"].close()
+    if fp64 is not None:
+        fp64["g"].close()
+
+
+def main_reference(args):
+    """The oracle (plain numpy/scipy, host cores) on the same workload and metric."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle.fem import Mesh, Params, System
+    from oracle.solvers import Preconditioner, fgmres
+    wl = oi.WORKLOADS[args.workload]
+    sysm = System(Mesh(wl.dim, wl.n), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
+    u0 = oi.initial_u(wl)
+    w0 = sysm.initial_w(u0)
+    F = sysm.residual(u0, w0, u0, w0)
+    J = sysm.jacobian(u0)
+    P = Preconditioner(sysm, u0, mode="inexact", q_A=10, n_V=5, k_R=1)
+    per_step = 2
+    run = lambda: fgmres(lambda z: J @ z, P.apply, -F, restart=wl.restart, rtol=wl.gmres_rtol, max_its=per_step)[1]
+    for _ in range(args.warmup):
+        run()
+    times, its = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        its += run()
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    dof = 2 * sysm.mesh.nv
+    value = dof * its / total
+    sample = (f"each step: {per_step} FGMRES iterations of the first Newton solve of {wl.name} "
+              f"({dof} DoF), oracle scipy CSR operators, 1 thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "dim": wl.dim, "n": wl.n, "dofs": dof, "restart": wl.restart,
+                   "gmres_rtol": wl.gmres_rtol},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ok(a)

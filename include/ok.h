@@ -90,7 +90,8 @@ typedef struct ok_opts {
   int smooth_post;    /* post-smoothing steps per level [2]                     */
   int precision;      /* OK_FP64 or OK_MIXED [OK_FP64]                          */
   int coarse_max;     /* halve the grid while n is even and > coarse_max [4]    */
-  int use_graphs;     /* capture preconditioner applications in CUDA graphs [1] */
+  int use_graphs;     /* capture each Arnoldi step in a CUDA graph [1]          */
+  int fuse_coarse;    /* run the coarse multigrid levels in one kernel [1]      */
   double gmres_rtol;  /* stop when ||f - J x|| <= gmres_rtol ||f|| [1e-10]      */
   double newton_atol; /* Newton stops when ||F||_2 <= max(atol, rtol ||F_0||)   */
   double newton_rtol; /*   [atol 1e-10, rtol 0]                                 */
@@ -191,6 +192,27 @@ typedef struct ok_batch_info {
 /* Run every request to completion.  Requests on distinct handles are
  * independent; each gets its own stream, derived from `stream`'s device. */
 int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream stream);
+
+/* Sampled kernel timing (no counterpart in the paper: measurement support).
+ * ok_profile(g, 1) clears the counters and, from the next Arnoldi step on,
+ * records one CUDA-event pair per kernel class per step on the handle's
+ * stream: "precond" (one whole preconditioner application), "apply_j" (the
+ * Jacobian kernel), "cgs2" (the four orthogonalisation kernels),
+ * "mg_smooth_l0" (the first finest-level Chebyshev smoothing kernel) and
+ * "cheb_mass_step" (the first Chebyshev step on M).  ok_profile(g, 0) stops.
+ * Toggling re-captures the handle's CUDA graphs.  ok_profile_read copies up
+ * to `max` records into `out` (host) and the number written into *count. */
+typedef struct ok_kernel_stat {
+  char name[32];
+  long long samples;   /* timed launches                  */
+  double total_ms;     /* summed duration of those launches */
+} ok_kernel_stat;
+int ok_profile(ok_grid* g, int enable);
+int ok_profile_read(const ok_grid* g, ok_kernel_stat* out, int max, int* count);
+
+/* Number of this library's kernels launched by the process so far (graph
+ * replays count every kernel node). */
+long long ok_launch_count(void);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* ok_last_error(void);

@@ -89,6 +89,19 @@ class Workload:
     def dofs(self) -> int:
         return 2 * self.n_vertices
 
+    @property
+    def newton_tols(self):
+        """(atol, rtol) of the Newton stop test ||F||_2 <= max(atol, rtol ||F_0||_2).
+
+        The 32x32 case states 1e-10 absolute.  The others scale that absolute
+        level by h^d sqrt(N_v) (the size of a weak-form vector of O(1)
+        nodal values) and add a relative floor of 1e-12.
+        """
+        if self.name == "2d_n32":
+            return self.newton_atol, 0.0
+        h = 1.0 / self.n
+        return self.newton_atol * h ** self.dim * math.sqrt(self.n_vertices), 1e-12
+
 
 def initial_u(w: Workload) -> np.ndarray:
     """Nodal u0 in compact lexicographic order (x fastest)."""

@@ -30,7 +30,7 @@ class Params(Structure):
 class Opts(Structure):
     _fields_ = [("restart", c_int), ("max_gmres", c_int), ("max_newton", c_int), ("newton_extra", c_int),
                 ("q_A", c_int), ("n_V", c_int), ("k_R", c_int), ("smooth_pre", c_int), ("smooth_post", c_int),
-                ("precision", c_int), ("coarse_max", c_int), ("use_graphs", c_int),
+                ("precision", c_int), ("coarse_max", c_int), ("use_graphs", c_int), ("fuse_coarse", c_int),
                 ("gmres_rtol", c_double), ("newton_atol", c_double), ("newton_rtol", c_double),
                 ("smooth_lo_frac", c_double)]
 
@@ -51,6 +51,10 @@ class Request(Structure):
 
 class BatchInfo(Structure):
     _fields_ = [("completed", c_int), ("failed", c_int), ("seconds", c_double)]
+
+
+class KernelStat(Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("samples", c_longlong), ("total_ms", c_double)]
 
 
 class OkError(RuntimeError):
@@ -91,6 +95,9 @@ def load(build: bool = True):
         "ok_newton_step": (c_int, [P, P, P, P, P, POINTER(StepInfo), P]),
         "ok_timestep": (c_int, [P, P, P, POINTER(StepInfo), P]),
         "ok_solve_batch": (c_int, [POINTER(Request), c_int, POINTER(BatchInfo), P]),
+        "ok_profile": (c_int, [P, c_int]),
+        "ok_profile_read": (c_int, [P, POINTER(KernelStat), c_int, POINTER(c_int)]),
+        "ok_launch_count": (c_longlong, []),
         "ok_last_error": (c_char_p, []),
         "ok_version": (c_char_p, []),
     }
@@ -214,6 +221,22 @@ def ok_timestep(h, nv, u, w, stream=None, check=True):
     if check:
         _check(st)
     return info
+
+
+def ok_profile(h, enable: bool):
+    _check(load().ok_profile(h, 1 if enable else 0))
+
+
+def ok_profile_read(h):
+    """{kernel class: (samples, total_ms)} of the handle's sampled timings."""
+    arr = (KernelStat * 16)()
+    n = c_int()
+    _check(load().ok_profile_read(h, arr, 16, byref(n)))
+    return {arr[i].name.decode(): (arr[i].samples, arr[i].total_ms) for i in range(n.value)}
+
+
+def ok_launch_count() -> int:
+    return load().ok_launch_count()
 
 
 def ok_solve_batch(requests, stream=None):

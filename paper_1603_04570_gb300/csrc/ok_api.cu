@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -85,6 +87,64 @@ void cheb_coefs(double lo, double hi, int steps, std::vector<double>& c1, std::v
 
 }  // namespace
 
+std::atomic<long long> okg::g_launch_count{0};
+
+// ---------------------------------------------------------------------------
+// sampled kernel timing: one CUDA-event pair per kernel class per Arnoldi
+// step, recorded on the handle's stream (inside the captured graph when
+// graphs are on) and read after the step's host synchronisation.
+// ---------------------------------------------------------------------------
+enum ProfTag { PT_PRECOND = 0, PT_APPLYJ, PT_CGS2, PT_SMOOTH0, PT_CHEBM, PT_COUNT };
+static const char* const kProfNames[PT_COUNT] = {"precond", "apply_j", "cgs2", "mg_smooth_l0",
+                                                 "cheb_mass_step"};
+using TagSet = std::array<bool, PT_COUNT>;
+
+struct Profiler {
+  bool on = false;
+  cudaEvent_t ev[PT_COUNT][2] = {};
+  TagSet began{}, ended{};
+  long long samples[PT_COUNT] = {};
+  double total_ms[PT_COUNT] = {};
+  void create() {
+    for (int t = 0; t < PT_COUNT; ++t)
+      for (int k = 0; k < 2; ++k)
+        if (!ev[t][k]) CK(cudaEventCreate(&ev[t][k]));
+  }
+  void destroy() {
+    for (int t = 0; t < PT_COUNT; ++t)
+      for (int k = 0; k < 2; ++k)
+        if (ev[t][k]) cudaEventDestroy(ev[t][k]), ev[t][k] = nullptr;
+  }
+  void reset_step() {
+    began.fill(false);
+    ended.fill(false);
+  }
+  void begin(int t, cudaStream_t s) {
+    if (!on || t < 0 || began[t]) return;
+    // "external" records stay real event records (timable) inside stream capture
+    CK(cudaEventRecordWithFlags(ev[t][0], s, cudaEventRecordExternal));
+    began[t] = true;
+  }
+  void end(int t, cudaStream_t s) {
+    if (!on || t < 0 || !began[t] || ended[t]) return;
+    CK(cudaEventRecordWithFlags(ev[t][1], s, cudaEventRecordExternal));
+    ended[t] = true;
+  }
+  // after the stream was synchronised; a sample that cannot be read is skipped
+  void collect(const TagSet& had) {
+    for (int t = 0; t < PT_COUNT; ++t)
+      if (had[t]) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[t][0], ev[t][1]) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        samples[t] += 1;
+        total_ms[t] += ms;
+      }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // device memory owned by a handle
 // ---------------------------------------------------------------------------
@@ -134,17 +194,24 @@ template <typename T> struct Prec {
   double thM = 1, thS = 1;
   double inv_a11 = 1, dth = 0;
   int q_A = 10, n_V = 5, k_R = 1, nu_pre = 2, nu_post = 2;
+  Profiler* prof = nullptr;
+  bool fused = false;          // coarse levels Lc..L run as one shared-memory kernel
+  int Lc = 0;
+  CoarseArgs<T> ca{};
+  size_t csmem = 0;
 
   template <typename TB, typename TO>
   void cheb(const Geom& g, const T* W, const T* dinv, const TB* b, bool x_zero, T* x, T* r, T* d0, T* d1,
             int steps, double th, const std::vector<double>& c1, const std::vector<double>& c2, TO* out,
-            T oscale, bool want_r, cudaStream_t s) {
+            T oscale, bool want_r, cudaStream_t s, int tag = -1) {
     if (x_zero) launch_cheb_init<T, TB>(dim, g, dinv, b, (T)1, r, d0, (T)(1.0 / th), s);
     else launch_resid_init<T>(dim, g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s);
     T* d[2] = {d0, d1};
     int cur = 0;
     for (int k = 0; k + 1 < steps; ++k) {
+      if (k == 0 && prof) prof->begin(tag, s);
       launch_cheb_step<T>(dim, g, W, dinv, x, r, d[cur], d[1 - cur], (T)c1[k], (T)c2[k], x_zero && k == 0, s);
+      if (k == 0 && prof) prof->end(tag, s);
       cur ^= 1;
     }
     launch_cheb_last<T, TO>(dim, g, W, x, want_r ? r : nullptr, d[cur], x_zero && steps == 1, out, oscale, s);
@@ -154,13 +221,18 @@ template <typename T> struct Prec {
   void vcycle(int l, bool x_zero, TO* out, cudaStream_t s) {
     Level<T>& L = lv[l];
     const bool coarsest = (l + 1 == (int)lv.size());
+    if (fused && l == Lc) {                 // levels Lc..L in one thread block
+      launch_coarse_vcycle<T>(dim, ca, csmem, L.b, x_zero ? (const T*)nullptr : L.x, L.x, s);
+      if (out) launch_axpby<T, TO>(L.g.nv, 1.0, L.x, 0.0, out, s);
+      return;
+    }
     if (coarsest) {
       launch_coarse_solve<T>(nc, coarse_inv, L.b, L.x, s);
       if (out) launch_axpby<T, TO>(L.g.nv, 1.0, L.x, 0.0, out, s);
       return;
     }
     cheb<T, T>(L.g, L.WS, L.dinvS, L.b, x_zero, L.x, L.r, L.d0, L.d1, nu_pre, thS, cS1, cS2, (T*)nullptr,
-               (T)1, true, s);
+               (T)1, true, s, l == 0 ? PT_SMOOTH0 : -1);
     Level<T>& C = lv[l + 1];
     launch_restrict<T>(dim, L.g, C.g, L.r, C.b, s);
     vcycle<T>(l + 1, true, (T*)nullptr, s);
@@ -177,7 +249,8 @@ template <typename T> struct Prec {
   // A~^{-1} b into cx (unscaled Chebyshev on M; A~^{-1} b = cx / a11)
   template <typename TB, typename TO>
   void a_inv(const TB* b, TO* out, cudaStream_t s) {
-    cheb<TB, TO>(lv[0].g, WM, dinvM, b, true, cx, cr, cd0, cd1, q_A, thM, cM1, cM2, out, (T)inv_a11, false, s);
+    cheb<TB, TO>(lv[0].g, WM, dinvM, b, true, cx, cr, cd0, cd1, q_A, thM, cM1, cM2, out, (T)inv_a11, false, s,
+                 PT_CHEBM);
   }
 
   // z = P^{-1} v  (v: 2 nv doubles; z: 2 nv of TZ)
@@ -243,6 +316,9 @@ struct ok_grid {
   Prec<double> pd;
   Prec<float> pf;
   std::vector<cudaGraphExec_t> graphs;   // one Arnoldi step per j
+  std::vector<long long> graph_kernels;  // kernels captured in each graph
+  std::vector<TagSet> graph_tags;        // profiled kernel classes in each graph
+  Profiler prof;
   double cheb_init_th = 1;
   std::vector<double> cI1, cI2;          // 60-step mass Chebyshev for w0
 };
@@ -336,6 +412,43 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
     }
     CK(cudaDeviceSynchronize());
   }
+  // fused coarse part: the longest suffix of levels whose five vectors fit in
+  // shared memory (at most COARSE_MAXLEV levels); worth it from two levels on
+  const int nl = (int)P.lv.size();
+  const size_t budget = 200 * 1024;
+  size_t tot = 0;
+  int Lc = nl;
+  for (int l = nl - 1; l >= 0; --l) {
+    const size_t need = 5 * (size_t)P.lv[l].g.nv * sizeof(T);
+    if (tot + need > budget || nl - l > COARSE_MAXLEV) break;
+    tot += need;
+    Lc = l;
+  }
+  if (G->o.fuse_coarse && nl - Lc >= 2) {
+    CoarseArgs<T>& ca = P.ca;
+    ca.nlev = nl - Lc;
+    long long off = 0;
+    for (int i = 0; i < ca.nlev; ++i) {
+      const Level<T>& L = P.lv[Lc + i];
+      ca.g[i] = L.g;
+      ca.W[i] = L.WS;
+      ca.dinv[i] = L.dinvS;
+      ca.off[i] = off;
+      off += 5 * L.g.nv;
+    }
+    ca.Ainv = P.coarse_inv;
+    ca.inv_th = (T)(1.0 / P.thS);
+    for (int k = 0; k < 16; ++k) {
+      ca.c1[k] = k < (int)P.cS1.size() ? (T)P.cS1[k] : (T)0;
+      ca.c2[k] = k < (int)P.cS2.size() ? (T)P.cS2[k] : (T)0;
+    }
+    ca.nu_pre = P.nu_pre;
+    ca.nu_post = P.nu_post;
+    P.csmem = (size_t)off * sizeof(T);
+    CK(prepare_coarse_vcycle<T>(dim, P.csmem));
+    P.fused = true;
+    P.Lc = Lc;
+  }
 }
 
 void validate(int dim, int n, const ok_params* p, const ok_opts* o) {
@@ -421,12 +534,19 @@ void arnoldi(ok_grid* G, TZ* Z, int j, cudaStream_t s) {
   const double* vj = G->V + (long long)j * N;
   double* w = G->V + (long long)(j + 1) * N;
   TZ* zj = Z + (long long)j * N;
+  Profiler& pr = G->prof;
+  pr.begin(PT_PRECOND, s);
   precond<TZ>(G, vj, zj, s);
+  pr.end(PT_PRECOND, s);
+  pr.begin(PT_APPLYJ, s);
   launch_apply_j<TZ>(G->dim, G->g0, G->refWM, G->refWK, G->jc, G->coef, zj, w, nullptr, s);
+  pr.end(PT_APPLYJ, s);
+  pr.begin(PT_CGS2, s);
   launch_multidot(G->V, N, j + 1, w, N, G->rs, ks_h1_ptr(G->ks), s);
   launch_update_multidot(G->V, N, j + 1, ks_h1_ptr(G->ks), w, N, G->rs, ks_h2_ptr(G->ks), s);
   launch_update_norm_givens(G->V, N, j + 1, w, N, G->rs, G->ks, j, s);
   launch_scale_by(w, N, ks_eta_ptr(G->ks) + 1, s);   // inv_eta follows eta
+  pr.end(PT_CGS2, s);
 }
 
 // Right-preconditioned restarted FGMRES for J x = f (all device pointers).
@@ -457,25 +577,37 @@ void fgmres(ok_grid* G, TZ* Z, const double* f, double* x, int& its, double& rel
     CKL();
     int jused = 0;
     for (int j = 0; j < m; ++j) {
+      TagSet tags;
       if (graphs) {
         if (!G->graphs[j]) {
           cudaGraph_t gr;
+          G->prof.reset_step();
+          const long long c0 = g_launch_count.load();
           CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
           arnoldi<TZ>(G, Z, j, s);
           cudaError_t e = cudaStreamEndCapture(s, &gr);
           ck(e, "graph capture of an Arnoldi step");
+          const long long c1 = g_launch_count.load();
+          g_launch_count.fetch_sub(c1 - c0);          // counted when the graph runs
+          G->graph_kernels[j] = c1 - c0;
+          G->graph_tags[j] = G->prof.ended;
           CK(cudaGraphInstantiate(&G->graphs[j], gr, 0));
           cudaGraphDestroy(gr);
         }
         CK(cudaGraphLaunch(G->graphs[j], s));
+        g_launch_count.fetch_add(G->graph_kernels[j]);
+        tags = G->graph_tags[j];
       } else {
+        G->prof.reset_step();
         arnoldi<TZ>(G, Z, j, s);
         CKL();
+        tags = G->prof.ended;
       }
       ++its;
       jused = j + 1;
       CK(cudaMemcpyAsync(G->hpin, ks_eta_ptr(G->ks), 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      if (G->prof.on) G->prof.collect(tags);
       const double eta = G->hpin[0], est = G->hpin[2];
       if (!std::isfinite(est)) fail(OK_ERR_NONFINITE, "non-finite value in FGMRES");
       if (est <= rtol * fnorm || its >= G->o.max_gmres || eta == 0.0) break;
@@ -553,6 +685,7 @@ void ok_default_opts(ok_opts* o) {
   o->precision = OK_FP64;
   o->coarse_max = 4;
   o->use_graphs = 1;
+  o->fuse_coarse = 1;
   o->gmres_rtol = 1e-10;
   o->newton_atol = 1e-10;
   o->newton_rtol = 0.0;
@@ -662,6 +795,10 @@ int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid
       G->pd.coef = G->coef;
     }
     G->graphs.assign(od.restart, nullptr);
+    G->graph_kernels.assign(od.restart, 0);
+    G->graph_tags.assign(od.restart, TagSet{});
+    G->pd.prof = &G->prof;
+    G->pf.prof = &G->prof;
     krylov_blocks();
     CK(cudaDeviceSynchronize());
   });
@@ -678,6 +815,7 @@ int ok_grid_destroy(ok_grid* G) {
   if (G->s) cudaStreamSynchronize(G->s);
   for (auto& ge : G->graphs)
     if (ge) cudaGraphExecDestroy(ge);
+  G->prof.destroy();
   G->arena.release();
   if (G->hpin) cudaFreeHost(G->hpin);
   if (G->ev_in) cudaEventDestroy(G->ev_in);
@@ -893,6 +1031,44 @@ int ok_timestep(ok_grid* G, double* u, double* w, ok_step_info* info, ok_stream 
   if (info) *info = loc;
   return st;
 }
+
+int ok_profile(ok_grid* G, int enable) {
+  if (!G) {
+    g_last_error = "NULL handle";
+    return OK_ERR_INVALID_ARG;
+  }
+  return guarded([&] {
+    CK(cudaStreamSynchronize(G->s));
+    const bool on = enable != 0;
+    if (on != G->prof.on) {            // graphs are re-captured with/without the event nodes
+      for (auto& ge : G->graphs)
+        if (ge) cudaGraphExecDestroy(ge), ge = nullptr;
+    }
+    if (on) G->prof.create();
+    G->prof.on = on;
+    for (int t = 0; t < PT_COUNT; ++t) {
+      if (on) G->prof.samples[t] = 0, G->prof.total_ms[t] = 0.0;
+    }
+  });
+}
+
+int ok_profile_read(const ok_grid* G, ok_kernel_stat* out, int max, int* count) {
+  if (!G || (max > 0 && !out)) {
+    g_last_error = "NULL argument";
+    return OK_ERR_INVALID_ARG;
+  }
+  int n = 0;
+  for (int t = 0; t < PT_COUNT && n < max; ++t, ++n) {
+    std::memset(&out[n], 0, sizeof(ok_kernel_stat));
+    std::strncpy(out[n].name, kProfNames[t], sizeof(out[n].name) - 1);
+    out[n].samples = G->prof.samples[t];
+    out[n].total_ms = G->prof.total_ms[t];
+  }
+  if (count) *count = n;
+  return OK_SUCCESS;
+}
+
+long long ok_launch_count(void) { return g_launch_count.load(); }
 
 int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream stream) {
   if (count < 0 || (count > 0 && !reqs)) {

@@ -278,30 +278,30 @@ void launch_residual(int dim, const Geom& g, const double* WM, const double* WK,
                      const double* un, const double* wn, const double* u, const double* w, double* f,
                      cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) k_residual<2><<<grd, 128, 0, s>>>(g, WM, WK, rc, un, wn, u, w, f);
-  else k_residual<3><<<grd, 128, 0, s>>>(g, WM, WK, rc, un, wn, u, w, f);
+  if (dim == 2) count_launch(), k_residual<2><<<grd, 128, 0, s>>>(g, WM, WK, rc, un, wn, u, w, f);
+  else count_launch(), k_residual<3><<<grd, 128, 0, s>>>(g, WM, WK, rc, un, wn, u, w, f);
 }
 
 void launch_initw_rhs(int dim, const Geom& g, const double* WK, const ResidualCoefs& rc, const double* u,
                       double* out, cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) k_initw_rhs<2><<<grd, 128, 0, s>>>(g, WK, rc, u, out);
-  else k_initw_rhs<3><<<grd, 128, 0, s>>>(g, WK, rc, u, out);
+  if (dim == 2) count_launch(), k_initw_rhs<2><<<grd, 128, 0, s>>>(g, WK, rc, u, out);
+  else count_launch(), k_initw_rhs<3><<<grd, 128, 0, s>>>(g, WK, rc, u, out);
 }
 
 void launch_assemble_c(int dim, const Geom& g, const ResidualCoefs& rc, const double* u, double* coef,
                        float* coef32, cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) k_assemble_c<2><<<grd, 128, 0, s>>>(g, rc, u, coef, coef32);
-  else k_assemble_c<3><<<grd, 128, 0, s>>>(g, rc, u, coef, coef32);
+  if (dim == 2) count_launch(), k_assemble_c<2><<<grd, 128, 0, s>>>(g, rc, u, coef, coef32);
+  else count_launch(), k_assemble_c<3><<<grd, 128, 0, s>>>(g, rc, u, coef, coef32);
 }
 
 template <typename TZ>
 void launch_apply_j(int dim, const Geom& g, const double* WM, const double* WK, const JCoefs& jc,
                     const double* coef, const TZ* z, double* y, const double* y0, cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) k_apply_j<2, TZ><<<grd, 128, 0, s>>>(g, WM, WK, jc, coef, z, y, y0);
-  else k_apply_j<3, TZ><<<grd, 128, 0, s>>>(g, WM, WK, jc, coef, z, y, y0);
+  if (dim == 2) count_launch(), k_apply_j<2, TZ><<<grd, 128, 0, s>>>(g, WM, WK, jc, coef, z, y, y0);
+  else count_launch(), k_apply_j<3, TZ><<<grd, 128, 0, s>>>(g, WM, WK, jc, coef, z, y, y0);
 }
 template void launch_apply_j<double>(int, const Geom&, const double*, const double*, const JCoefs&,
                                      const double*, const double*, double*, const double*, cudaStream_t);
@@ -312,8 +312,8 @@ template <typename T, typename TV>
 void launch_cstep(int dim, const Geom& g, const T* coef, const TV* v2, T vscale, const T* y1, T yscale, T* t,
                   cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) k_cstep<2, T, TV><<<grd, 128, 0, s>>>(g, coef, v2, vscale, y1, yscale, t);
-  else k_cstep<3, T, TV><<<grd, 128, 0, s>>>(g, coef, v2, vscale, y1, yscale, t);
+  if (dim == 2) count_launch(), k_cstep<2, T, TV><<<grd, 128, 0, s>>>(g, coef, v2, vscale, y1, yscale, t);
+  else count_launch(), k_cstep<3, T, TV><<<grd, 128, 0, s>>>(g, coef, v2, vscale, y1, yscale, t);
 }
 template void launch_cstep<double, double>(int, const Geom&, const double*, const double*, double, const double*,
                                            double, double*, cudaStream_t);
@@ -324,8 +324,8 @@ template <typename T>
 void launch_schur_resid(int dim, const Geom& g, const T* WM, T hd, const T* coef, const T* t, const T* y,
                         const T* a, T ascale, T* out, cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) k_schur_resid<2, T><<<grd, 128, 0, s>>>(g, WM, hd, coef, t, y, a, ascale, out);
-  else k_schur_resid<3, T><<<grd, 128, 0, s>>>(g, WM, hd, coef, t, y, a, ascale, out);
+  if (dim == 2) count_launch(), k_schur_resid<2, T><<<grd, 128, 0, s>>>(g, WM, hd, coef, t, y, a, ascale, out);
+  else count_launch(), k_schur_resid<3, T><<<grd, 128, 0, s>>>(g, WM, hd, coef, t, y, a, ascale, out);
 }
 template void launch_schur_resid<double>(int, const Geom&, const double*, double, const double*, const double*,
                                          const double*, const double*, double, double*, cudaStream_t);

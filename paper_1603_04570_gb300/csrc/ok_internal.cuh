@@ -22,7 +22,14 @@
 #include <type_traits>
 #include <utility>
 
+#include <atomic>
+
 namespace okg {
+
+// Kernels launched by this process (host-side count; a launch inside stream
+// capture is counted by the capturing code per graph replay instead).
+extern std::atomic<long long> g_launch_count;
+inline void count_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // compile-time topology
@@ -122,6 +129,7 @@ __device__ __forceinline__ int axis_class(int i, int n) { return i == 0 ? 0 : (i
 // Per-vertex position data: index, class per axis and the linear class.
 template <int D> struct Vtx {
   long long idx;
+  int p[3];      // grid coordinates (i, j, k)
   int c[3];
   int cls;
 };
@@ -133,6 +141,9 @@ __device__ __forceinline__ bool vertex_of_thread(const Geom& g, Vtx<D>& v) {
   if (i >= g.n1) return false;
   int j = blockIdx.y;
   int k = D == 3 ? blockIdx.z : 0;
+  v.p[0] = i;
+  v.p[1] = j;
+  v.p[2] = k;
   v.idx = i + g.sy * j + g.sz * k;
   v.c[0] = axis_class(i, g.n);
   v.c[1] = axis_class(j, g.n);

@@ -78,6 +78,28 @@ void launch_coarse_solve(long long nc, const T* Ainv, const T* b, T* x, cudaStre
 template <typename T, typename TX, typename TY>
 void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha,
                      const TY* y0, T beta, cudaStream_t s);
+// Fused coarse V-cycle: levels Lc..L of the hierarchy in one thread block with
+// every level vector in shared memory (x, b, r, d0, d1 at off[l]).
+constexpr int COARSE_MAXLEV = 8;
+template <typename T> struct CoarseArgs {
+  int nlev;                          // levels in the fused part (>= 2)
+  Geom g[COARSE_MAXLEV];
+  const T* W[COARSE_MAXLEV];         // S_hat weight tables (global)
+  const T* dinv[COARSE_MAXLEV];
+  long long off[COARSE_MAXLEV];      // element offset of the level's 5 vectors
+  const T* Ainv;                     // coarsest dense inverse (global)
+  T inv_th;                          // smoother 1/centre
+  T c1[16], c2[16];                  // smoother coefficients per step
+  int nu_pre, nu_post;
+};
+// b_in: right-hand side of level Lc; x_in: start iterate (null = zero); x_out: result
+template <typename T>
+void launch_coarse_vcycle(int dim, const CoarseArgs<T>& a, size_t smem, const T* b_in, const T* x_in, T* x_out,
+                          cudaStream_t s);
+// allow `smem` bytes of dynamic shared memory for the fused kernel (call before capture)
+template <typename T>
+cudaError_t prepare_coarse_vcycle(int dim, size_t smem);
+
 // dense matrix of a level operator (row-major nv x nv) from its class table
 void launch_dense_from_table(int dim, const Geom& g, const double* W, double* A, cudaStream_t s);
 // in-place Gauss--Jordan inverse of an SPD matrix (single block); work: n x 2n

@@ -288,19 +288,19 @@ void launch_multidot(const double* V, long long ldv, int K, const double* w, lon
                      double* out, cudaStream_t s) {
   for (int k0 = 0; k0 < K; k0 += KC) {
     int kk = K - k0 < KC ? K - k0 : KC;
-    k_multidot<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, kk, w, N, rs.partials, rs.counter, out + k0);
+    count_launch(), k_multidot<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, kk, w, N, rs.partials, rs.counter, out + k0);
   }
 }
 
 void launch_update_multidot(const double* V, long long ldv, int K, const double* h_in, double* w, long long N,
                             RedScratch rs, double* h_out, cudaStream_t s) {
   if (K <= KC) {
-    k_update_multidot<<<krylov_blocks(), RT, 0, s>>>(V, ldv, K, h_in, w, N, rs.partials, rs.counter, h_out);
+    count_launch(), k_update_multidot<<<krylov_blocks(), RT, 0, s>>>(V, ldv, K, h_in, w, N, rs.partials, rs.counter, h_out);
     return;
   }
   for (int k0 = 0; k0 < K; k0 += KC) {   // all updates first, then the dots of the final w
     int kk = K - k0 < KC ? K - k0 : KC;
-    k_update_only<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, kk, h_in + k0, w, N);
+    count_launch(), k_update_only<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, kk, h_in + k0, w, N);
   }
   launch_multidot(V, ldv, K, w, N, rs, h_out, s);
 }
@@ -310,30 +310,30 @@ void launch_update_norm_givens(const double* V, long long ldv, int K, double* w,
   int k0 = 0;
   for (; K - k0 > KC; k0 += KC) {
     // h2 lives in device memory inside ks; chunk offsets index it directly
-    k_update_only<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, KC, ks->h2 + k0, w, N);
+    count_launch(), k_update_only<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, KC, ks->h2 + k0, w, N);
   }
-  k_update_norm_givens<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, K - k0, w, N, rs.partials, rs.counter,
+  count_launch(), k_update_norm_givens<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, K - k0, w, N, rs.partials, rs.counter,
                                                        ks, j, k0);
 }
 
 void launch_scale_by(double* w, long long N, const double* factor, cudaStream_t s) {
-  k_scale_by<<<krylov_blocks(), RT, 0, s>>>(w, N, factor);
+  count_launch(), k_scale_by<<<krylov_blocks(), RT, 0, s>>>(w, N, factor);
 }
 
 void launch_norm(const double* x, long long N, RedScratch rs, double* out, cudaStream_t s) {
-  k_sumsq<<<krylov_blocks(), RT, 0, s>>>(x, N, rs.partials, rs.counter, out);
+  count_launch(), k_sumsq<<<krylov_blocks(), RT, 0, s>>>(x, N, rs.partials, rs.counter, out);
 }
 
 void launch_cycle_start(KrylovState* ks, const double* beta, cudaStream_t s) {
-  k_cycle_start<<<1, 32, 0, s>>>(ks, beta);
+  count_launch(), k_cycle_start<<<1, 32, 0, s>>>(ks, beta);
 }
 
-void launch_lsq(KrylovState* ks, int k, cudaStream_t s) { k_lsq<<<1, 32, 0, s>>>(ks, k); }
+void launch_lsq(KrylovState* ks, int k, cudaStream_t s) { count_launch(), k_lsq<<<1, 32, 0, s>>>(ks, k); }
 
 template <typename TZ>
 void launch_multi_axpy(const TZ* Z, long long ldz, int K, const KrylovState* ks, double* x, long long N,
                        cudaStream_t s) {
-  k_multi_axpy<TZ><<<krylov_blocks(), RT, 0, s>>>(Z, ldz, K, ks, x, N);
+  count_launch(), k_multi_axpy<TZ><<<krylov_blocks(), RT, 0, s>>>(Z, ldz, K, ks, x, N);
 }
 template void launch_multi_axpy<double>(const double*, long long, int, const KrylovState*, double*, long long,
                                         cudaStream_t);
@@ -342,7 +342,7 @@ template void launch_multi_axpy<float>(const float*, long long, int, const Krylo
 
 template <typename TX, typename TY>
 void launch_axpby(long long N, double a, const TX* x, double b, TY* y, cudaStream_t s) {
-  k_axpby<TX, TY><<<krylov_blocks(), RT, 0, s>>>(N, a, x, b, y);
+  count_launch(), k_axpby<TX, TY><<<krylov_blocks(), RT, 0, s>>>(N, a, x, b, y);
 }
 template void launch_axpby<double, double>(long long, double, const double*, double, double*, cudaStream_t);
 template void launch_axpby<float, double>(long long, double, const float*, double, double*, cudaStream_t);
@@ -350,7 +350,7 @@ template void launch_axpby<double, float>(long long, double, const double*, doub
 template void launch_axpby<float, float>(long long, double, const float*, double, float*, cudaStream_t);
 
 void launch_check_finite(const double* x, long long N, int* flag, cudaStream_t s) {
-  k_check_finite<<<krylov_blocks(), RT, 0, s>>>(x, N, flag);
+  count_launch(), k_check_finite<<<krylov_blocks(), RT, 0, s>>>(x, N, flag);
 }
 
 }  // namespace okg

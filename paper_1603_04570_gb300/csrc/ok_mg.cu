@@ -28,58 +28,49 @@ static inline dim3 grid_of(int dim, const Geom& g) {
   return dim3((g.n1 + BX - 1) / BX, g.n1, dim == 3 ? g.n1 : 1);
 }
 
+// ---------------------------------------------------------------------------
+// per-vertex bodies, shared by the one-kernel-per-step path and the fused
+// coarse V-cycle below (explicit fma everywhere a product feeds a sum, so the
+// two paths round identically)
+// ---------------------------------------------------------------------------
 template <int D, typename T, typename TB>
-__global__ void __launch_bounds__(BX) k_cheb_init(Geom g, const T* __restrict__ dinv, const TB* __restrict__ b,
-                                                  T bscale, T* __restrict__ r, T* __restrict__ d, T inv_th) {
-  Vtx<D> v;
-  if (!vertex_of_thread<D>(g, v)) return;
+__device__ __forceinline__ void cheb_init_at(const Vtx<D>& v, const T* dinv, const TB* b, T bscale, T* r, T* d,
+                                             T inv_th) {
   T rr = (T)b[v.idx] * bscale;
   r[v.idx] = rr;
   d[v.idx] = dinv[v.cls] * rr * inv_th;
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(BX) k_resid_init(Geom g, const T* __restrict__ W, const T* __restrict__ dinv,
-                                                   const T* __restrict__ b, const T* __restrict__ x,
-                                                   T* __restrict__ r, T* __restrict__ d, T inv_th) {
-  using Tp = Topo<D>;
-  Vtx<D> v;
-  if (!vertex_of_thread<D>(g, v)) return;
-  T xs[Tp::NOFF];
+__device__ __forceinline__ void resid_init_at(const Geom& g, const Vtx<D>& v, const T* W, const T* dinv,
+                                              const T* b, const T* x, T* r, T* d, T inv_th) {
+  T xs[Topo<D>::NOFF];
   load_nb<D>(x, g, v, xs);
-  T rr = b[v.idx] - dot_w<D, Tp::NOFF>(W, v.cls, xs);
+  T rr = b[v.idx] - dot_w<D, Topo<D>::NOFF>(W, v.cls, xs);
   r[v.idx] = rr;
   d[v.idx] = dinv[v.cls] * rr * inv_th;
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(BX) k_cheb_step(Geom g, const T* __restrict__ W, const T* __restrict__ dinv,
-                                                  T* __restrict__ x, T* __restrict__ r, const T* __restrict__ din,
-                                                  T* __restrict__ dout, T c1, T c2, int first) {
-  using Tp = Topo<D>;
-  Vtx<D> v;
-  if (!vertex_of_thread<D>(g, v)) return;
-  T ds[Tp::NOFF];
+__device__ __forceinline__ void cheb_step_at(const Geom& g, const Vtx<D>& v, const T* W, const T* dinv, T* x,
+                                             T* r, const T* din, T* dout, T c1, T c2, bool first) {
+  T ds[Topo<D>::NOFF];
   load_nb<D>(din, g, v, ds);
   x[v.idx] = (first ? (T)0 : x[v.idx]) + ds[0];
-  T rr = r[v.idx] - dot_w<D, Tp::NOFF>(W, v.cls, ds);
+  T rr = r[v.idx] - dot_w<D, Topo<D>::NOFF>(W, v.cls, ds);
   r[v.idx] = rr;
-  dout[v.idx] = c1 * ds[0] + c2 * (dinv[v.cls] * rr);
+  dout[v.idx] = fma(c1, ds[0], c2 * (dinv[v.cls] * rr));
 }
 
 template <int D, typename T, typename TO>
-__global__ void __launch_bounds__(BX) k_cheb_last(Geom g, const T* __restrict__ W, T* __restrict__ x,
-                                                  T* __restrict__ r, const T* __restrict__ din, int first,
-                                                  TO* __restrict__ out, T oscale) {
-  using Tp = Topo<D>;
-  Vtx<D> v;
-  if (!vertex_of_thread<D>(g, v)) return;
+__device__ __forceinline__ void cheb_last_at(const Geom& g, const Vtx<D>& v, const T* W, T* x, T* r,
+                                             const T* din, bool first, TO* out, T oscale) {
   T xx;
   if (r) {
-    T ds[Tp::NOFF];
+    T ds[Topo<D>::NOFF];
     load_nb<D>(din, g, v, ds);
     xx = (first ? (T)0 : x[v.idx]) + ds[0];
-    r[v.idx] = r[v.idx] - dot_w<D, Tp::NOFF>(W, v.cls, ds);
+    r[v.idx] = r[v.idx] - dot_w<D, Topo<D>::NOFF>(W, v.cls, ds);
   } else {
     xx = (first ? (T)0 : x[v.idx]) + din[v.idx];
   }
@@ -87,44 +78,37 @@ __global__ void __launch_bounds__(BX) k_cheb_last(Geom g, const T* __restrict__ 
   if (out) out[v.idx] = (TO)(xx * oscale);
 }
 
+// v: coarse vertex (position p), gf: fine geometry
 template <int D, typename T>
-__global__ void __launch_bounds__(BX) k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ bc) {
-  using Tp = Topo<D>;
-  Vtx<D> v;                               // coarse vertex
-  if (!vertex_of_thread<D>(gc, v)) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = D == 3 ? blockIdx.z : 0;
-  long long fc = 2LL * i + gf.sy * (2LL * j) + gf.sz * (2LL * k);
+__device__ __forceinline__ void restrict_at(const Geom& gf, const Vtx<D>& v, const T* rf, T* bc) {
+  long long fc = 2LL * v.p[0] + gf.sy * (2LL * v.p[1]) + gf.sz * (2LL * v.p[2]);
   T acc = (T)0;
-  static_for<1, Tp::NOFF>([&](auto O) {
+  static_for<1, Topo<D>::NOFF>([&](auto O) {
     constexpr int o = decltype(O)::value;
     if (nb_valid<D, o>(v.c)) acc += rf[fc + nb_delta<D, o>(gf)];
   });
-  bc[v.idx] = rf[fc] + (T)0.5 * acc;
+  bc[v.idx] = fma((T)0.5, acc, rf[fc]);
 }
 
+// v: fine vertex, gc: coarse geometry
 template <int D, typename T>
-__global__ void __launch_bounds__(BX) k_prolong_add(Geom gf, Geom gc, T* __restrict__ xf, const T* __restrict__ xc) {
-  Vtx<D> v;                               // fine vertex
-  if (!vertex_of_thread<D>(gf, v)) return;
-  int f[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)blockIdx.y, D == 3 ? (int)blockIdx.z : 0};
+__device__ __forceinline__ void prolong_add_at(const Geom& gc, const Vtx<D>& v, T* xf, const T* xc) {
   long long ci = 0, cj = 0;
   bool mid = false;
-  long long st[3] = {1, gc.sy, gc.sz};
+  const long long st[3] = {1, gc.sy, gc.sz};
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    ci += (long long)(f[a] >> 1) * st[a];
-    cj += (long long)((f[a] >> 1) + (f[a] & 1)) * st[a];
-    mid = mid || (f[a] & 1);
+    ci += (long long)(v.p[a] >> 1) * st[a];
+    cj += (long long)((v.p[a] >> 1) + (v.p[a] & 1)) * st[a];
+    mid = mid || (v.p[a] & 1);
   }
-  T add = mid ? (T)0.5 * (xc[ci] + xc[cj]) : xc[ci];
-  xf[v.idx] += add;
+  xf[v.idx] = mid ? fma((T)0.5, xc[ci] + xc[cj], xf[v.idx]) : xf[v.idx] + xc[ci];
 }
 
-// one block; warp per row
+// x[r] = sum_c A[r][c] b[c] for the rows of this warp (lane-strided, xor-reduced)
 template <typename T>
-__global__ void __launch_bounds__(512) k_coarse_solve(long long nc, const T* __restrict__ A, const T* __restrict__ b,
-                                                      T* __restrict__ x) {
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ __forceinline__ void coarse_rows(long long nc, const T* A, const T* b, T* x, int warp, int nw) {
+  const int lane = threadIdx.x & 31;
   for (long long r = warp; r < nc; r += nw) {
     T acc = (T)0;
     for (long long c = lane; c < nc; c += 32) acc = fma(A[r * nc + c], b[c], acc);
@@ -132,6 +116,158 @@ __global__ void __launch_bounds__(512) k_coarse_solve(long long nc, const T* __r
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) x[r] = acc;
   }
+}
+
+// ---------------------------------------------------------------------------
+// one kernel per step
+// ---------------------------------------------------------------------------
+template <int D, typename T, typename TB>
+__global__ void __launch_bounds__(BX) k_cheb_init(Geom g, const T* __restrict__ dinv, const TB* __restrict__ b,
+                                                  T bscale, T* __restrict__ r, T* __restrict__ d, T inv_th) {
+  Vtx<D> v;
+  if (!vertex_of_thread<D>(g, v)) return;
+  cheb_init_at<D, T, TB>(v, dinv, b, bscale, r, d, inv_th);
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(BX) k_resid_init(Geom g, const T* __restrict__ W, const T* __restrict__ dinv,
+                                                   const T* __restrict__ b, const T* __restrict__ x,
+                                                   T* __restrict__ r, T* __restrict__ d, T inv_th) {
+  Vtx<D> v;
+  if (!vertex_of_thread<D>(g, v)) return;
+  resid_init_at<D, T>(g, v, W, dinv, b, x, r, d, inv_th);
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(BX) k_cheb_step(Geom g, const T* __restrict__ W, const T* __restrict__ dinv,
+                                                  T* __restrict__ x, T* __restrict__ r, const T* __restrict__ din,
+                                                  T* __restrict__ dout, T c1, T c2, int first) {
+  Vtx<D> v;
+  if (!vertex_of_thread<D>(g, v)) return;
+  cheb_step_at<D, T>(g, v, W, dinv, x, r, din, dout, c1, c2, first != 0);
+}
+
+template <int D, typename T, typename TO>
+__global__ void __launch_bounds__(BX) k_cheb_last(Geom g, const T* __restrict__ W, T* __restrict__ x,
+                                                  T* __restrict__ r, const T* __restrict__ din, int first,
+                                                  TO* __restrict__ out, T oscale) {
+  Vtx<D> v;
+  if (!vertex_of_thread<D>(g, v)) return;
+  cheb_last_at<D, T, TO>(g, v, W, x, r, din, first != 0, out, oscale);
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(BX) k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ bc) {
+  Vtx<D> v;                               // coarse vertex
+  if (!vertex_of_thread<D>(gc, v)) return;
+  restrict_at<D, T>(gf, v, rf, bc);
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(BX) k_prolong_add(Geom gf, Geom gc, T* __restrict__ xf, const T* __restrict__ xc) {
+  Vtx<D> v;                               // fine vertex
+  if (!vertex_of_thread<D>(gf, v)) return;
+  prolong_add_at<D, T>(gc, v, xf, xc);
+}
+
+// one block; warp per row
+template <typename T>
+__global__ void __launch_bounds__(512) k_coarse_solve(long long nc, const T* __restrict__ A, const T* __restrict__ b,
+                                                      T* __restrict__ x) {
+  coarse_rows<T>(nc, A, b, x, threadIdx.x >> 5, blockDim.x >> 5);
+}
+
+// ---------------------------------------------------------------------------
+// fused coarse V-cycle: levels Lc..L in one thread block, vectors in shared
+// memory; the same sequence of steps as Prec::vcycle on the host, each step a
+// block-stride loop followed by __syncthreads().
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__device__ __forceinline__ void vertex_of_index(const Geom& g, long long idx, Vtx<D>& v) {
+  const long long n1 = g.n1;
+  v.idx = idx;
+  v.p[0] = (int)(idx % n1);
+  const long long rest = idx / n1;
+  v.p[1] = (int)(rest % n1);
+  v.p[2] = D == 3 ? (int)(rest / n1) : 0;
+  v.c[0] = axis_class(v.p[0], g.n);
+  v.c[1] = axis_class(v.p[1], g.n);
+  v.c[2] = D == 3 ? axis_class(v.p[2], g.n) : 1;
+  v.cls = v.c[0] + 3 * v.c[1] + (D == 3 ? 9 * v.c[2] : 0);
+}
+
+#define OK_FOR_VERTICES(G, V, BODY)                                                   \
+  for (long long _i = threadIdx.x; _i < (G).nv; _i += blockDim.x) {                  \
+    Vtx<D> V;                                                                        \
+    vertex_of_index<D, T>((G), _i, V);                                               \
+    BODY;                                                                            \
+  }                                                                                  \
+  __syncthreads();
+
+template <int D, typename T>
+__device__ void fused_smooth(const CoarseArgs<T>& a, int l, T* sm, bool x_zero, int nu, bool want_r) {
+  const Geom& g = a.g[l];
+  const long long nv = g.nv;
+  T* X = sm + a.off[l];
+  T* B = X + nv;
+  T* R = B + nv;
+  T* Dd[2] = {R + nv, R + 2 * nv};
+  const T* W = a.W[l];
+  const T* dv = a.dinv[l];
+  if (x_zero) {
+    OK_FOR_VERTICES(g, v, (cheb_init_at<D, T, T>(v, dv, B, (T)1, R, Dd[0], a.inv_th)))
+  } else {
+    OK_FOR_VERTICES(g, v, (resid_init_at<D, T>(g, v, W, dv, B, X, R, Dd[0], a.inv_th)))
+  }
+  int cur = 0;
+  for (int k = 0; k + 1 < nu; ++k) {
+    const bool first = x_zero && k == 0;
+    OK_FOR_VERTICES(g, v, (cheb_step_at<D, T>(g, v, W, dv, X, R, Dd[cur], Dd[1 - cur], a.c1[k], a.c2[k], first)))
+    cur ^= 1;
+  }
+  const bool first = x_zero && nu == 1;
+  OK_FOR_VERTICES(g, v, (cheb_last_at<D, T, T>(g, v, W, X, want_r ? R : (T*)nullptr, Dd[cur], first, (T*)nullptr,
+                                               (T)1)))
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseArgs<T> a, const T* __restrict__ b_in,
+                                                        const T* x_in, T* x_out) {   // x_in may equal x_out
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int L = a.nlev - 1;
+  {
+    T* X0 = sm + a.off[0];
+    T* B0 = X0 + a.g[0].nv;
+    for (long long i = threadIdx.x; i < a.g[0].nv; i += blockDim.x) {
+      B0[i] = b_in[i];
+      if (x_in) X0[i] = x_in[i];
+    }
+    __syncthreads();
+  }
+  // descend
+  for (int l = 0; l < L; ++l) {
+    fused_smooth<D, T>(a, l, sm, l > 0 || x_in == nullptr, a.nu_pre, true);
+    const Geom& gc = a.g[l + 1];
+    T* Rf = sm + a.off[l] + 2 * a.g[l].nv;
+    T* Bc = sm + a.off[l + 1] + gc.nv;
+    OK_FOR_VERTICES(gc, v, (restrict_at<D, T>(a.g[l], v, Rf, Bc)))
+  }
+  // coarsest: exact
+  {
+    T* Xc = sm + a.off[L];
+    coarse_rows<T>(a.g[L].nv, a.Ainv, Xc + a.g[L].nv, Xc, threadIdx.x >> 5, blockDim.x >> 5);
+    __syncthreads();
+  }
+  // ascend
+  for (int l = L - 1; l >= 0; --l) {
+    const Geom& g = a.g[l];
+    T* Xf = sm + a.off[l];
+    const T* Xc = sm + a.off[l + 1];
+    OK_FOR_VERTICES(g, v, (prolong_add_at<D, T>(a.g[l + 1], v, Xf, Xc)))
+    fused_smooth<D, T>(a, l, sm, false, a.nu_post, false);
+  }
+  for (long long i = threadIdx.x; i < a.g[0].nv; i += blockDim.x) x_out[i] = sm[a.off[0] + i];
 }
 
 template <int D, typename T, typename TX, typename TY>
@@ -201,53 +337,72 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(long long n, const double
 template <typename T, typename TB>
 void launch_cheb_init(int dim, const Geom& g, const T* dinv, const TB* b, T bscale, T* r, T* d, T inv_th,
                       cudaStream_t s) {
-  if (dim == 2) k_cheb_init<2, T, TB><<<grid_of(2, g), BX, 0, s>>>(g, dinv, b, bscale, r, d, inv_th);
-  else k_cheb_init<3, T, TB><<<grid_of(3, g), BX, 0, s>>>(g, dinv, b, bscale, r, d, inv_th);
+  if (dim == 2) count_launch(), k_cheb_init<2, T, TB><<<grid_of(2, g), BX, 0, s>>>(g, dinv, b, bscale, r, d, inv_th);
+  else count_launch(), k_cheb_init<3, T, TB><<<grid_of(3, g), BX, 0, s>>>(g, dinv, b, bscale, r, d, inv_th);
 }
 template <typename T>
 void launch_resid_init(int dim, const Geom& g, const T* W, const T* dinv, const T* b, const T* x, T* r, T* d,
                        T inv_th, cudaStream_t s) {
-  if (dim == 2) k_resid_init<2, T><<<grid_of(2, g), BX, 0, s>>>(g, W, dinv, b, x, r, d, inv_th);
-  else k_resid_init<3, T><<<grid_of(3, g), BX, 0, s>>>(g, W, dinv, b, x, r, d, inv_th);
+  if (dim == 2) count_launch(), k_resid_init<2, T><<<grid_of(2, g), BX, 0, s>>>(g, W, dinv, b, x, r, d, inv_th);
+  else count_launch(), k_resid_init<3, T><<<grid_of(3, g), BX, 0, s>>>(g, W, dinv, b, x, r, d, inv_th);
 }
 template <typename T>
 void launch_cheb_step(int dim, const Geom& g, const T* W, const T* dinv, T* x, T* r, const T* d_in, T* d_out,
                       T c1, T c2, bool first, cudaStream_t s) {
-  if (dim == 2) k_cheb_step<2, T><<<grid_of(2, g), BX, 0, s>>>(g, W, dinv, x, r, d_in, d_out, c1, c2, first);
-  else k_cheb_step<3, T><<<grid_of(3, g), BX, 0, s>>>(g, W, dinv, x, r, d_in, d_out, c1, c2, first);
+  if (dim == 2) count_launch(), k_cheb_step<2, T><<<grid_of(2, g), BX, 0, s>>>(g, W, dinv, x, r, d_in, d_out, c1, c2, first);
+  else count_launch(), k_cheb_step<3, T><<<grid_of(3, g), BX, 0, s>>>(g, W, dinv, x, r, d_in, d_out, c1, c2, first);
 }
 template <typename T, typename TO>
 void launch_cheb_last(int dim, const Geom& g, const T* W, T* x, T* r, const T* d_in, bool first, TO* out,
                       T oscale, cudaStream_t s) {
-  if (dim == 2) k_cheb_last<2, T, TO><<<grid_of(2, g), BX, 0, s>>>(g, W, x, r, d_in, first, out, oscale);
-  else k_cheb_last<3, T, TO><<<grid_of(3, g), BX, 0, s>>>(g, W, x, r, d_in, first, out, oscale);
+  if (dim == 2) count_launch(), k_cheb_last<2, T, TO><<<grid_of(2, g), BX, 0, s>>>(g, W, x, r, d_in, first, out, oscale);
+  else count_launch(), k_cheb_last<3, T, TO><<<grid_of(3, g), BX, 0, s>>>(g, W, x, r, d_in, first, out, oscale);
 }
 template <typename T>
 void launch_restrict(int dim, const Geom& gf, const Geom& gc, const T* rf, T* bc, cudaStream_t s) {
-  if (dim == 2) k_restrict<2, T><<<grid_of(2, gc), BX, 0, s>>>(gf, gc, rf, bc);
-  else k_restrict<3, T><<<grid_of(3, gc), BX, 0, s>>>(gf, gc, rf, bc);
+  if (dim == 2) count_launch(), k_restrict<2, T><<<grid_of(2, gc), BX, 0, s>>>(gf, gc, rf, bc);
+  else count_launch(), k_restrict<3, T><<<grid_of(3, gc), BX, 0, s>>>(gf, gc, rf, bc);
 }
 template <typename T>
 void launch_prolong_add(int dim, const Geom& gf, const Geom& gc, T* xf, const T* xc, cudaStream_t s) {
-  if (dim == 2) k_prolong_add<2, T><<<grid_of(2, gf), BX, 0, s>>>(gf, gc, xf, xc);
-  else k_prolong_add<3, T><<<grid_of(3, gf), BX, 0, s>>>(gf, gc, xf, xc);
+  if (dim == 2) count_launch(), k_prolong_add<2, T><<<grid_of(2, gf), BX, 0, s>>>(gf, gc, xf, xc);
+  else count_launch(), k_prolong_add<3, T><<<grid_of(3, gf), BX, 0, s>>>(gf, gc, xf, xc);
 }
 template <typename T>
 void launch_coarse_solve(long long nc, const T* Ainv, const T* b, T* x, cudaStream_t s) {
-  k_coarse_solve<T><<<1, 512, 0, s>>>(nc, Ainv, b, x);
+  count_launch(), k_coarse_solve<T><<<1, 512, 0, s>>>(nc, Ainv, b, x);
 }
 template <typename T, typename TX, typename TY>
 void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha,
                      const TY* y0, T beta, cudaStream_t s) {
-  if (dim == 2) k_op_apply<2, T, TX, TY><<<grid_of(2, g), BX, 0, s>>>(g, W, axis_only, x, y, alpha, y0, beta);
-  else k_op_apply<3, T, TX, TY><<<grid_of(3, g), BX, 0, s>>>(g, W, axis_only, x, y, alpha, y0, beta);
+  if (dim == 2) count_launch(), k_op_apply<2, T, TX, TY><<<grid_of(2, g), BX, 0, s>>>(g, W, axis_only, x, y, alpha, y0, beta);
+  else count_launch(), k_op_apply<3, T, TX, TY><<<grid_of(3, g), BX, 0, s>>>(g, W, axis_only, x, y, alpha, y0, beta);
 }
+template <typename T>
+void launch_coarse_vcycle(int dim, const CoarseArgs<T>& a, size_t smem, const T* b_in, const T* x_in, T* x_out,
+                          cudaStream_t s) {
+  if (dim == 2) count_launch(), k_coarse_vcycle<2, T><<<1, 1024, smem, s>>>(a, b_in, x_in, x_out);
+  else count_launch(), k_coarse_vcycle<3, T><<<1, 1024, smem, s>>>(a, b_in, x_in, x_out);
+}
+template <typename T>
+cudaError_t prepare_coarse_vcycle(int dim, size_t smem) {
+  if (dim == 2)
+    return cudaFuncSetAttribute(k_coarse_vcycle<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(k_coarse_vcycle<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+template void launch_coarse_vcycle<double>(int, const CoarseArgs<double>&, size_t, const double*, const double*,
+                                           double*, cudaStream_t);
+template void launch_coarse_vcycle<float>(int, const CoarseArgs<float>&, size_t, const float*, const float*, float*,
+                                          cudaStream_t);
+template cudaError_t prepare_coarse_vcycle<double>(int, size_t);
+template cudaError_t prepare_coarse_vcycle<float>(int, size_t);
+
 void launch_dense_from_table(int dim, const Geom& g, const double* W, double* A, cudaStream_t s) {
-  if (dim == 2) k_dense_from_table<2><<<grid_of(2, g), BX, 0, s>>>(g, W, A);
-  else k_dense_from_table<3><<<grid_of(3, g), BX, 0, s>>>(g, W, A);
+  if (dim == 2) count_launch(), k_dense_from_table<2><<<grid_of(2, g), BX, 0, s>>>(g, W, A);
+  else count_launch(), k_dense_from_table<3><<<grid_of(3, g), BX, 0, s>>>(g, W, A);
 }
 void launch_gauss_jordan(long long n, const double* A, double* work, double* Ainv, cudaStream_t s) {
-  k_gauss_jordan<<<1, 1024, n * sizeof(double), s>>>(n, A, work, Ainv);
+  count_launch(), k_gauss_jordan<<<1, 1024, n * sizeof(double), s>>>(n, A, work, Ainv);
 }
 
 #define OK_INST_T(T)                                                                                          \

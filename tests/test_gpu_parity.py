@@ -240,3 +240,39 @@ def test_batch_runs_each_request():
         assert st == ok.OK_SUCCESS and info.completed == 2
         assert torch.equal(a_u, ref_u) and torch.equal(a_w, ref_w)
         assert reqs[1].newton_its >= 3
+
+
+def test_profiling_samples_and_launch_count():
+    wl = oi.SMALL_2D
+    u0 = oi.initial_u(wl)
+    with ok.Grid(2, 32, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt) as g:
+        u, w = dev(u0), torch.zeros(g.nv, dtype=torch.float64, device="cuda")
+        g.init_w(u, w)
+        ok.ok_profile(g.handle, True)
+        l0 = ok.ok_launch_count()
+        info = g.timestep(u, w)
+        launched = ok.ok_launch_count() - l0
+        stats = ok.ok_profile_read(g.handle)
+        ok.ok_profile(g.handle, False)
+        for name in ("precond", "apply_j", "cgs2", "mg_smooth_l0", "cheb_mass_step"):
+            n, ms = stats[name]
+            assert n == info.gmres_its and ms > 0, name
+        assert launched > 20 * info.gmres_its        # preconditioner + Arnoldi kernels per iteration
+
+
+@pytest.mark.parametrize("dim,n", [(2, 64), (2, 160), (2, 12), (3, 24), (3, 16), (3, 6)])
+@pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
+def test_fused_coarse_vcycle_is_bitwise_identical(dim, n, precision):
+    """The one-block shared-memory coarse V-cycle takes the same steps as the
+    one-kernel-per-step path, so the preconditioner outputs agree bitwise."""
+    sysm, p, rng = make(dim, n, seed=5, dt=1e-4)
+    nv = sysm.mesh.nv
+    u = dev(rng.uniform(-1.0, 1.0, nv))
+    v = dev(rng.standard_normal(2 * nv))
+    out = []
+    for fuse in (0, 1):
+        with ok.Grid(dim, n, **p, n_V=2, precision=precision, fuse_coarse=fuse) as g:
+            z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+            g.apply_preconditioner(u, v, z)
+            out.append(host(z))
+    assert np.array_equal(out[0], out[1])
