@@ -243,9 +243,11 @@ def test_batch_runs_each_request():
 
 
 def test_profiling_samples_and_launch_count():
-    wl = oi.SMALL_2D
+    # 128^2: the finest level is not part of the fused coarse kernel, so every
+    # sampled kernel class occurs once per Arnoldi step
+    wl = oi.scaled(oi.SMALL_2D, 128)
     u0 = oi.initial_u(wl)
-    with ok.Grid(2, 32, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt) as g:
+    with ok.Grid(2, 128, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt) as g:
         u, w = dev(u0), torch.zeros(g.nv, dtype=torch.float64, device="cuda")
         g.init_w(u, w)
         ok.ok_profile(g.handle, True)
