@@ -210,6 +210,28 @@ typedef struct ok_kernel_stat {
 int ok_profile(ok_grid* g, int enable);
 int ok_profile_read(const ok_grid* g, ok_kernel_stat* out, int max, int* count);
 
+/* y = J(u_k) z like ok_apply_jacobian, for callers that cannot allocate
+ * device memory: applications that own all GPU memory through their own
+ * allocator or run under a fixed memory budget, and latency-critical loops
+ * that cannot afford cudaMalloc's device-wide synchronisation.  The paper has
+ * no counterpart; this is an interface convenience of the library.
+ *
+ * No handle is needed and nothing is allocated: the per-Newton-step
+ * coefficients of C = -eps^2 K - M_E(u_k) go to a 16 MiB static device array
+ * that every GPU loading the library holds until the process exits.
+ *   - dim 2 or 3, n cells per side, p as in ok_grid_create;
+ *   - u_k (N_v), z and y (2 N_v) must be DEVICE arrays (no host staging);
+ *   - grids needing more than 16 MiB of coefficients are rejected with
+ *     OK_ERR_INVALID_ARG (2D: n <= 590; 3D: n <= 54);
+ *   - work is enqueued on `stream`; the call does not synchronise;
+ *   - every call shares the one array and leaves its coefficients there:
+ *     calls whose work overlaps on the GPU race, so serialise them;
+ *   - the first call on a device looks up the array's address and uploads
+ *     the stencil tables (synchronously): make it before any stream capture.
+ * Errors are reported through ok_last_error(). */
+int ok_apply_jacobian_noalloc(int dim, int n, const ok_params* p, const double* u_k, const double* z,
+                              double* y, ok_stream stream);
+
 /* Number of this library's kernels launched by the process so far (graph
  * replays count every kernel node). */
 long long ok_launch_count(void);

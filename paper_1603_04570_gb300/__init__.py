@@ -98,6 +98,7 @@ def load(build: bool = True):
         "ok_profile": (c_int, [P, c_int]),
         "ok_profile_read": (c_int, [P, POINTER(KernelStat), c_int, POINTER(c_int)]),
         "ok_launch_count": (c_longlong, []),
+        "ok_apply_jacobian_noalloc": (c_int, [c_int, c_int, POINTER(Params), P, P, P, P]),
         "ok_last_error": (c_char_p, []),
         "ok_version": (c_char_p, []),
     }
@@ -233,6 +234,13 @@ def ok_profile_read(h):
     n = c_int()
     _check(load().ok_profile_read(h, arr, 16, byref(n)))
     return {arr[i].name.decode(): (arr[i].samples, arr[i].total_ms) for i in range(n.value)}
+
+
+def ok_apply_jacobian_noalloc(dim, n, params: Params, u_k, z, y, stream=None):
+    """y = J(u_k) z with no device allocation (device arrays only; see include/ok.h)."""
+    nv = (n + 1) ** dim
+    _check(load().ok_apply_jacobian_noalloc(dim, n, byref(params), _ptr(u_k, nv, "u_k"), _ptr(z, 2 * nv, "z"),
+                                            _ptr(y, 2 * nv, "y"), _stream(stream, y, z)))
 
 
 def ok_launch_count() -> int:

@@ -1115,3 +1115,6 @@ int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream st
 }
 
 }  // extern "C"
+
+// Lets other translation units set the message ok_last_error() returns.
+void okg::set_last_error(const char* msg) { g_last_error = msg; }

@@ -139,6 +139,8 @@ void launch_axpby(long long N, double a, const TX* x, double b, TY* y, cudaStrea
 // flag |= any non-finite in x
 void launch_check_finite(const double* x, long long N, int* flag, cudaStream_t s);
 size_t krylov_state_bytes();
+// sets the message ok_last_error() returns (defined in ok_api.cu)
+void set_last_error(const char* msg);
 double* ks_resid_ptr(KrylovState* ks);
 double* ks_eta_ptr(KrylovState* ks);
 double* ks_beta_ptr(KrylovState* ks);
