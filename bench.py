@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--workload", default="2d_n1024", choices=sorted(oi.WORKLOADS))
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer run (short profiling runs)")
     ap.add_argument("--profile-out", default=None, help="write per-kernel samples as JSON")
     return ap.parse_args()
 
@@ -160,6 +161,16 @@ def kernel_model(tag, wl, precision):
         return by, fl, "alu"
     if tag in ("mg_smooth_l0", "cheb_mass_step"):
         return nv * 6 * bp, nv * 2 * (noff + 4), "hbm"
+    nc = (wl.n // 2 + 1) ** d
+    if tag == "mg_tile_pre_l0":
+        # first pre-smoothing launch of a solve starts from x = 0: reads b, writes x and P^T r
+        return nv * 2 * bp + nc * bp, nv * 2 * (3 * noff + 12) + nc * 2 * noff, "hbm"
+    if tag == "mg_tile_post_l0":
+        # reads x, b and the coarse x; writes x
+        return nv * 3 * bp + nc * bp, nv * 2 * (2 * noff + 12), "hbm"
+    if tag == "tile_mass_cstep":
+        # reads v (2 float64 fields) and the C store (1 + NPOS values), writes z1 and t
+        return nv * (16 + bp * (npos + 1) + bz + bp), nv * 2 * (9 * (noff + 4) + 2 * npos + 2), "hbm"
     return None, None, None
 
 
@@ -171,6 +182,10 @@ def launches_per_iteration(tag, opts):
         return k * opts["n_V"] * ((opts["smooth_pre"] - 1) + (opts["smooth_post"] - 1))
     if tag == "cheb_mass_step":
         return (opts["q_A"] - 1) * (1 if opts.get("k_R", 1) == 1 else 2)
+    if tag in ("mg_tile_pre_l0", "mg_tile_post_l0"):
+        return 2 * opts["n_V"]
+    if tag == "tile_mass_cstep":
+        return 1
     return None
 
 
@@ -321,7 +336,7 @@ def main_ok(args):
     clk = clocks.stop()
     fp64 = None if args.no_fp64 else run_precision(ok, torch, wl, "fp64", args.steps, args.warmup, rank, True,
                                                    flush)
-    e2e = e2e_run(ok, torch, mixed, wl, args.steps, flush)
+    e2e = None if args.no_e2e else e2e_run(ok, torch, mixed, wl, args.steps, flush)
     dof = 2 * wl.n_vertices
     total_ms = sum(mixed["step_ms"])
     agg = reduce_across({"ms": total_ms}, "max")

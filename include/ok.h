@@ -92,6 +92,7 @@ typedef struct ok_opts {
   int coarse_max;     /* halve the grid while n is even and > coarse_max [4]    */
   int use_graphs;     /* capture each Arnoldi step in a CUDA graph [1]          */
   int fuse_coarse;    /* run the coarse multigrid levels in one kernel [1]      */
+  int tile_fine;      /* 2D: shared-memory tile kernels on the fine levels [1]  */
   double gmres_rtol;  /* stop when ||f - J x|| <= gmres_rtol ||f|| [1e-10]      */
   double newton_atol; /* Newton stops when ||F||_2 <= max(atol, rtol ||F_0||)   */
   double newton_rtol; /*   [atol 1e-10, rtol 0]                                 */

@@ -94,9 +94,10 @@ std::atomic<long long> okg::g_launch_count{0};
 // step, recorded on the handle's stream (inside the captured graph when
 // graphs are on) and read after the step's host synchronisation.
 // ---------------------------------------------------------------------------
-enum ProfTag { PT_PRECOND = 0, PT_APPLYJ, PT_CGS2, PT_SMOOTH0, PT_CHEBM, PT_COUNT };
+enum ProfTag { PT_PRECOND = 0, PT_APPLYJ, PT_CGS2, PT_SMOOTH0, PT_CHEBM, PT_TPRE0, PT_TPOST0, PT_TAMASS, PT_COUNT };
 static const char* const kProfNames[PT_COUNT] = {"precond", "apply_j", "cgs2", "mg_smooth_l0",
-                                                 "cheb_mass_step"};
+                                                 "cheb_mass_step", "mg_tile_pre_l0", "mg_tile_post_l0",
+                                                 "tile_mass_cstep"};
 using TagSet = std::array<bool, PT_COUNT>;
 
 struct Profiler {
@@ -177,6 +178,7 @@ template <typename T> struct Level {
   int n;
   Geom g;
   T *x, *b, *r, *d0, *d1;
+  T* xa;           // second iterate buffer for the tile kernels (read one, write the other)
   T *WS, *dinvS;
 };
 
@@ -199,6 +201,55 @@ template <typename T> struct Prec {
   int Lc = 0;
   CoarseArgs<T> ca{};
   size_t csmem = 0;
+  bool tiled = false;          // 2D: levels above Lc by shared-memory tile kernels
+  std::vector<TileSmooth<T>> ts;
+  TileMass<T> tm{};
+  T* b2 = nullptr;             // right-hand side of the second S_hat solve (M S_hat^{-1} t)
+  std::vector<int> cur;        // per level: 0 = x holds the iterate, 1 = xa does
+
+  T* X(int l) { return cur[l] ? lv[l].xa : lv[l].x; }
+  T* Xalt(int l) { return cur[l] ? lv[l].x : lv[l].xa; }
+
+  // V-cycle with tile kernels on the levels above Lc (x ping-pongs between x and xa)
+  template <typename TO>
+  void vcycle_t(int l, bool x_zero, const T* rhs, TO* out, T* mx, cudaStream_t s) {
+    if (fused && l == Lc) {
+      launch_coarse_vcycle<T>(dim, ca, csmem, rhs, x_zero ? (const T*)nullptr : X(l), X(l), s);
+      return;
+    }
+    if (l + 1 == (int)lv.size()) {
+      launch_coarse_solve<T>(nc, coarse_inv, rhs, X(l), s);
+      return;
+    }
+    if (l == 0 && prof) prof->begin(PT_TPRE0, s);
+    launch_tile_pre<T>(ts[l], x_zero ? (const T*)nullptr : X(l), rhs, Xalt(l), lv[l + 1].b, s);
+    if (l == 0 && prof) prof->end(PT_TPRE0, s);
+    cur[l] ^= 1;
+    vcycle_t<T>(l + 1, true, lv[l + 1].b, (T*)nullptr, (T*)nullptr, s);
+    if (l == 0 && prof) prof->begin(PT_TPOST0, s);
+    launch_tile_post<T, TO>(ts[l], X(l), X(l + 1), rhs, Xalt(l), mx, out, (T)1, s);
+    if (l == 0 && prof) prof->end(PT_TPOST0, s);
+    cur[l] ^= 1;
+  }
+
+  template <typename TO>
+  void mg_solve_t(const T* rhs, TO* out, T* mx, cudaStream_t s) {
+    std::fill(cur.begin(), cur.end(), 0);
+    for (int c = 0; c < n_V; ++c) {
+      const bool last = c + 1 == n_V;
+      vcycle_t<TO>(0, c == 0, rhs, last ? out : (TO*)nullptr, last ? mx : (T*)nullptr, s);
+    }
+  }
+
+  template <typename TZ>
+  void apply_tiled(const double* v, TZ* z, cudaStream_t s) {
+    const long long nv = lv[0].g.nv;
+    if (prof) prof->begin(PT_TAMASS, s);
+    launch_tile_amass<T, TZ>(tm, v, z, lv[0].b, s);            // z1 = A~^{-1} r1, t = r2 - C z1
+    if (prof) prof->end(PT_TAMASS, s);
+    mg_solve_t<T>(lv[0].b, (T*)nullptr, b2, s);                  // b2 = M S_hat^{-1} t
+    mg_solve_t<TZ>(b2, z + nv, (T*)nullptr, s);                  // z2 = S_hat^{-1} b2
+  }
 
   template <typename TB, typename TO>
   void cheb(const Geom& g, const T* W, const T* dinv, const TB* b, bool x_zero, T* x, T* r, T* d0, T* d1,
@@ -256,6 +307,10 @@ template <typename T> struct Prec {
   // z = P^{-1} v  (v: 2 nv doubles; z: 2 nv of TZ)
   template <typename TZ>
   void apply(const double* v, TZ* z, cudaStream_t s) {
+    if (tiled) {
+      apply_tiled<TZ>(v, z, s);
+      return;
+    }
     const Geom& g = lv[0].g;
     const long long nv = g.nv;
     Level<T>& L0 = lv[0];
@@ -287,6 +342,7 @@ template <typename T> struct Prec {
 struct ok_grid {
   int dim = 0, n = 0;
   int device = 0;
+  int sms = 1;           // streaming multiprocessors of the device
   Geom g0;
   ok_params p;
   ok_opts o;
@@ -366,6 +422,7 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
     L.r = A.alloc<T>(nv);
     L.d0 = A.alloc<T>(nv);
     L.d1 = A.alloc<T>(nv);
+    L.xa = A.alloc<T>(nv);
     if (l == 0) {
       for (int i = 0; i < NCLASS * NOFF; ++i) tab[i] = (T)(hd * refM[i]);
       for (int c = 0; c < NCLASS; ++c) dv[c] = (T)(1.0 / (hd * refM[c * NOFF]));
@@ -419,7 +476,7 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
   size_t tot = 0;
   int Lc = nl;
   for (int l = nl - 1; l >= 0; --l) {
-    const size_t need = 5 * (size_t)P.lv[l].g.nv * sizeof(T);
+    const size_t need = (5 * (size_t)P.lv[l].g.nv + NCLASS * NOFF + NCLASS) * sizeof(T);
     if (tot + need > budget || nl - l > COARSE_MAXLEV) break;
     tot += need;
     Lc = l;
@@ -435,6 +492,13 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
       ca.dinv[i] = L.dinvS;
       ca.off[i] = off;
       off += 5 * L.g.nv;
+      ca.mul[i] = (unsigned)((0x100000000ull + L.g.n1 - 1) / L.g.n1);   // ceil(2^32 / (n+1))
+      const unsigned long long wI = L.g.n > 2 ? (unsigned long long)(L.g.n - 1) : 2ull;
+      ca.mulI[i] = (unsigned)((0x100000000ull + wI - 1) / wI);           // ceil(2^32 / (n-1))
+    }
+    for (int i = 0; i < ca.nlev; ++i) {          // table copies after the vectors
+      ca.toff[i] = off;
+      off += NCLASS * NOFF + NCLASS;
     }
     ca.Ainv = P.coarse_inv;
     ca.inv_th = (T)(1.0 / P.thS);
@@ -448,6 +512,44 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
     CK(prepare_coarse_vcycle<T>(dim, P.csmem));
     P.fused = true;
     P.Lc = Lc;
+  }
+  P.cur.assign(nl, 0);
+  // 2D tile kernels for the levels above the fused part (two smoothing steps,
+  // S~^{-1} form, at most 16 mass Chebyshev steps)
+  const int top = P.fused ? P.Lc : nl - 1;
+  // (the mass kernel is compiled for q_A = 10, the paper's ten Chebyshev steps)
+  if (G->o.tile_fine && dim == 2 && P.nu_pre == 2 && P.nu_post == 2 && P.k_R == 1 && P.q_A == 10 && top >= 1) {
+    P.ts.resize(nl);
+    for (int l = 0; l + 1 < nl; ++l) {
+      TileSmooth<T>& t = P.ts[l];
+      t.g = P.lv[l].g;
+      t.gc = P.lv[l + 1].g;
+      t.W = P.lv[l].WS;
+      t.dinv = P.lv[l].dinvS;
+      t.WM = P.WM;            // only used on level 0 (M x between the two S_hat solves)
+      t.inv_th = (T)(1.0 / P.thS);
+      t.c1 = (T)P.cS1[0];
+      t.c2 = (T)P.cS2[0];
+      // 32-wide tiles while they give at least two blocks per SM, else 16-wide
+      // (4x the blocks, about half the per-block latency, more redundant halo work)
+      const long long nb32 = (long long)((t.g.n1 + 31) / 32) * ((t.g.n1 + 31) / 32);
+      t.tile = nb32 >= 2 * G->sms ? 32 : 16;
+    }
+    TileMass<T>& m = P.tm;
+    m.g = P.lv[0].g;
+    m.WM = P.WM;
+    m.dinvM = P.dinvM;
+    m.coef = nullptr;         // set when the coefficient store is bound
+    m.q = P.q_A;
+    m.inv_th = (T)(1.0 / P.thM);
+    m.inv_a11 = (T)P.inv_a11;
+    for (int k = 0; k < 16; ++k) {
+      m.c1[k] = k < (int)P.cM1.size() ? (T)P.cM1[k] : (T)0;
+      m.c2[k] = k < (int)P.cM2.size() ? (T)P.cM2[k] : (T)0;
+    }
+    P.b2 = A.alloc<T>(P.lv[0].g.nv);
+    CK(prepare_tiles<T>(P.q_A));
+    P.tiled = true;
   }
 }
 
@@ -686,6 +788,7 @@ void ok_default_opts(ok_opts* o) {
   o->coarse_max = 4;
   o->use_graphs = 1;
   o->fuse_coarse = 1;
+  o->tile_fine = 1;
   o->gmres_rtol = 1e-10;
   o->newton_atol = 1e-10;
   o->newton_rtol = 0.0;
@@ -718,6 +821,7 @@ int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid
     G->p = *p;
     G->o = od;
     CK(cudaGetDevice(&G->device));
+    CK(cudaDeviceGetAttribute(&G->sms, cudaDevAttrMultiProcessorCount, G->device));
     G->g0 = make_geom(dim, n);
     G->n_levels = (int)sizes.size();
     const double h = 1.0 / n;
@@ -790,9 +894,11 @@ int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid
     if (od.precision == OK_MIXED) {
       build_prec<float>(G, G->pf, sizes, refM, refK);
       G->pf.coef = G->coef32;
+      G->pf.tm.coef = G->coef32;
     } else {
       build_prec<double>(G, G->pd, sizes, refM, refK);
       G->pd.coef = G->coef;
+      G->pd.tm.coef = G->coef;
     }
     G->graphs.assign(od.restart, nullptr);
     G->graph_kernels.assign(od.restart, 0);

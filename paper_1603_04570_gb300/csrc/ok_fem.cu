@@ -216,6 +216,49 @@ __device__ __forceinline__ T capply_at(const Geom& g, const Vtx<D>& v, const T* 
   return acc;
 }
 
+// The same sum from neighbour values already loaded (ys[o] = y at offset o,
+// converted once): no second load and no second float->double conversion.
+template <int D, typename T>
+__device__ __forceinline__ T capply_from(const Geom& g, const Vtx<D>& v, const T* __restrict__ coef,
+                                         const T (&ys)[Topo<D>::NOFF]) {
+  using Tp = Topo<D>;
+  T acc = coef[v.idx] * ys[0];
+  static_for<0, Tp::NPOS>([&](auto P) {
+    constexpr int p = decltype(P)::value;
+    constexpr int op = 2 * p + 1, om = 2 * p + 2;
+    if (nb_valid<D, op>(v.c)) acc = fma(coef[(1 + p) * g.nv + v.idx], ys[op], acc);
+    if (nb_valid<D, om>(v.c)) acc = fma(coef[(1 + p) * g.nv + v.idx + nb_delta<D, om>(g)], ys[om], acc);
+  });
+  return acc;
+}
+
+// float -> double without the float64 pipe (which runs at 1/58 of the float32
+// rate on this GPU): for normal numbers the IEEE-754 binary32 fields map to
+// binary64 by re-biasing the exponent (+1023-127) and widening the fraction;
+// zero, subnormals, inf and nan take the conversion instruction.  Exact.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned long long r = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)r);
+}
+
+template <int D, typename TX>
+__device__ __forceinline__ void load_nb_d(const TX* __restrict__ x, const Geom& g, const Vtx<D>& v,
+                                          double (&out)[Topo<D>::NOFF]) {
+  if constexpr (std::is_same<TX, float>::value) {
+    static_for<0, Topo<D>::NOFF>([&](auto O) {
+      constexpr int o = decltype(O)::value;
+      out[o] = nb_valid<D, o>(v.c) ? f2d_exact(x[v.idx + nb_delta<D, o>(g)]) : 0.0;
+    });
+  } else {
+    load_nb<D>(x, g, v, out);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // y = alpha J z + beta y0, J = [a11 M, dth K; C, M]  (eqn newton)
 // ---------------------------------------------------------------------------
@@ -228,10 +271,10 @@ __global__ void __launch_bounds__(128) k_apply_j(Geom g, const double* __restric
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   double z1[Tp::NOFF], z2[Tp::NOFF];
-  load_nb<D>(z, g, v, z1);
-  load_nb<D>(z + g.nv, g, v, z2);
+  load_nb_d<D, TZ>(z, g, v, z1);
+  load_nb_d<D, TZ>(z + g.nv, g, v, z2);
   double y1 = jc.a11hd * dot_w<D, Tp::NOFF>(WM, v.cls, z1) + jc.dthhk * dot_w<D, Tp::NAX>(WK, v.cls, z2);
-  double y2 = jc.hd * dot_w<D, Tp::NOFF>(WM, v.cls, z2) + capply_at<D, double>(g, v, coef, z, 1.0);
+  double y2 = jc.hd * dot_w<D, Tp::NOFF>(WM, v.cls, z2) + capply_from<D, double>(g, v, coef, z1);
   if (y0) {
     y1 = jc.beta * y0[v.idx] + jc.alpha * y1;
     y2 = jc.beta * y0[v.idx + g.nv] + jc.alpha * y2;

@@ -87,6 +87,9 @@ template <typename T> struct CoarseArgs {
   const T* W[COARSE_MAXLEV];         // S_hat weight tables (global)
   const T* dinv[COARSE_MAXLEV];
   long long off[COARSE_MAXLEV];      // element offset of the level's 5 vectors
+  long long toff[COARSE_MAXLEV];     // element offset of the level's W and dinv copies
+  unsigned mul[COARSE_MAXLEV];       // ceil(2^32 / (n+1)): i / (n+1) = umulhi(i, mul)
+  unsigned mulI[COARSE_MAXLEV];      // ceil(2^32 / (n-1)) for the interior vertices (n > 2)
   const T* Ainv;                     // coarsest dense inverse (global)
   T inv_th;                          // smoother 1/centre
   T c1[16], c2[16];                  // smoother coefficients per step
@@ -99,6 +102,37 @@ void launch_coarse_vcycle(int dim, const CoarseArgs<T>& a, size_t smem, const T*
 // allow `smem` bytes of dynamic shared memory for the fused kernel (call before capture)
 template <typename T>
 cudaError_t prepare_coarse_vcycle(int dim, size_t smem);
+
+// ---- shared-memory tile kernels, 2D (ok_tile.cu) -------------------------
+template <typename T> struct TileSmooth {
+  Geom g, gc;             // this level and the next coarser one
+  const T* W;             // S_hat table of this level
+  const T* dinv;
+  const T* WM;            // M table of this level (post kernel's optional M x)
+  T inv_th, c1, c2;       // smoother: 1/centre, coefficients of the middle step
+  int tile;               // owned vertices per tile side: 32, or 16 on small levels
+};
+template <typename T> struct TileMass {
+  Geom g;
+  const T* WM;            // M table (finest level)
+  const T* dinvM;
+  const T* coef;          // C = -eps^2 K - M_E coefficients, symmetric store
+  int q;                  // Chebyshev steps (halo width), 1..16
+  T inv_th, inv_a11;
+  T c1[16], c2[16];
+};
+// pre-smoothing (2 steps from x_in, or zero when x_in is null), restriction into bc
+template <typename T>
+void launch_tile_pre(const TileSmooth<T>& a, const T* x_in, const T* b, T* x_out, T* bc, cudaStream_t s);
+// x_out = post-smoothed (x_in + P xc); mx_out = M x_out (optional); out = oscale x_out (optional)
+template <typename T, typename TO>
+void launch_tile_post(const TileSmooth<T>& a, const T* x_in, const T* xc, const T* b, T* x_out, T* mx_out, TO* out,
+                      T oscale, cudaStream_t s);
+// z1 = A~^{-1} v1, t_out = v2 - C z1
+template <typename T, typename TZ>
+void launch_tile_amass(const TileMass<T>& a, const double* v, TZ* z1, T* t_out, cudaStream_t s);
+template <typename T>
+cudaError_t prepare_tiles(int q);
 
 // dense matrix of a level operator (row-major nv x nv) from its class table
 void launch_dense_from_table(int dim, const Geom& g, const double* W, double* A, cudaStream_t s);

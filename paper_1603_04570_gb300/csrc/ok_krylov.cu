@@ -44,7 +44,7 @@ int krylov_blocks() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g_blocks = sms > 0 ? 2 * sms : 256;
+    g_blocks = sms > 0 ? 4 * sms : 512;
     if (g_blocks > RED_MAX_BLOCKS) g_blocks = RED_MAX_BLOCKS;
   }
   return g_blocks;
@@ -88,80 +88,96 @@ __device__ __forceinline__ bool last_block(unsigned int* counter) {
   return last;
 }
 
+// Sum of the per-block partials of value k, by one warp: lane-strided over the
+// blocks, then an xor-shuffle tree (a fixed order, so results are reproducible).
+__device__ __forceinline__ double warp_sum_partials(const double* __restrict__ partials, int k) {
+  const int lane = threadIdx.x & 31;
+  double a = 0.0;
+  for (int b = lane; b < (int)gridDim.x; b += 32) a += partials[b * KRYLOV_MAX + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
+
 __device__ __forceinline__ void final_sums(const double* __restrict__ partials, int K, double* __restrict__ out) {
-  if (threadIdx.x < K) {
-    double a = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) a += partials[b * KRYLOV_MAX + threadIdx.x];
-    out[threadIdx.x] = a;
+  const int warp = threadIdx.x >> 5;
+  for (int k = warp; k < K; k += RT / 32) {
+    const double a = warp_sum_partials(partials, k);
+    if ((threadIdx.x & 31) == 0) out[k] = a;
   }
 }
 
-__global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ V, long long ldv, int K,
+// The multi-dot and update kernels take the number of basis vectors K
+// (<= KC) as a template argument, so that every V load of an element is
+// unconditional and can be in flight at once.
+template <int K>
+__global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ V, long long ldv,
                                                  const double* __restrict__ w, long long N,
                                                  double* __restrict__ partials, unsigned int* counter,
                                                  double* __restrict__ out) {
-  double acc[KC];
+  double acc[K];
 #pragma unroll
-  for (int k = 0; k < KC; ++k) acc[k] = 0.0;
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
     const double we = w[e];
 #pragma unroll
-    for (int k = 0; k < KC; ++k)
-      if (k < K) acc[k] = fma(V[k * ldv + e], we, acc[k]);
+    for (int k = 0; k < K; ++k) acc[k] = fma(V[k * ldv + e], we, acc[k]);
   }
-  block_partials<KC>(acc, K, partials);
+  block_partials<K>(acc, K, partials);
   if (last_block(counter)) final_sums(partials, K, out);
 }
 
-__global__ void __launch_bounds__(RT) k_update_multidot(const double* __restrict__ V, long long ldv, int K,
+template <int K>
+__global__ void __launch_bounds__(RT) k_update_multidot(const double* __restrict__ V, long long ldv,
                                                         const double* __restrict__ hin, double* __restrict__ w,
                                                         long long N, double* __restrict__ partials,
                                                         unsigned int* counter, double* __restrict__ out) {
-  __shared__ double hs[KC];
-  if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < K ? hin[threadIdx.x] : 0.0;
+  __shared__ double hs[K];
+  if (threadIdx.x < K) hs[threadIdx.x] = hin[threadIdx.x];
   __syncthreads();
-  double acc[KC];
+  double acc[K];
 #pragma unroll
-  for (int k = 0; k < KC; ++k) acc[k] = 0.0;
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
-    double vals[KC];
+    double vals[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) vals[k] = V[k * ldv + e];
     double we = w[e];
 #pragma unroll
-    for (int k = 0; k < KC; ++k)
-      if (k < K) {
-        vals[k] = V[k * ldv + e];
-        we = fma(-hs[k], vals[k], we);
-      }
+    for (int k = 0; k < K; ++k) we = fma(-hs[k], vals[k], we);
     w[e] = we;
 #pragma unroll
-    for (int k = 0; k < KC; ++k)
-      if (k < K) acc[k] = fma(vals[k], we, acc[k]);
+    for (int k = 0; k < K; ++k) acc[k] = fma(vals[k], we, acc[k]);
   }
-  block_partials<KC>(acc, K, partials);
+  block_partials<K>(acc, K, partials);
   if (last_block(counter)) final_sums(partials, K, out);
 }
 
-// w -= V h2 (h2 = ks->h2), ||w||^2; last block: column j of H, Givens, residual.
-__global__ void __launch_bounds__(RT) k_update_norm_givens(const double* __restrict__ V, long long ldv, int K,
+// w -= V h2 (h2 = ks->h2[K0..K0+K)), ||w||^2; last block: column j of H,
+// Givens rotations, residual estimate.
+template <int K>
+__global__ void __launch_bounds__(RT) k_update_norm_givens(const double* __restrict__ V, long long ldv,
                                                            double* __restrict__ w, long long N,
                                                            double* __restrict__ partials, unsigned int* counter,
                                                            KrylovState* ks, int j, int K0) {
-  __shared__ double hs[KC];
-  if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < K ? ks->h2[K0 + threadIdx.x] : 0.0;
+  __shared__ double hs[K];
+  if (threadIdx.x < K) hs[threadIdx.x] = ks->h2[K0 + threadIdx.x];
   __syncthreads();
   double acc[1] = {0.0};
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
+    double vals[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) vals[k] = V[k * ldv + e];
     double we = w[e];
 #pragma unroll
-    for (int k = 0; k < KC; ++k)
-      if (k < K) we = fma(-hs[k], V[k * ldv + e], we);
+    for (int k = 0; k < K; ++k) we = fma(-hs[k], vals[k], we);
     w[e] = we;
     acc[0] = fma(we, we, acc[0]);
   }
   block_partials<1>(acc, 1, partials);
-  if (last_block(counter) && threadIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += partials[b * KRYLOV_MAX];
+  if (!last_block(counter) || threadIdx.x >= 32) return;
+  const double s = warp_sum_partials(partials, 0);
+  if (threadIdx.x == 0) {
     const int ld = KRYLOV_MAX + 1;
     double* Hj = ks->H + (long long)ld * j;
     for (int i = 0; i <= j; ++i) Hj[i] = ks->h1[i] + ks->h2[i];
@@ -187,21 +203,33 @@ __global__ void __launch_bounds__(RT) k_update_norm_givens(const double* __restr
   }
 }
 
-// The second CGS2 pass may need several KC-vector chunks: the update kernel
-// above handles one chunk (K0 offset); when K > KC the host launches the
-// update chunks first and the norm/Givens only with the last chunk.
-__global__ void __launch_bounds__(RT) k_update_only(const double* __restrict__ V, long long ldv, int K,
+template <int K>
+__global__ void __launch_bounds__(RT) k_update_only(const double* __restrict__ V, long long ldv,
                                                     const double* __restrict__ h, double* __restrict__ w,
                                                     long long N) {
-  __shared__ double hs[KC];
-  if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < K ? h[threadIdx.x] : 0.0;
+  __shared__ double hs[K];
+  if (threadIdx.x < K) hs[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
+    double vals[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) vals[k] = V[k * ldv + e];
     double we = w[e];
 #pragma unroll
-    for (int k = 0; k < KC; ++k)
-      if (k < K) we = fma(-hs[k], V[k * ldv + e], we);
+    for (int k = 0; k < K; ++k) we = fma(-hs[k], vals[k], we);
     w[e] = we;
+  }
+}
+
+// run F.template operator()<K>() for the runtime K in 1..KC
+template <typename F>
+static void with_k(int K, F&& f) {
+  switch (K) {
+#define OK_K(k) case k: f(std::integral_constant<int, k>{}); break;
+    OK_K(1) OK_K(2) OK_K(3) OK_K(4) OK_K(5) OK_K(6) OK_K(7) OK_K(8)
+    OK_K(9) OK_K(10) OK_K(11) OK_K(12) OK_K(13) OK_K(14) OK_K(15) OK_K(16)
+#undef OK_K
+    default: break;
   }
 }
 
@@ -212,11 +240,9 @@ __global__ void __launch_bounds__(RT) k_sumsq(const double* __restrict__ x, long
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT)
     acc[0] = fma(x[e], x[e], acc[0]);
   block_partials<1>(acc, 1, partials);
-  if (last_block(counter) && threadIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += partials[b * KRYLOV_MAX];
-    *out = sqrt(s);
-  }
+  if (!last_block(counter) || threadIdx.x >= 32) return;
+  const double s = warp_sum_partials(partials, 0);
+  if (threadIdx.x == 0) *out = sqrt(s);
 }
 
 __global__ void __launch_bounds__(RT) k_scale_by(double* __restrict__ w, long long N,
@@ -287,20 +313,29 @@ __global__ void __launch_bounds__(RT) k_check_finite(const double* __restrict__ 
 void launch_multidot(const double* V, long long ldv, int K, const double* w, long long N, RedScratch rs,
                      double* out, cudaStream_t s) {
   for (int k0 = 0; k0 < K; k0 += KC) {
-    int kk = K - k0 < KC ? K - k0 : KC;
-    count_launch(), k_multidot<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, kk, w, N, rs.partials, rs.counter, out + k0);
+    const int kk = K - k0 < KC ? K - k0 : KC;
+    with_k(kk, [&](auto KK) {
+      count_launch(), k_multidot<decltype(KK)::value><<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, w, N,
+                                                                                    rs.partials, rs.counter, out + k0);
+    });
   }
 }
 
 void launch_update_multidot(const double* V, long long ldv, int K, const double* h_in, double* w, long long N,
                             RedScratch rs, double* h_out, cudaStream_t s) {
   if (K <= KC) {
-    count_launch(), k_update_multidot<<<krylov_blocks(), RT, 0, s>>>(V, ldv, K, h_in, w, N, rs.partials, rs.counter, h_out);
+    with_k(K, [&](auto KK) {
+      count_launch(), k_update_multidot<decltype(KK)::value><<<krylov_blocks(), RT, 0, s>>>(
+                          V, ldv, h_in, w, N, rs.partials, rs.counter, h_out);
+    });
     return;
   }
   for (int k0 = 0; k0 < K; k0 += KC) {   // all updates first, then the dots of the final w
-    int kk = K - k0 < KC ? K - k0 : KC;
-    count_launch(), k_update_only<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, kk, h_in + k0, w, N);
+    const int kk = K - k0 < KC ? K - k0 : KC;
+    with_k(kk, [&](auto KK) {
+      count_launch(), k_update_only<decltype(KK)::value><<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, h_in + k0,
+                                                                                       w, N);
+    });
   }
   launch_multidot(V, ldv, K, w, N, rs, h_out, s);
 }
@@ -310,10 +345,12 @@ void launch_update_norm_givens(const double* V, long long ldv, int K, double* w,
   int k0 = 0;
   for (; K - k0 > KC; k0 += KC) {
     // h2 lives in device memory inside ks; chunk offsets index it directly
-    count_launch(), k_update_only<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, KC, ks->h2 + k0, w, N);
+    count_launch(), k_update_only<KC><<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, ks->h2 + k0, w, N);
   }
-  count_launch(), k_update_norm_givens<<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, K - k0, w, N, rs.partials, rs.counter,
-                                                       ks, j, k0);
+  with_k(K - k0, [&](auto KK) {
+    count_launch(), k_update_norm_givens<decltype(KK)::value><<<krylov_blocks(), RT, 0, s>>>(
+                        V + k0 * ldv, ldv, w, N, rs.partials, rs.counter, ks, j, k0);
+  });
 }
 
 void launch_scale_by(double* w, long long N, const double* factor, cudaStream_t s) {

@@ -19,6 +19,7 @@
 // the second sum running over the same offsets +-b as the P1 stencil.
 #include "ok_internal.cuh"
 #include "ok_kernels.h"
+#include "ok_stencil.cuh"
 
 namespace okg {
 
@@ -26,96 +27,6 @@ static constexpr int BX = 128;
 
 static inline dim3 grid_of(int dim, const Geom& g) {
   return dim3((g.n1 + BX - 1) / BX, g.n1, dim == 3 ? g.n1 : 1);
-}
-
-// ---------------------------------------------------------------------------
-// per-vertex bodies, shared by the one-kernel-per-step path and the fused
-// coarse V-cycle below (explicit fma everywhere a product feeds a sum, so the
-// two paths round identically)
-// ---------------------------------------------------------------------------
-template <int D, typename T, typename TB>
-__device__ __forceinline__ void cheb_init_at(const Vtx<D>& v, const T* dinv, const TB* b, T bscale, T* r, T* d,
-                                             T inv_th) {
-  T rr = (T)b[v.idx] * bscale;
-  r[v.idx] = rr;
-  d[v.idx] = dinv[v.cls] * rr * inv_th;
-}
-
-template <int D, typename T>
-__device__ __forceinline__ void resid_init_at(const Geom& g, const Vtx<D>& v, const T* W, const T* dinv,
-                                              const T* b, const T* x, T* r, T* d, T inv_th) {
-  T xs[Topo<D>::NOFF];
-  load_nb<D>(x, g, v, xs);
-  T rr = b[v.idx] - dot_w<D, Topo<D>::NOFF>(W, v.cls, xs);
-  r[v.idx] = rr;
-  d[v.idx] = dinv[v.cls] * rr * inv_th;
-}
-
-template <int D, typename T>
-__device__ __forceinline__ void cheb_step_at(const Geom& g, const Vtx<D>& v, const T* W, const T* dinv, T* x,
-                                             T* r, const T* din, T* dout, T c1, T c2, bool first) {
-  T ds[Topo<D>::NOFF];
-  load_nb<D>(din, g, v, ds);
-  x[v.idx] = (first ? (T)0 : x[v.idx]) + ds[0];
-  T rr = r[v.idx] - dot_w<D, Topo<D>::NOFF>(W, v.cls, ds);
-  r[v.idx] = rr;
-  dout[v.idx] = fma(c1, ds[0], c2 * (dinv[v.cls] * rr));
-}
-
-template <int D, typename T, typename TO>
-__device__ __forceinline__ void cheb_last_at(const Geom& g, const Vtx<D>& v, const T* W, T* x, T* r,
-                                             const T* din, bool first, TO* out, T oscale) {
-  T xx;
-  if (r) {
-    T ds[Topo<D>::NOFF];
-    load_nb<D>(din, g, v, ds);
-    xx = (first ? (T)0 : x[v.idx]) + ds[0];
-    r[v.idx] = r[v.idx] - dot_w<D, Topo<D>::NOFF>(W, v.cls, ds);
-  } else {
-    xx = (first ? (T)0 : x[v.idx]) + din[v.idx];
-  }
-  x[v.idx] = xx;
-  if (out) out[v.idx] = (TO)(xx * oscale);
-}
-
-// v: coarse vertex (position p), gf: fine geometry
-template <int D, typename T>
-__device__ __forceinline__ void restrict_at(const Geom& gf, const Vtx<D>& v, const T* rf, T* bc) {
-  long long fc = 2LL * v.p[0] + gf.sy * (2LL * v.p[1]) + gf.sz * (2LL * v.p[2]);
-  T acc = (T)0;
-  static_for<1, Topo<D>::NOFF>([&](auto O) {
-    constexpr int o = decltype(O)::value;
-    if (nb_valid<D, o>(v.c)) acc += rf[fc + nb_delta<D, o>(gf)];
-  });
-  bc[v.idx] = fma((T)0.5, acc, rf[fc]);
-}
-
-// v: fine vertex, gc: coarse geometry
-template <int D, typename T>
-__device__ __forceinline__ void prolong_add_at(const Geom& gc, const Vtx<D>& v, T* xf, const T* xc) {
-  long long ci = 0, cj = 0;
-  bool mid = false;
-  const long long st[3] = {1, gc.sy, gc.sz};
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    ci += (long long)(v.p[a] >> 1) * st[a];
-    cj += (long long)((v.p[a] >> 1) + (v.p[a] & 1)) * st[a];
-    mid = mid || (v.p[a] & 1);
-  }
-  xf[v.idx] = mid ? fma((T)0.5, xc[ci] + xc[cj], xf[v.idx]) : xf[v.idx] + xc[ci];
-}
-
-// x[r] = sum_c A[r][c] b[c] for the rows of this warp (lane-strided, xor-reduced)
-template <typename T>
-__device__ __forceinline__ void coarse_rows(long long nc, const T* A, const T* b, T* x, int warp, int nw) {
-  const int lane = threadIdx.x & 31;
-  for (long long r = warp; r < nc; r += nw) {
-    T acc = (T)0;
-    for (long long c = lane; c < nc; c += 32) acc = fma(A[r * nc + c], b[c], acc);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) x[r] = acc;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -182,26 +93,74 @@ __global__ void __launch_bounds__(512) k_coarse_solve(long long nc, const T* __r
 // memory; the same sequence of steps as Prec::vcycle on the host, each step a
 // block-stride loop followed by __syncthreads().
 // ---------------------------------------------------------------------------
-template <int D, typename T>
-__device__ __forceinline__ void vertex_of_index(const Geom& g, long long idx, Vtx<D>& v) {
-  const long long n1 = g.n1;
-  v.idx = idx;
-  v.p[0] = (int)(idx % n1);
-  const long long rest = idx / n1;
-  v.p[1] = (int)(rest % n1);
-  v.p[2] = D == 3 ? (int)(rest / n1) : 0;
+// vertex record of linear index i (< 2^16) without division: i / (n+1) = umulhi(i, mul)
+template <int D>
+__device__ __forceinline__ void vertex_fast(const Geom& g, unsigned mul, int i, Vtx<D>& v) {
+  const int n1 = g.n1;
+  const int q = (int)__umulhi((unsigned)i, mul);
+  v.idx = i;
+  v.p[0] = i - q * n1;
+  if (D == 3) {
+    const int q2 = (int)__umulhi((unsigned)q, mul);
+    v.p[1] = q - q2 * n1;
+    v.p[2] = q2;
+  } else {
+    v.p[1] = q;
+    v.p[2] = 0;
+  }
   v.c[0] = axis_class(v.p[0], g.n);
   v.c[1] = axis_class(v.p[1], g.n);
   v.c[2] = D == 3 ? axis_class(v.p[2], g.n) : 1;
   v.cls = v.c[0] + 3 * v.c[1] + (D == 3 ? 9 * v.c[2] : 0);
 }
 
-#define OK_FOR_VERTICES(G, V, BODY)                                                   \
-  for (long long _i = threadIdx.x; _i < (G).nv; _i += blockDim.x) {                  \
+#define OK_FOR_VERTICES(L, G, V, BODY)                                               \
+  for (int _i = threadIdx.x; _i < (int)(G).nv; _i += blockDim.x) {                   \
     Vtx<D> V;                                                                        \
-    vertex_of_index<D, T>((G), _i, V);                                               \
+    vertex_fast<D>((G), a.mul[L], _i, V);                                            \
     BODY;                                                                            \
   }                                                                                  \
+  __syncthreads();
+
+// interior vertex number i (0 <= i < (n-1)^D): every class is the interior
+// one, known at compile time, so the stencil needs no validity tests
+template <int D>
+__device__ __forceinline__ void interior_vertex(const Geom& g, unsigned mulI, int i, Vtx<D>& v) {
+  const int w = g.n - 1;
+  const int q = (w == 1) ? i : (int)__umulhi((unsigned)i, mulI);
+  v.p[0] = i - q * w + 1;
+  if (D == 3) {
+    const int q2 = (w == 1) ? q : (int)__umulhi((unsigned)q, mulI);
+    v.p[1] = q - q2 * w + 1;
+    v.p[2] = q2 + 1;
+  } else {
+    v.p[1] = q + 1;
+    v.p[2] = 0;
+  }
+  v.idx = v.p[0] + g.sy * v.p[1] + g.sz * v.p[2];
+  v.c[0] = v.c[1] = v.c[2] = 1;
+  v.cls = D == 2 ? 4 : 13;
+}
+
+// BODY over all vertices: the interior ones first (fast path), then the
+// boundary ones; each vertex exactly once, then a barrier
+#define OK_FOR_SPLIT(L, G, V, BODY)                                                    \
+  {                                                                                    \
+    const int _w = (G).n - 1;                                                          \
+    const int _ni = D == 3 ? _w * _w * _w : _w * _w;                                   \
+    for (int _i = threadIdx.x; _i < _ni; _i += blockDim.x) {                           \
+      Vtx<D> V;                                                                        \
+      interior_vertex<D>((G), a.mulI[L], _i, V);                                       \
+      BODY;                                                                            \
+    }                                                                                  \
+    for (int _i = threadIdx.x; _i < (int)(G).nv; _i += blockDim.x) {                   \
+      Vtx<D> V;                                                                        \
+      vertex_fast<D>((G), a.mul[L], _i, V);                                            \
+      if (V.cls != (D == 2 ? 4 : 13)) {                                                \
+        BODY;                                                                          \
+      }                                                                                \
+    }                                                                                  \
+  }                                                                                    \
   __syncthreads();
 
 template <int D, typename T>
@@ -212,21 +171,21 @@ __device__ void fused_smooth(const CoarseArgs<T>& a, int l, T* sm, bool x_zero, 
   T* B = X + nv;
   T* R = B + nv;
   T* Dd[2] = {R + nv, R + 2 * nv};
-  const T* W = a.W[l];
-  const T* dv = a.dinv[l];
+  const T* W = sm + a.toff[l];                        // shared-memory copies of the tables
+  const T* dv = W + Topo<D>::NCLASS * Topo<D>::NOFF;
   if (x_zero) {
-    OK_FOR_VERTICES(g, v, (cheb_init_at<D, T, T>(v, dv, B, (T)1, R, Dd[0], a.inv_th)))
+    OK_FOR_SPLIT(l, g, v, (cheb_init_at<D, T, T>(v, dv, B, (T)1, R, Dd[0], a.inv_th)))
   } else {
-    OK_FOR_VERTICES(g, v, (resid_init_at<D, T>(g, v, W, dv, B, X, R, Dd[0], a.inv_th)))
+    OK_FOR_SPLIT(l, g, v, (resid_init_at<D, T>(g, v, W, dv, B, X, R, Dd[0], a.inv_th)))
   }
   int cur = 0;
   for (int k = 0; k + 1 < nu; ++k) {
     const bool first = x_zero && k == 0;
-    OK_FOR_VERTICES(g, v, (cheb_step_at<D, T>(g, v, W, dv, X, R, Dd[cur], Dd[1 - cur], a.c1[k], a.c2[k], first)))
+    OK_FOR_SPLIT(l, g, v, (cheb_step_at<D, T>(g, v, W, dv, X, R, Dd[cur], Dd[1 - cur], a.c1[k], a.c2[k], first)))
     cur ^= 1;
   }
   const bool first = x_zero && nu == 1;
-  OK_FOR_VERTICES(g, v, (cheb_last_at<D, T, T>(g, v, W, X, want_r ? R : (T*)nullptr, Dd[cur], first, (T*)nullptr,
+  OK_FOR_SPLIT(l, g, v, (cheb_last_at<D, T, T>(g, v, W, X, want_r ? R : (T*)nullptr, Dd[cur], first, (T*)nullptr,
                                                (T)1)))
 }
 
@@ -239,10 +198,33 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseArgs<T> a, const T
   {
     T* X0 = sm + a.off[0];
     T* B0 = X0 + a.g[0].nv;
-    for (long long i = threadIdx.x; i < a.g[0].nv; i += blockDim.x) {
+    // loads first (all in flight), then the shared-memory stores; the fused
+    // part holds at most 200 KB / (5 * 4 B) = 10240 vertices on level 0
+    const int nv0 = (int)a.g[0].nv;
+    constexpr int NL = 10;
+    T br[NL], xr[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int i = threadIdx.x + k * 1024;
+      br[k] = i < nv0 ? b_in[i] : (T)0;
+      xr[k] = (x_in && i < nv0) ? x_in[i] : (T)0;
+    }
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int i = threadIdx.x + k * 1024;
+      if (i < nv0) {
+        B0[i] = br[k];
+        if (x_in) X0[i] = xr[k];
+      }
+    }
+    for (int i = threadIdx.x + NL * 1024; i < nv0; i += blockDim.x) {   // (not reached with the budget above)
       B0[i] = b_in[i];
       if (x_in) X0[i] = x_in[i];
     }
+    constexpr int NT = Topo<D>::NCLASS * Topo<D>::NOFF;
+    for (int l = 0; l <= L; ++l)
+      for (int i = threadIdx.x; i < NT + Topo<D>::NCLASS; i += blockDim.x)
+        sm[a.toff[l] + i] = i < NT ? a.W[l][i] : a.dinv[l][i - NT];
     __syncthreads();
   }
   // descend
@@ -251,7 +233,7 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseArgs<T> a, const T
     const Geom& gc = a.g[l + 1];
     T* Rf = sm + a.off[l] + 2 * a.g[l].nv;
     T* Bc = sm + a.off[l + 1] + gc.nv;
-    OK_FOR_VERTICES(gc, v, (restrict_at<D, T>(a.g[l], v, Rf, Bc)))
+    OK_FOR_SPLIT(l + 1, gc, v, (restrict_at<D, T>(a.g[l], v, Rf, Bc)))
   }
   // coarsest: exact
   {
@@ -264,7 +246,7 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseArgs<T> a, const T
     const Geom& g = a.g[l];
     T* Xf = sm + a.off[l];
     const T* Xc = sm + a.off[l + 1];
-    OK_FOR_VERTICES(g, v, (prolong_add_at<D, T>(a.g[l + 1], v, Xf, Xc)))
+    OK_FOR_VERTICES(l, g, v, (prolong_add_at<D, T>(a.g[l + 1], v, Xf, Xc)))
     fused_smooth<D, T>(a, l, sm, false, a.nu_post, false);
   }
   for (long long i = threadIdx.x; i < a.g[0].nv; i += blockDim.x) x_out[i] = sm[a.off[0] + i];

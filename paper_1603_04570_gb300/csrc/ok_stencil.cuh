@@ -1,0 +1,113 @@
+// ok_stencil.cuh -- per-vertex bodies of the Chebyshev, transfer and coarse
+// steps, shared by every kernel that performs them (one kernel per step, the
+// fused coarse V-cycle, the shared-memory tile kernels), so that all paths
+// take the same arithmetic in the same order and round identically.  Every
+// product that feeds a sum is an explicit fma.
+#pragma once
+
+#include "ok_internal.cuh"
+
+namespace okg {
+
+template <int D, typename T, typename TB>
+__device__ __forceinline__ void cheb_init_at(const Vtx<D>& v, const T* dinv, const TB* b, T bscale, T* r, T* d,
+                                             T inv_th) {
+  T rr = (T)b[v.idx] * bscale;
+  r[v.idx] = rr;
+  d[v.idx] = dinv[v.cls] * rr * inv_th;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void resid_init_at(const Geom& g, const Vtx<D>& v, const T* W, const T* dinv,
+                                              const T* b, const T* x, T* r, T* d, T inv_th) {
+  T xs[Topo<D>::NOFF];
+  load_nb<D>(x, g, v, xs);
+  T rr = b[v.idx] - dot_w<D, Topo<D>::NOFF>(W, v.cls, xs);
+  r[v.idx] = rr;
+  d[v.idx] = dinv[v.cls] * rr * inv_th;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void cheb_step_at(const Geom& g, const Vtx<D>& v, const T* W, const T* dinv, T* x,
+                                             T* r, const T* din, T* dout, T c1, T c2, bool first) {
+  T ds[Topo<D>::NOFF];
+  load_nb<D>(din, g, v, ds);
+  x[v.idx] = (first ? (T)0 : x[v.idx]) + ds[0];
+  T rr = r[v.idx] - dot_w<D, Topo<D>::NOFF>(W, v.cls, ds);
+  r[v.idx] = rr;
+  dout[v.idx] = fma(c1, ds[0], c2 * (dinv[v.cls] * rr));
+}
+
+template <int D, typename T, typename TO>
+__device__ __forceinline__ void cheb_last_at(const Geom& g, const Vtx<D>& v, const T* W, T* x, T* r,
+                                             const T* din, bool first, TO* out, T oscale) {
+  T xx;
+  if (r) {
+    T ds[Topo<D>::NOFF];
+    load_nb<D>(din, g, v, ds);
+    xx = (first ? (T)0 : x[v.idx]) + ds[0];
+    r[v.idx] = r[v.idx] - dot_w<D, Topo<D>::NOFF>(W, v.cls, ds);
+  } else {
+    xx = (first ? (T)0 : x[v.idx]) + din[v.idx];
+  }
+  x[v.idx] = xx;
+  if (out) out[v.idx] = (TO)(xx * oscale);
+}
+
+// v: coarse vertex (position p), gf: fine geometry
+template <int D, typename T>
+__device__ __forceinline__ void restrict_at(const Geom& gf, const Vtx<D>& v, const T* rf, T* bc) {
+  long long fc = 2LL * v.p[0] + gf.sy * (2LL * v.p[1]) + gf.sz * (2LL * v.p[2]);
+  T acc = (T)0;
+  static_for<1, Topo<D>::NOFF>([&](auto O) {
+    constexpr int o = decltype(O)::value;
+    if (nb_valid<D, o>(v.c)) acc += rf[fc + nb_delta<D, o>(gf)];
+  });
+  bc[v.idx] = fma((T)0.5, acc, rf[fc]);
+}
+
+// v: fine vertex, gc: coarse geometry
+template <int D, typename T>
+__device__ __forceinline__ void prolong_add_at(const Geom& gc, const Vtx<D>& v, T* xf, const T* xc) {
+  long long ci = 0, cj = 0;
+  bool mid = false;
+  const long long st[3] = {1, gc.sy, gc.sz};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    ci += (long long)(v.p[a] >> 1) * st[a];
+    cj += (long long)((v.p[a] >> 1) + (v.p[a] & 1)) * st[a];
+    mid = mid || (v.p[a] & 1);
+  }
+  xf[v.idx] = mid ? fma((T)0.5, xc[ci] + xc[cj], xf[v.idx]) : xf[v.idx] + xc[ci];
+}
+
+// x[r] = sum_c A[r][c] b[c] for the rows of this warp (lane-strided, xor-reduced)
+template <typename T>
+__device__ __forceinline__ void coarse_rows(long long nc, const T* A, const T* b, T* x, int warp, int nw) {
+  const int lane = threadIdx.x & 31;
+  for (long long r = warp; r < nc; r += nw) {
+    T acc = (T)0;
+    for (long long c = lane; c < nc; c += 32) acc = fma(A[r * nc + c], b[c], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) x[r] = acc;
+  }
+}
+
+// vertex data from a linear index (block-stride loops)
+template <int D, typename T>
+__device__ __forceinline__ void vertex_of_index(const Geom& g, long long idx, Vtx<D>& v) {
+  const long long n1 = g.n1;
+  v.idx = idx;
+  v.p[0] = (int)(idx % n1);
+  const long long rest = idx / n1;
+  v.p[1] = (int)(rest % n1);
+  v.p[2] = D == 3 ? (int)(rest / n1) : 0;
+  v.c[0] = axis_class(v.p[0], g.n);
+  v.c[1] = axis_class(v.p[1], g.n);
+  v.c[2] = D == 3 ? axis_class(v.p[2], g.n) : 1;
+  v.cls = v.c[0] + 3 * v.c[1] + (D == 3 ? 9 * v.c[2] : 0);
+}
+
+
+}  // namespace okg

@@ -40,7 +40,7 @@ def test_default_opts_match_header_documentation():
     assert (o.restart, o.q_A, o.n_V, o.k_R, o.smooth_pre, o.smooth_post) == (30, 10, 5, 1, 2, 2)
     assert o.precision == ok.OK_FP64 and o.gmres_rtol == 1e-10 and o.smooth_lo_frac == 0.25
     assert o.use_graphs == 1 and o.fuse_coarse == 1
-    assert ok.Opts.gmres_rtol.offset == 56 and ctypes.sizeof(ok.Opts) == 88   # 13 ints, pad, 4 doubles
+    assert ok.Opts.gmres_rtol.offset == 56 and ctypes.sizeof(ok.Opts) == 88   # 14 ints, 4 doubles
 
 
 @pytest.mark.parametrize("dim,n,kw,msg", [

@@ -242,12 +242,15 @@ def test_batch_runs_each_request():
         assert reqs[1].newton_its >= 3
 
 
-def test_profiling_samples_and_launch_count():
+@pytest.mark.parametrize("tile", [0, 1])
+def test_profiling_samples_and_launch_count(tile):
     # 128^2: the finest level is not part of the fused coarse kernel, so every
-    # sampled kernel class occurs once per Arnoldi step
+    # sampled kernel class of the path occurs once per Arnoldi step
     wl = oi.scaled(oi.SMALL_2D, 128)
     u0 = oi.initial_u(wl)
-    with ok.Grid(2, 128, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt) as g:
+    names = ("precond", "apply_j", "cgs2") + (("mg_tile_pre_l0", "mg_tile_post_l0", "tile_mass_cstep") if tile
+                                             else ("mg_smooth_l0", "cheb_mass_step"))
+    with ok.Grid(2, 128, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, tile_fine=tile) as g:
         u, w = dev(u0), torch.zeros(g.nv, dtype=torch.float64, device="cuda")
         g.init_w(u, w)
         ok.ok_profile(g.handle, True)
@@ -256,7 +259,7 @@ def test_profiling_samples_and_launch_count():
         launched = ok.ok_launch_count() - l0
         stats = ok.ok_profile_read(g.handle)
         ok.ok_profile(g.handle, False)
-        for name in ("precond", "apply_j", "cgs2", "mg_smooth_l0", "cheb_mass_step"):
+        for name in names:
             n, ms = stats[name]
             assert n == info.gmres_its and ms > 0, name
         assert launched > 20 * info.gmres_its        # preconditioner + Arnoldi kernels per iteration
@@ -274,6 +277,25 @@ def test_fused_coarse_vcycle_is_bitwise_identical(dim, n, precision):
     out = []
     for fuse in (0, 1):
         with ok.Grid(dim, n, **p, n_V=2, precision=precision, fuse_coarse=fuse) as g:
+            z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+            g.apply_preconditioner(u, v, z)
+            out.append(host(z))
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("n", [100, 160, 256])
+@pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
+def test_tile_kernels_are_bitwise_identical(n, precision):
+    """2D shared-memory tile kernels (temporal blocking with redundant halos)
+    against the one-kernel-per-step path: same arithmetic, same bits.  n = 100
+    gives ragged tiles (101 vertices per row, 32-wide tiles)."""
+    sysm, p, rng = make(2, n, seed=6, dt=1e-4)
+    nv = sysm.mesh.nv
+    u = dev(rng.uniform(-1.0, 1.0, nv))
+    v = dev(rng.standard_normal(2 * nv))
+    out = []
+    for tile in (0, 1):
+        with ok.Grid(2, n, **p, precision=precision, tile_fine=tile) as g:
             z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
             g.apply_preconditioner(u, v, z)
             out.append(host(z))
