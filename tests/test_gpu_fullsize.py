@@ -1,0 +1,119 @@
+"""Full-size checks at the benchmark's workloads, through the C ABI.
+
+The oracle cannot take whole timesteps at 2.1M/4.3M DoF in seconds, so these
+use what it can compute at any size:
+  * 2D 1024^2 (the timed workload): the oracle's own residual F(u1, w1) of the
+    GPU timestep, the mean-relaxation law, the w0 projection residual, and
+    sampled rows of J z against the oracle's CSR Jacobian;
+  * 3D 128^3 Kuhn: the mean law with the lumped vertex masses, agreement of the
+    mixed and float64 paths, convergence;
+  * both: mixed precision within 1e-8 of float64 (the method's target).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import ok_inputs as oi
+import paper_1603_04570_gb300 as ok
+
+pytestmark = pytest.mark.gpu
+
+
+def _grid(wl, precision):
+    atol, rtol = wl.newton_tols
+    return ok.Grid(wl.dim, wl.n, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, restart=wl.restart,
+                   gmres_rtol=wl.gmres_rtol, newton_atol=atol, newton_rtol=rtol, precision=precision)
+
+
+def _lumped_mass(dim, n):
+    """1^T M per vertex = |T|/(d+1) x (simplices at the vertex), for the
+    uniform meshes: count incident simplices from the cell structure."""
+    n1 = n + 1
+    if dim == 2:
+        inc = np.zeros((n1, n1))
+        # each cell contributes 2 triangles at its (0,0) and (1,1) corners, 1 at (1,0) and (0,1)
+        inc[:-1, :-1] += 2
+        inc[1:, 1:] += 2
+        inc[:-1, 1:] += 1
+        inc[1:, :-1] += 1
+        return inc.ravel() * (1.0 / n) ** 2 / 2 / 3        # index [j, i] -> j*(n+1)+i, x fastest
+    inc = np.zeros((n1, n1, n1))
+    # Kuhn: 6 tets at corners 000 and 111 of each cube, 2 at each of the other six
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                k = 6 if (cx, cy, cz) in ((0, 0, 0), (1, 1, 1)) else 2
+                inc[cz:n + cz, cy:n + cy, cx:n + cx] += k
+    return inc.ravel() * (1.0 / n) ** 3 / 6 / 4
+
+
+def _mean_law(wl, u0, u1, lm):
+    ub0, ub1 = lm @ u0, lm @ u1
+    lhs = (ub1 - wl.m) * (1 + wl.dt * wl.theta * wl.sigma)
+    rhs = (ub0 - wl.m) * (1 - wl.dt * (1 - wl.theta) * wl.sigma)
+    return abs(lhs - rhs) / max(abs(rhs), 1e-300)
+
+
+def test_large_2d_timestep_against_oracle_properties():
+    from oracle.fem import Mesh, Params, System, nonlinear_term
+    wl = oi.LARGE_2D
+    sysm = System(Mesh(wl.dim, wl.n), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
+    nv = sysm.mesh.nv
+    u0 = oi.initial_u(wl)
+    res = {}
+    for prec in (ok.OK_MIXED, ok.OK_FP64):
+        with _grid(wl, prec) as g:
+            u = torch.from_numpy(u0.copy()).cuda()
+            w = torch.empty_like(u)
+            g.init_w(u, w)
+            w0 = w.cpu().numpy()
+            info = g.timestep(u, w)
+            assert info.converged and info.rel_resid <= wl.gmres_rtol
+            res[prec] = (u.cpu().numpy(), w.cpu().numpy(), w0, info)
+            if prec == ok.OK_MIXED:                      # sampled Jacobian rows at full size
+                rng = np.random.default_rng(0)
+                z = rng.standard_normal(2 * nv)
+                y = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+                g.apply_jacobian(torch.from_numpy(u0.copy()).cuda(), torch.from_numpy(z).cuda(), y)
+                J = sysm.jacobian(u0)
+                rows = rng.choice(2 * nv, 4000, replace=False)
+                ref = J[rows] @ z
+                scale = abs(J[rows]) @ np.abs(z)
+                assert (np.abs(y.cpu().numpy()[rows] - ref) <= 1e-13 * scale.max()).all()
+    u1, w1, w0, info = res[ok.OK_MIXED]
+    # w0 solves the okb projection M w0 = eps^2 K u0 + N(u0)
+    rhs = wl.eps ** 2 * (sysm.K @ u0) + nonlinear_term(sysm.mesh, u0)
+    assert np.linalg.norm(sysm.M @ w0 - rhs) <= 1e-12 * np.linalg.norm(rhs)
+    # the oracle's residual of the GPU timestep
+    F = sysm.residual(u0, w0, u1, w1)
+    atol, rtol = wl.newton_tols
+    assert np.linalg.norm(F) <= 10 * max(atol, rtol * info.newton_resid0)
+    # mean relaxation (Sec. 1 eqn oka integrated over the domain)
+    assert _mean_law(wl, u0, u1, np.ones(nv) @ sysm.M) <= 1e-9
+    # mixed within 1e-8 of float64
+    uf, wf = res[ok.OK_FP64][:2]
+    assert np.linalg.norm(u1 - uf) <= 1e-8 * np.linalg.norm(uf)
+    assert np.linalg.norm(w1 - wf) <= 1e-8 * np.linalg.norm(wf)
+
+
+def test_cube_128_timestep_properties():
+    wl = oi.CUBE_128
+    u0 = oi.initial_u(wl)
+    lm = _lumped_mass(3, wl.n)
+    assert abs(lm.sum() - 1.0) < 1e-12                    # the lumped masses total |Omega|
+    out = {}
+    for prec in (ok.OK_MIXED, ok.OK_FP64):
+        with _grid(wl, prec) as g:
+            u = torch.from_numpy(u0.copy()).cuda()
+            w = torch.empty_like(u)
+            g.init_w(u, w)
+            info = g.timestep(u, w)
+            assert info.converged and info.rel_resid <= wl.gmres_rtol
+            out[prec] = (u.cpu().numpy(), w.cpu().numpy(), info)
+    u1, w1, info = out[ok.OK_MIXED]
+    assert _mean_law(wl, u0, u1, lm) <= 1e-9
+    uf, wf, infof = out[ok.OK_FP64]
+    assert np.linalg.norm(u1 - uf) <= 1e-8 * np.linalg.norm(uf)
+    assert np.linalg.norm(w1 - wf) <= 1e-8 * np.linalg.norm(wf)
+    assert info.gmres_its <= 3 * infof.gmres_its + 10     # mixed does not lose the preconditioner
