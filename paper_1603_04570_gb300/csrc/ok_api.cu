@@ -473,11 +473,19 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
   // shared memory (at most COARSE_MAXLEV levels); worth it from two levels on
   const int nl = (int)P.lv.size();
   const size_t budget = 200 * 1024;
+  // 2D tile kernels need two smoothing steps, the S~^{-1} form and the
+  // ten-step mass solve they are compiled for (the paper's ten Chebyshev steps)
+  const bool tiles_ok =
+      G->o.tile_fine && dim == 2 && P.nu_pre == 2 && P.nu_post == 2 && P.k_R == 1 && P.q_A == 10;
   size_t tot = 0;
   int Lc = nl;
   for (int l = nl - 1; l >= 0; --l) {
     const size_t need = (5 * (size_t)P.lv[l].g.nv + NCLASS * NOFF + NCLASS) * sizeof(T);
-    if (tot + need > budget || nl - l > COARSE_MAXLEV) break;
+    // one SM issues the whole fused part: keep its largest level small
+    // (<= 1200 vertices, 33^2 in 2D, 9^3 in 3D) when a multi-block path exists
+    // for the levels above it (the 2D tile kernels)
+    const bool small_enough = P.lv[l].g.nv <= 1200 || !tiles_ok;
+    if (tot + need > budget || nl - l > COARSE_MAXLEV || !small_enough) break;
     tot += need;
     Lc = l;
   }
@@ -518,7 +526,7 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
   // S~^{-1} form, at most 16 mass Chebyshev steps)
   const int top = P.fused ? P.Lc : nl - 1;
   // (the mass kernel is compiled for q_A = 10, the paper's ten Chebyshev steps)
-  if (G->o.tile_fine && dim == 2 && P.nu_pre == 2 && P.nu_post == 2 && P.k_R == 1 && P.q_A == 10 && top >= 1) {
+  if (tiles_ok && top >= 1) {
     P.ts.resize(nl);
     for (int l = 0; l + 1 < nl; ++l) {
       TileSmooth<T>& t = P.ts[l];

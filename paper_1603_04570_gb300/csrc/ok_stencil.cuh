@@ -94,6 +94,75 @@ __device__ __forceinline__ void coarse_rows(long long nc, const T* A, const T* b
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same bodies with one class's weights held in registers (vertices all of
+// that class, e.g. the interior of a tile): identical arithmetic and order.
+// ---------------------------------------------------------------------------
+template <int D, typename T> struct RegW {
+  T w[Topo<D>::NOFF];
+  T dinv;
+};
+
+template <int D, typename T>
+__device__ __forceinline__ RegW<D, T> reg_weights(const T* W, const T* dinv, int cls) {
+  RegW<D, T> r;
+#pragma unroll
+  for (int o = 0; o < Topo<D>::NOFF; ++o) r.w[o] = W[cls * Topo<D>::NOFF + o];
+  r.dinv = dinv[cls];
+  return r;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ T dot_r(const RegW<D, T>& rw, const T (&xs)[Topo<D>::NOFF]) {
+  T acc = rw.w[0] * xs[0];
+#pragma unroll
+  for (int o = 1; o < Topo<D>::NOFF; ++o) acc = fma(rw.w[o], xs[o], acc);
+  return acc;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void cheb_init_r(const Vtx<D>& v, const RegW<D, T>& rw, const T* b, T* r, T* d, T inv_th) {
+  T rr = b[v.idx] * (T)1;
+  r[v.idx] = rr;
+  d[v.idx] = rw.dinv * rr * inv_th;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void resid_init_r(const Geom& g, const Vtx<D>& v, const RegW<D, T>& rw, const T* b,
+                                             const T* x, T* r, T* d, T inv_th) {
+  T xs[Topo<D>::NOFF];
+  load_nb<D>(x, g, v, xs);
+  T rr = b[v.idx] - dot_r<D, T>(rw, xs);
+  r[v.idx] = rr;
+  d[v.idx] = rw.dinv * rr * inv_th;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void cheb_step_r(const Geom& g, const Vtx<D>& v, const RegW<D, T>& rw, T* x, T* r,
+                                            const T* din, T* dout, T c1, T c2, bool first) {
+  T ds[Topo<D>::NOFF];
+  load_nb<D>(din, g, v, ds);
+  x[v.idx] = (first ? (T)0 : x[v.idx]) + ds[0];
+  T rr = r[v.idx] - dot_r<D, T>(rw, ds);
+  r[v.idx] = rr;
+  dout[v.idx] = fma(c1, ds[0], c2 * (rw.dinv * rr));
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void cheb_last_r(const Geom& g, const Vtx<D>& v, const RegW<D, T>& rw, T* x, T* r,
+                                            const T* din, bool first) {
+  T xx;
+  if (r) {
+    T ds[Topo<D>::NOFF];
+    load_nb<D>(din, g, v, ds);
+    xx = (first ? (T)0 : x[v.idx]) + ds[0];
+    r[v.idx] = r[v.idx] - dot_r<D, T>(rw, ds);
+  } else {
+    xx = (first ? (T)0 : x[v.idx]) + din[v.idx];
+  }
+  x[v.idx] = xx;
+}
+
 // vertex data from a linear index (block-stride loops)
 template <int D, typename T>
 __device__ __forceinline__ void vertex_of_index(const Geom& g, long long idx, Vtx<D>& v) {

@@ -134,11 +134,24 @@ __device__ __forceinline__ void tile_pre_body(const TileSmooth<T>& a, const Fram
   }
   __syncthreads();
   const Geom& lg = F.lg;
-  if (xz) tile_loop<TL, S, 1, S - 1, INT>(F, [&](const Vtx<2>& v) { cheb_init_at<2, T, T>(v, sD, B, (T)1, R, D0, a.inv_th); });
-  else tile_loop<TL, S, 1, S - 1, INT>(F, [&](const Vtx<2>& v) { resid_init_at<2, T>(lg, v, sW, sD, B, X, R, D0, a.inv_th); });
-  tile_loop<TL, S, 2, S - 2, INT>(F, [&](const Vtx<2>& v) { cheb_step_at<2, T>(lg, v, sW, sD, X, R, D0, D1, a.c1, a.c2, xz); });
+  const RegW<2, T> rw = reg_weights<2, T>(sW, sD, 4);   // interior class, used when INT
+  if (xz)
+    tile_loop<TL, S, 1, S - 1, INT>(F, [&](const Vtx<2>& v) {
+      if constexpr (INT) cheb_init_r<2, T>(v, rw, B, R, D0, a.inv_th);
+      else cheb_init_at<2, T, T>(v, sD, B, (T)1, R, D0, a.inv_th);
+    });
+  else
+    tile_loop<TL, S, 1, S - 1, INT>(F, [&](const Vtx<2>& v) {
+      if constexpr (INT) resid_init_r<2, T>(lg, v, rw, B, X, R, D0, a.inv_th);
+      else resid_init_at<2, T>(lg, v, sW, sD, B, X, R, D0, a.inv_th);
+    });
+  tile_loop<TL, S, 2, S - 2, INT>(F, [&](const Vtx<2>& v) {
+    if constexpr (INT) cheb_step_r<2, T>(lg, v, rw, X, R, D0, D1, a.c1, a.c2, xz);
+    else cheb_step_at<2, T>(lg, v, sW, sD, X, R, D0, D1, a.c1, a.c2, xz);
+  });
   tile_loop<TL, S, 3, S - 3, INT>(F, [&](const Vtx<2>& v) {
-    cheb_last_at<2, T, T>(lg, v, sW, X, R, D1, false, (T*)nullptr, (T)1);
+    if constexpr (INT) cheb_last_r<2, T>(lg, v, rw, X, R, D1, false);
+    else cheb_last_at<2, T, T>(lg, v, sW, X, R, D1, false, (T*)nullptr, (T)1);
   });
   // restriction for the coarse vertices whose fine centre this block owns
   const int nc = a.gc.n;
@@ -218,10 +231,18 @@ __device__ __forceinline__ void tile_post_body(const TileSmooth<T>& a, const Fra
   }
   __syncthreads();
   const Geom& lg = F.lg;
-  tile_loop<TL, S, 1, S - 1, INT>(F, [&](const Vtx<2>& v) { resid_init_at<2, T>(lg, v, sW, sD, B, X, R, D0, a.inv_th); });
-  tile_loop<TL, S, 2, S - 2, INT>(F, [&](const Vtx<2>& v) { cheb_step_at<2, T>(lg, v, sW, sD, X, R, D0, D1, a.c1, a.c2, false); });
+  const RegW<2, T> rw = reg_weights<2, T>(sW, sD, 4);   // interior class, used when INT
+  tile_loop<TL, S, 1, S - 1, INT>(F, [&](const Vtx<2>& v) {
+    if constexpr (INT) resid_init_r<2, T>(lg, v, rw, B, X, R, D0, a.inv_th);
+    else resid_init_at<2, T>(lg, v, sW, sD, B, X, R, D0, a.inv_th);
+  });
   tile_loop<TL, S, 2, S - 2, INT>(F, [&](const Vtx<2>& v) {
-    cheb_last_at<2, T, T>(lg, v, sW, X, (T*)nullptr, D1, false, (T*)nullptr, (T)1);
+    if constexpr (INT) cheb_step_r<2, T>(lg, v, rw, X, R, D0, D1, a.c1, a.c2, false);
+    else cheb_step_at<2, T>(lg, v, sW, sD, X, R, D0, D1, a.c1, a.c2, false);
+  });
+  tile_loop<TL, S, 2, S - 2, INT>(F, [&](const Vtx<2>& v) {
+    if constexpr (INT) cheb_last_r<2, T>(lg, v, rw, X, (T*)nullptr, D1, false);
+    else cheb_last_at<2, T, T>(lg, v, sW, X, (T*)nullptr, D1, false, (T*)nullptr, (T)1);
   });
   tile_loop<TL, S, Frame<TL, S>::H, Frame<TL, S>::H + TL, INT>(F, [&](const Vtx<2>& v) {
     const long long gi = gidx(F, v);
@@ -288,19 +309,25 @@ __device__ __forceinline__ void tile_amass_body(const TileMass<T>& a, const Fram
   }
   __syncthreads();
   const Geom& lg = F.lg;
-  tile_loop<TILE, S, 0, S, INT>(F, [&](const Vtx<2>& w) { cheb_init_at<2, T, T>(w, sD, B, (T)1, R, D0, a.inv_th); });
+  const RegW<2, T> rw = reg_weights<2, T>(sW, sD, 4);   // interior class, used when INT
+  tile_loop<TILE, S, 0, S, INT>(F, [&](const Vtx<2>& w) {
+    if constexpr (INT) cheb_init_r<2, T>(w, rw, B, R, D0, a.inv_th);
+    else cheb_init_at<2, T, T>(w, sD, B, (T)1, R, D0, a.inv_th);
+  });
   T* Dd[2] = {D0, D1};
   static_for<0, Q - 1>([&](auto Kc) {
     constexpr int k = decltype(Kc)::value;
     T* din = Dd[k & 1];
     T* dout = Dd[(k + 1) & 1];
     tile_loop<TILE, S, k + 1, S - k - 1, INT>(F, [&](const Vtx<2>& w) {
-      cheb_step_at<2, T>(lg, w, sW, sD, X, R, din, dout, a.c1[k], a.c2[k], k == 0);
+      if constexpr (INT) cheb_step_r<2, T>(lg, w, rw, X, R, din, dout, a.c1[k], a.c2[k], k == 0);
+      else cheb_step_at<2, T>(lg, w, sW, sD, X, R, din, dout, a.c1[k], a.c2[k], k == 0);
     });
   });
   T* dl = Dd[(Q - 1) & 1];
   tile_loop<TILE, S, Q - 1, S - Q + 1, INT>(F, [&](const Vtx<2>& w) {
-    cheb_last_at<2, T, T>(lg, w, sW, X, (T*)nullptr, dl, Q == 1, (T*)nullptr, (T)1);
+    if constexpr (INT) cheb_last_r<2, T>(lg, w, rw, X, (T*)nullptr, dl, Q == 1);
+    else cheb_last_at<2, T, T>(lg, w, sW, X, (T*)nullptr, dl, Q == 1, (T*)nullptr, (T)1);
   });
   const long long nv = a.g.nv;
   tile_loop<TILE, S, Q, Q + TILE, INT>(F, [&](const Vtx<2>& w) {
