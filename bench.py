@@ -225,7 +225,8 @@ def measured_peaks():
 def grid_opts(wl, precision):
     atol, rtol = wl.newton_tols
     return dict(restart=wl.restart, gmres_rtol=wl.gmres_rtol, newton_atol=atol, newton_rtol=rtol,
-                precision=precision, q_A=10, n_V=5, k_R=1, smooth_pre=2, smooth_post=2, use_graphs=1)
+                precision=precision, q_A=10, n_V=5, k_R=1, smooth_pre=2, smooth_post=2, use_graphs=1,
+                coarse_max=32 if wl.dim == 2 else 4)
 
 
 def run_precision(ok, torch, wl, precision_name, steps, warmup, rank, profile, flush):

@@ -152,7 +152,7 @@ class Preconditioner:
     """
 
     def __init__(self, system: System, u_k, mode="inexact", q_A=10, n_V=5, k_R=1,
-                 nu_pre=2, nu_post=2, smooth_lo_frac=0.25, schur="matching"):
+                 nu_pre=2, nu_post=2, smooth_lo_frac=0.25, schur="matching", coarse_max=4):
         self.sys, self.mode = system, mode
         self.q_A, self.n_V, self.k_R = q_A, n_V, k_R
         p, dim = system.p, system.mesh.dim
@@ -169,7 +169,7 @@ class Preconditioner:
                 S = (self.M - self.Cblk @ spla.spsolve(self.Ablk.tocsc(), self.Bblk.tocsc())).toarray()
                 self.S_exact = sla.lu_factor(S)
         else:
-            self.mg = Multigrid(dim, system.mesh.n, p.gamma, nu_pre, nu_post, smooth_lo_frac)
+            self.mg = Multigrid(dim, system.mesh.n, p.gamma, nu_pre, nu_post, smooth_lo_frac, coarse_max)
 
     def A_inv(self, r):
         if self.mode == "exact":
@@ -255,13 +255,14 @@ def fgmres(J_apply, P_apply, f, restart=30, rtol=1e-10, max_its=1000):
 class Options:
     def __init__(self, restart=30, gmres_rtol=1e-10, max_gmres=1000, q_A=10, n_V=5,
                  k_R=1, nu_pre=2, nu_post=2, newton_atol=1e-10, newton_rtol=0.0,
-                 max_newton=25, newton_extra=0, linear="fgmres", prec_mode="inexact"):
+                 max_newton=25, newton_extra=0, linear="fgmres", prec_mode="inexact", coarse_max=4):
         self.restart, self.gmres_rtol, self.max_gmres = restart, gmres_rtol, max_gmres
         self.q_A, self.n_V, self.k_R = q_A, n_V, k_R
         self.nu_pre, self.nu_post = nu_pre, nu_post
         self.newton_atol, self.newton_rtol = newton_atol, newton_rtol
         self.max_newton, self.newton_extra = max_newton, newton_extra
         self.linear, self.prec_mode = linear, prec_mode
+        self.coarse_max = coarse_max
 
 
 def linear_solve(system: System, u_k, rhs, opts: Options):
@@ -271,7 +272,7 @@ def linear_solve(system: System, u_k, rhs, opts: Options):
         d = spla.spsolve(J.tocsc(), rhs)
         return d, 0, np.linalg.norm(rhs - J @ d) / max(np.linalg.norm(rhs), 1e-300)
     P = Preconditioner(system, u_k, opts.prec_mode, opts.q_A, opts.n_V, opts.k_R,
-                       opts.nu_pre, opts.nu_post)
+                       opts.nu_pre, opts.nu_post, coarse_max=opts.coarse_max)
     return fgmres(lambda z: J @ z, P.apply, rhs, opts.restart, opts.gmres_rtol, opts.max_gmres)
 
 

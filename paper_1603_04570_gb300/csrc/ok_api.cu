@@ -171,6 +171,7 @@ struct Arena {
     ptrs.clear();
     bytes = 0;
   }
+  ~Arena() { release(); }
 };
 
 // One multigrid level of S_hat in precision T.
@@ -450,11 +451,12 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
     const double h = 1.0 / C.n, hd = std::pow(h, dim), hk = std::pow(h, dim - 2);
     std::vector<double> td(NCLASS * NOFF);
     for (int i = 0; i < NCLASS * NOFF; ++i) td[i] = hd * refM[i] + gamma * hk * refK[i];
-    double* Wd = A.alloc<double>(td.size());
+    Arena setup;                       // released when this block ends
+    double* Wd = setup.alloc<double>(td.size());
     CK(cudaMemcpy(Wd, td.data(), td.size() * sizeof(double), cudaMemcpyHostToDevice));
-    double* dense = A.alloc<double>(nc * nc);
-    double* work = A.alloc<double>(2 * nc * nc);
-    double* inv = A.alloc<double>(nc * nc);
+    double* dense = setup.alloc<double>(nc * nc);
+    double* work = setup.alloc<double>(2 * nc * nc + nc);
+    double* inv = std::is_same<T, double>::value ? A.alloc<double>(nc * nc) : setup.alloc<double>(nc * nc);
     CK(cudaMemset(dense, 0, nc * nc * sizeof(double)));
     launch_dense_from_table(dim, C.g, Wd, dense, 0);
     CKL();
@@ -820,9 +822,9 @@ int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid
     validate(dim, n, p, &od);
     std::vector<int> sizes = level_sizes(n, od.coarse_max);
     const long long ncoarse = (long long)std::pow((double)(sizes.back() + 1), dim);
-    if (ncoarse > 1000)
+    if (ncoarse > 4913)
       fail(OK_ERR_INVALID_ARG, "the coarsest multigrid level has " + std::to_string(ncoarse) +
-                                   " unknowns (> 1000); use n = c 2^k with (c+1)^dim <= 1000");
+                                   " unknowns (> 4913); use n = c 2^k with (c+1)^dim <= 4913");
     G = new ok_grid();
     G->dim = dim;
     G->n = n;

@@ -278,33 +278,47 @@ __global__ void k_dense_from_table(Geom g, const double* __restrict__ W, double*
   });
 }
 
-// Gauss--Jordan on [A | I] without pivoting (A is SPD), one block.
-__global__ void __launch_bounds__(1024) k_gauss_jordan(long long n, const double* __restrict__ A,
-                                                       double* __restrict__ w, double* __restrict__ Ainv) {
+// Gauss--Jordan on the n x 2n array [A | I] without pivoting (A is SPD): per
+// pivot p one single-block kernel scales row p and saves the column factors,
+// then one grid-wide kernel eliminates column p from every other row.
+__global__ void k_gj_init(long long n, const double* __restrict__ A, double* __restrict__ w) {
   const long long n2 = 2 * n;
-  for (long long e = threadIdx.x; e < n * n2; e += blockDim.x) {
-    long long r = e / n2, c = e % n2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n2;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / n2, c = e % n2;
     w[e] = c < n ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
   }
-  extern __shared__ double col[];   // n factors
+}
+__global__ void __launch_bounds__(1024) k_gj_pivot(long long n, double* __restrict__ w, double* __restrict__ col,
+                                                   long long p) {
+  const long long n2 = 2 * n;
+  const double piv = w[p * n2 + p];
   __syncthreads();
-  for (long long p = 0; p < n; ++p) {
-    const double piv = w[p * n2 + p];
-    __syncthreads();
-    for (long long c = threadIdx.x; c < n2; c += blockDim.x) w[p * n2 + c] /= piv;
-    __syncthreads();
-    for (long long r = threadIdx.x; r < n; r += blockDim.x) col[r] = (r == p) ? 0.0 : w[r * n2 + p];
-    __syncthreads();
-    for (long long e = threadIdx.x; e < n * n2; e += blockDim.x) {
-      long long r = e / n2, c = e % n2;
-      if (r != p) w[e] -= col[r] * w[p * n2 + c];
-    }
-    __syncthreads();
+  for (long long c = threadIdx.x; c < n2; c += blockDim.x) w[p * n2 + c] /= piv;
+  for (long long r = threadIdx.x; r < n; r += blockDim.x) col[r] = (r == p) ? 0.0 : w[r * n2 + p];
+}
+__global__ void k_gj_elim(long long n, double* __restrict__ w, const double* __restrict__ col, long long p) {
+  const long long n2 = 2 * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n2;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / n2, c = e % n2;
+    if (r != p) w[e] -= col[r] * w[p * n2 + c];
   }
-  for (long long e = threadIdx.x; e < n * n; e += blockDim.x) {
-    long long r = e / n, c = e % n;
-    Ainv[e] = w[r * n2 + n + c];
+}
+__global__ void k_gj_extract(long long n, const double* __restrict__ w, double* __restrict__ Ainv) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / n, c = e % n;
+    Ainv[e] = w[r * 2 * n + n + c];
   }
+}
+
+// x = Ainv b by many blocks, a warp per row (the rows' arithmetic is that of
+// the one-block coarse solve)
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_gemv(long long nc, const T* __restrict__ A, const T* __restrict__ b,
+                                                     T* __restrict__ x) {
+  coarse_rows<T>(nc, A, b, x, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), (int)((gridDim.x * blockDim.x) >> 5));
 }
 
 // ---------------------------------------------------------------------------
@@ -352,7 +366,12 @@ void launch_prolong_add(int dim, const Geom& gf, const Geom& gc, T* xf, const T*
 }
 template <typename T>
 void launch_coarse_solve(long long nc, const T* Ainv, const T* b, T* x, cudaStream_t s) {
-  count_launch(), k_coarse_solve<T><<<1, 512, 0, s>>>(nc, Ainv, b, x);
+  if (nc <= 512) {
+    count_launch(), k_coarse_solve<T><<<1, 512, 0, s>>>(nc, Ainv, b, x);
+    return;
+  }
+  const unsigned blocks = (unsigned)((nc + 7) / 8);   // 8 warps (rows) per block
+  count_launch(), k_coarse_gemv<T><<<blocks, 256, 0, s>>>(nc, Ainv, b, x);
 }
 template <typename T, typename TX, typename TY>
 void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha,
@@ -383,8 +402,16 @@ void launch_dense_from_table(int dim, const Geom& g, const double* W, double* A,
   if (dim == 2) count_launch(), k_dense_from_table<2><<<grid_of(2, g), BX, 0, s>>>(g, W, A);
   else count_launch(), k_dense_from_table<3><<<grid_of(3, g), BX, 0, s>>>(g, W, A);
 }
+// work: n x 2n array followed by n column factors
 void launch_gauss_jordan(long long n, const double* A, double* work, double* Ainv, cudaStream_t s) {
-  count_launch(), k_gauss_jordan<<<1, 1024, n * sizeof(double), s>>>(n, A, work, Ainv);
+  double* col = work + 2 * n * n;
+  const unsigned blocks = (unsigned)std::min<long long>((2 * n * n + 255) / 256, 4096);
+  count_launch(), k_gj_init<<<blocks, 256, 0, s>>>(n, A, work);
+  for (long long p = 0; p < n; ++p) {
+    count_launch(), k_gj_pivot<<<1, 1024, 0, s>>>(n, work, col, p);
+    count_launch(), k_gj_elim<<<blocks, 256, 0, s>>>(n, work, col, p);
+  }
+  count_launch(), k_gj_extract<<<blocks, 256, 0, s>>>(n, work, Ainv);
 }
 
 #define OK_INST_T(T)                                                                                          \

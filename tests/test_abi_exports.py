@@ -70,5 +70,5 @@ def test_invalid_params_rejected_on_host():
 
 def test_too_large_coarse_level_rejected():
     with pytest.raises(ok.OkError) as e:
-        ok.ok_grid_create(3, 11, ok.Params(0.04, 100, 0, 1, 1e-4))    # 12^3 coarse unknowns
+        ok.ok_grid_create(3, 17, ok.Params(0.04, 100, 0, 1, 1e-4))    # 18^3 coarse unknowns
     assert e.value.status == ok.OK_ERR_INVALID_ARG and "coarsest" in str(e.value)

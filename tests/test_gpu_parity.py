@@ -107,6 +107,24 @@ def test_preconditioner_parity(dim, n, k_R, precision):
         assert rel_inf(zh[nv:], ref[nv:]) < tol
 
 
+@pytest.mark.parametrize("dim,n,cmax", [(2, 64, 16), (2, 160, 40), (3, 24, 12)])
+@pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
+def test_preconditioner_parity_large_coarse_level(dim, n, cmax, precision):
+    """Coarsest level solved exactly at 17^2, 41^2 (multi-block solve) and 13^3
+    unknowns: the oracle with the same hierarchy."""
+    sysm, p, rng = make(dim, n, seed=12, dt=1e-4)
+    nv = sysm.mesh.nv
+    u = rng.uniform(-1.0, 1.0, nv)
+    v = rng.standard_normal(2 * nv)
+    ref = Preconditioner(sysm, u, mode="inexact", q_A=10, n_V=3, coarse_max=cmax).apply(v)
+    with ok.Grid(dim, n, **p, n_V=3, precision=precision, coarse_max=cmax) as g:
+        z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        g.apply_preconditioner(dev(u), dev(v), z)
+        tol = 1e-10 if precision == ok.OK_FP64 else 2e-4
+        zh = host(z)
+        assert rel_inf(zh[:nv], ref[:nv]) < tol and rel_inf(zh[nv:], ref[nv:]) < tol
+
+
 @pytest.mark.parametrize("dim,n", [(2, 32), (3, 8)])
 def test_init_w_parity(dim, n):
     sysm, p, rng = make(dim, n, seed=3)
