@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer run (short profiling runs)")
     ap.add_argument("--profile-out", default=None, help="write per-kernel samples as JSON")
+    ap.add_argument("--opt", action="append", default=[], metavar="KEY=INT",
+                    help="override an integer ok_opts field of the timed runs (e.g. use_pdl=0)")
     return ap.parse_args()
 
 
@@ -222,16 +224,20 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
-def grid_opts(wl, precision):
+def grid_opts(wl, precision, overrides=()):
     atol, rtol = wl.newton_tols
-    return dict(restart=wl.restart, gmres_rtol=wl.gmres_rtol, newton_atol=atol, newton_rtol=rtol,
-                precision=precision, q_A=10, n_V=5, k_R=1, smooth_pre=2, smooth_post=2, use_graphs=1,
-                coarse_max=32 if wl.dim == 2 else 4)
+    o = dict(restart=wl.restart, gmres_rtol=wl.gmres_rtol, newton_atol=atol, newton_rtol=rtol,
+             precision=precision, q_A=10, n_V=5, k_R=1, smooth_pre=2, smooth_post=2, use_graphs=1,
+             coarse_max=32 if wl.dim == 2 else 4)
+    for kv in overrides:
+        k, v = kv.split("=")
+        o[k] = int(v)
+    return o
 
 
-def run_precision(ok, torch, wl, precision_name, steps, warmup, rank, profile, flush):
+def run_precision(ok, torch, wl, precision_name, steps, warmup, rank, profile, flush, overrides=()):
     precision = ok.OK_MIXED if precision_name == "mixed" else ok.OK_FP64
-    opts = grid_opts(wl, precision)
+    opts = grid_opts(wl, precision, overrides)
     g = ok.Grid(wl.dim, wl.n, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, **opts)
     wl_r = dataclasses.replace(wl, seed=wl.seed + rank)
     u = torch.from_numpy(oi.initial_u(wl_r)).cuda()
@@ -333,10 +339,10 @@ def main_ok(args):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     clocks = ClockSampler(local)
     clocks.start()
-    mixed = run_precision(ok, torch, wl, "mixed", args.steps, args.warmup, rank, True, flush)
+    mixed = run_precision(ok, torch, wl, "mixed", args.steps, args.warmup, rank, True, flush, args.opt)
     clk = clocks.stop()
     fp64 = None if args.no_fp64 else run_precision(ok, torch, wl, "fp64", args.steps, args.warmup, rank, True,
-                                                   flush)
+                                                   flush, args.opt)
     e2e = None if args.no_e2e else e2e_run(ok, torch, mixed, wl, args.steps, flush)
     dof = 2 * wl.n_vertices
     total_ms = sum(mixed["step_ms"])
@@ -379,7 +385,8 @@ def main_ok(args):
                    "eps": wl.eps, "sigma": wl.sigma, "m": wl.m, "theta": wl.theta, "dt": wl.dt,
                    "restart": wl.restart, "gmres_rtol": wl.gmres_rtol, "mg_levels": mixed["g"].levels,
                    "precision": "mixed (float32 preconditioner, float64 FGMRES/J/residual)",
-                   "l2": "flushed by a 512 MB write before every timed step", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed by a 512 MB write before every timed step", "parallelism": f"replicas x{world}",
+                   **({"overrides": args.opt} if args.opt else {})},
         "gmres_its": mixed["its"], "newton_its": mixed["newton"],
         "its_per_newton": mixed["its"] / max(mixed["newton"], 1),
         "latency": {"step_p50_ms": pct(mixed["step_ms"], 0.5), "step_p99_ms": pct(mixed["step_ms"], 0.99),

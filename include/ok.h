@@ -92,7 +92,10 @@ typedef struct ok_opts {
   int coarse_max;     /* halve the grid while n is even and > coarse_max [4]    */
   int use_graphs;     /* capture each Arnoldi step in a CUDA graph [1]          */
   int fuse_coarse;    /* run the coarse multigrid levels in one kernel [1]      */
-  int tile_fine;      /* 2D: shared-memory tile kernels on the fine levels [1]  */
+  int tile_fine;      /* 2D: register-strip tile kernels on the fine levels:
+                         0 off, 1 automatic window width, 2 / 3 force 32 / 64
+                         columns [1]                                            */
+  int use_pdl;        /* programmatic dependent launch between kernels [0]      */
   double gmres_rtol;  /* stop when ||f - J x|| <= gmres_rtol ||f|| [1e-10]      */
   double newton_atol; /* Newton stops when ||F||_2 <= max(atol, rtol ||F_0||)   */
   double newton_rtol; /*   [atol 1e-10, rtol 0]                                 */
@@ -199,8 +202,11 @@ int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream st
  * records one CUDA-event pair per kernel class per step on the handle's
  * stream: "precond" (one whole preconditioner application), "apply_j" (the
  * Jacobian kernel), "cgs2" (the four orthogonalisation kernels),
- * "mg_smooth_l0" (the first finest-level Chebyshev smoothing kernel) and
- * "cheb_mass_step" (the first Chebyshev step on M).  ok_profile(g, 0) stops.
+ * "mg_smooth_l0" (the first finest-level Chebyshev smoothing kernel),
+ * "cheb_mass_step" (the first Chebyshev step on M); with the 2D tile kernels
+ * "tile_mass_cstep" (A~^{-1} r1 and the C-step), "mg_tile_pre_l<k>" and
+ * "mg_tile_post_l<k>" (the first pre-/post-smoothing tile kernel of level
+ * k = 0..4) and "mg_coarse" (the first coarsest-level solve).  ok_profile(g, 0) stops.
  * Toggling re-captures the handle's CUDA graphs.  ok_profile_read copies up
  * to `max` records into `out` (host) and the number written into *count. */
 typedef struct ok_kernel_stat {

@@ -31,7 +31,7 @@ class Opts(Structure):
     _fields_ = [("restart", c_int), ("max_gmres", c_int), ("max_newton", c_int), ("newton_extra", c_int),
                 ("q_A", c_int), ("n_V", c_int), ("k_R", c_int), ("smooth_pre", c_int), ("smooth_post", c_int),
                 ("precision", c_int), ("coarse_max", c_int), ("use_graphs", c_int), ("fuse_coarse", c_int),
-                ("tile_fine", c_int),
+                ("tile_fine", c_int), ("use_pdl", c_int),
                 ("gmres_rtol", c_double), ("newton_atol", c_double), ("newton_rtol", c_double),
                 ("smooth_lo_frac", c_double)]
 
@@ -231,9 +231,9 @@ def ok_profile(h, enable: bool):
 
 def ok_profile_read(h):
     """{kernel class: (samples, total_ms)} of the handle's sampled timings."""
-    arr = (KernelStat * 16)()
+    arr = (KernelStat * 64)()
     n = c_int()
-    _check(load().ok_profile_read(h, arr, 16, byref(n)))
+    _check(load().ok_profile_read(h, arr, len(arr), byref(n)))
     return {arr[i].name.decode(): (arr[i].samples, arr[i].total_ms) for i in range(n.value)}
 
 

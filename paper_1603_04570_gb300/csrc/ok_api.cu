@@ -88,16 +88,27 @@ void cheb_coefs(double lo, double hi, int steps, std::vector<double>& c1, std::v
 }  // namespace
 
 std::atomic<long long> okg::g_launch_count{0};
+thread_local bool okg::g_pdl = false;
 
 // ---------------------------------------------------------------------------
 // sampled kernel timing: one CUDA-event pair per kernel class per Arnoldi
 // step, recorded on the handle's stream (inside the captured graph when
 // graphs are on) and read after the step's host synchronisation.
 // ---------------------------------------------------------------------------
-enum ProfTag { PT_PRECOND = 0, PT_APPLYJ, PT_CGS2, PT_SMOOTH0, PT_CHEBM, PT_TPRE0, PT_TPOST0, PT_TAMASS, PT_COUNT };
-static const char* const kProfNames[PT_COUNT] = {"precond", "apply_j", "cgs2", "mg_smooth_l0",
-                                                 "cheb_mass_step", "mg_tile_pre_l0", "mg_tile_post_l0",
-                                                 "tile_mass_cstep"};
+enum ProfTag {
+  PT_PRECOND = 0, PT_APPLYJ, PT_CGS2, PT_SMOOTH0, PT_CHEBM, PT_TPRE0, PT_TPOST0, PT_TAMASS,
+  PT_TPRE1, PT_TPOST1, PT_TPRE2, PT_TPOST2, PT_TPRE3, PT_TPOST3, PT_TPRE4, PT_TPOST4, PT_COARSE, PT_COUNT
+};
+static const char* const kProfNames[PT_COUNT] = {
+    "precond", "apply_j", "cgs2", "mg_smooth_l0", "cheb_mass_step", "mg_tile_pre_l0", "mg_tile_post_l0",
+    "tile_mass_cstep", "mg_tile_pre_l1", "mg_tile_post_l1", "mg_tile_pre_l2", "mg_tile_post_l2",
+    "mg_tile_pre_l3", "mg_tile_post_l3", "mg_tile_pre_l4", "mg_tile_post_l4", "mg_coarse"};
+// tags of the tile kernels of level l (pre, post); -1 below level 4
+static inline int tile_tag(int l, bool post) {
+  if (l == 0) return post ? PT_TPOST0 : PT_TPRE0;
+  if (l <= 4) return PT_TPRE1 + 2 * (l - 1) + (post ? 1 : 0);
+  return -1;
+}
 using TagSet = std::array<bool, PT_COUNT>;
 
 struct Profiler {
@@ -190,6 +201,14 @@ template <typename T> struct Prec {
   T *WM = nullptr, *WK = nullptr, *dinvM = nullptr;   // finest level M, K (scaled)
   T* coarse_inv = nullptr;
   long long nc = 0;
+  T* gemv_inv = nullptr;       // nc > GEMV_MIN: the inverse with padded row stride gemv_ldA
+  long long gemv_ldA = 0;
+  static constexpr long long GEMV_MIN = 512;   // above: many-block GEMV, else one block
+
+  void coarse_solve(const T* rhs, T* x, cudaStream_t s) {
+    if (gemv_inv) launch_coarse_gemv<T>(nc, gemv_ldA, gemv_inv, rhs, x, s);
+    else launch_coarse_solve<T>(nc, coarse_inv, rhs, x, s);
+  }
   T *cx = nullptr, *cr = nullptr, *cd0 = nullptr, *cd1 = nullptr;   // Chebyshev on M
   T *tt = nullptr, *yy = nullptr;                                    // k_R = 2
   const T* coef = nullptr;                                           // C coefficients (T)
@@ -215,21 +234,25 @@ template <typename T> struct Prec {
   template <typename TO>
   void vcycle_t(int l, bool x_zero, const T* rhs, TO* out, T* mx, cudaStream_t s) {
     if (fused && l == Lc) {
+      if (prof) prof->begin(PT_COARSE, s);
       launch_coarse_vcycle<T>(dim, ca, csmem, rhs, x_zero ? (const T*)nullptr : X(l), X(l), s);
+      if (prof) prof->end(PT_COARSE, s);
       return;
     }
     if (l + 1 == (int)lv.size()) {
-      launch_coarse_solve<T>(nc, coarse_inv, rhs, X(l), s);
+      if (prof) prof->begin(PT_COARSE, s);
+      coarse_solve(rhs, X(l), s);
+      if (prof) prof->end(PT_COARSE, s);
       return;
     }
-    if (l == 0 && prof) prof->begin(PT_TPRE0, s);
+    if (prof) prof->begin(tile_tag(l, false), s);
     launch_tile_pre<T>(ts[l], x_zero ? (const T*)nullptr : X(l), rhs, Xalt(l), lv[l + 1].b, s);
-    if (l == 0 && prof) prof->end(PT_TPRE0, s);
+    if (prof) prof->end(tile_tag(l, false), s);
     cur[l] ^= 1;
     vcycle_t<T>(l + 1, true, lv[l + 1].b, (T*)nullptr, (T*)nullptr, s);
-    if (l == 0 && prof) prof->begin(PT_TPOST0, s);
+    if (prof) prof->begin(tile_tag(l, true), s);
     launch_tile_post<T, TO>(ts[l], X(l), X(l + 1), rhs, Xalt(l), mx, out, (T)1, s);
-    if (l == 0 && prof) prof->end(PT_TPOST0, s);
+    if (prof) prof->end(tile_tag(l, true), s);
     cur[l] ^= 1;
   }
 
@@ -279,7 +302,7 @@ template <typename T> struct Prec {
       return;
     }
     if (coarsest) {
-      launch_coarse_solve<T>(nc, coarse_inv, L.b, L.x, s);
+      coarse_solve(L.b, L.x, s);
       if (out) launch_axpby<T, TO>(L.g.nv, 1.0, L.x, 0.0, out, s);
       return;
     }
@@ -469,6 +492,14 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
       launch_axpby<double, T>(nc * nc, 1.0, inv, 0.0, P.coarse_inv, 0);
       CKL();
     }
+    if (nc > P.GEMV_MIN) {           // padded copy for the many-block GEMV
+      P.gemv_ldA = gemv_ld(nc, sizeof(T));
+      P.gemv_inv = A.alloc<T>(nc * P.gemv_ldA);
+      CK(cudaMemset(P.gemv_inv, 0, nc * P.gemv_ldA * sizeof(T)));
+      CK(cudaMemcpy2D(P.gemv_inv, P.gemv_ldA * sizeof(T), P.coarse_inv, nc * sizeof(T), nc * sizeof(T), nc,
+                      cudaMemcpyDeviceToDevice));
+      CK(prepare_coarse_gemv<T>(nc));
+    }
     CK(cudaDeviceSynchronize());
   }
   // fused coarse part: the longest suffix of levels whose five vectors fit in
@@ -540,10 +571,11 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
       t.inv_th = (T)(1.0 / P.thS);
       t.c1 = (T)P.cS1[0];
       t.c2 = (T)P.cS2[0];
-      // 32-wide tiles while they give at least two blocks per SM, else 16-wide
-      // (4x the blocks, about half the per-block latency, more redundant halo work)
-      const long long nb32 = (long long)((t.g.n1 + 31) / 32) * ((t.g.n1 + 31) / 32);
-      t.tile = nb32 >= 2 * G->sms ? 32 : 16;
+      // 64-column windows on levels of at least 512 vertices per side (less
+      // redundant halo work), 32-column windows below (more, shorter blocks);
+      // tile_fine = 2 or 3 forces 32 or 64 on every tiled level
+      const int tf = G->o.tile_fine;
+      t.tile = tf == 2 ? 32 : (tf == 3 ? 64 : (t.g.n1 >= 512 ? 64 : 32));
     }
     TileMass<T>& m = P.tm;
     m.g = P.lv[0].g;
@@ -583,6 +615,7 @@ void validate(int dim, int n, const ok_params* p, const ok_opts* o) {
     fail(OK_ERR_INVALID_ARG, "tolerances must be positive");
   if (!(o->smooth_lo_frac > 0 && o->smooth_lo_frac < 1)) fail(OK_ERR_INVALID_ARG, "smooth_lo_frac in (0,1)");
   if (o->coarse_max < 1) fail(OK_ERR_INVALID_ARG, "coarse_max must be >= 1");
+  if (o->tile_fine < 0 || o->tile_fine > 3) fail(OK_ERR_INVALID_ARG, "tile_fine must be 0, 1, 2 or 3");
 }
 
 std::vector<int> level_sizes(int n, int coarse_max) {
@@ -595,6 +628,7 @@ struct StreamScope {
   ok_grid* G;
   cudaStream_t user;
   StreamScope(ok_grid* g, cudaStream_t u) : G(g), user(u) {
+    g_pdl = G->o.use_pdl != 0;
     CK(cudaEventRecord(G->ev_in, user));
     CK(cudaStreamWaitEvent(G->s, G->ev_in, 0));
   }
@@ -799,6 +833,7 @@ void ok_default_opts(ok_opts* o) {
   o->use_graphs = 1;
   o->fuse_coarse = 1;
   o->tile_fine = 1;
+  o->use_pdl = 0;
   o->gmres_rtol = 1e-10;
   o->newton_atol = 1e-10;
   o->newton_rtol = 0.0;

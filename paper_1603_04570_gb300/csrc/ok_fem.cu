@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(128) k_residual(Geom g, const double* __restri
                                                   const double* __restrict__ un, const double* __restrict__ wn,
                                                   const double* __restrict__ u, const double* __restrict__ w,
                                                   double* __restrict__ f) {
+  pdl_entry();
   using Tp = Topo<D>;
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(128) k_residual(Geom g, const double* __restri
 template <int D>
 __global__ void __launch_bounds__(128) k_initw_rhs(Geom g, const double* __restrict__ WK, ResidualCoefs rc,
                                                    const double* __restrict__ u, double* __restrict__ out) {
+  pdl_entry();
   using Tp = Topo<D>;
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(128) k_initw_rhs(Geom g, const double* __restr
 template <int D>
 __global__ void __launch_bounds__(128) k_assemble_c(Geom g, ResidualCoefs rc, const double* __restrict__ u,
                                                     double* __restrict__ coef, float* __restrict__ coef32) {
+  pdl_entry();
   using Tp = Topo<D>;
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
@@ -267,6 +270,7 @@ __global__ void __launch_bounds__(128) k_apply_j(Geom g, const double* __restric
                                                  const double* __restrict__ WK, JCoefs jc,
                                                  const double* __restrict__ coef, const TZ* __restrict__ z,
                                                  double* __restrict__ y, const double* __restrict__ y0) {
+  pdl_entry();
   using Tp = Topo<D>;
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
@@ -289,6 +293,7 @@ __global__ void __launch_bounds__(128) k_apply_j(Geom g, const double* __restric
 template <int D, typename T, typename TV>
 __global__ void __launch_bounds__(128) k_cstep(Geom g, const T* __restrict__ coef, const TV* __restrict__ v2,
                                                T vscale, const T* __restrict__ y1, T yscale, T* __restrict__ t) {
+  pdl_entry();
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   T cy = capply_at<D, T>(g, v, coef, y1, yscale);
@@ -300,6 +305,7 @@ template <int D, typename T>
 __global__ void __launch_bounds__(128) k_schur_resid(Geom g, const T* __restrict__ WM, T hd, const T* __restrict__ coef,
                                                      const T* __restrict__ t, const T* __restrict__ y,
                                                      const T* __restrict__ a, T ascale, T* __restrict__ out) {
+  pdl_entry();
   using Tp = Topo<D>;
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
@@ -321,30 +327,30 @@ void launch_residual(int dim, const Geom& g, const double* WM, const double* WK,
                      const double* un, const double* wn, const double* u, const double* w, double* f,
                      cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) count_launch(), k_residual<2><<<grd, 128, 0, s>>>(g, WM, WK, rc, un, wn, u, w, f);
-  else count_launch(), k_residual<3><<<grd, 128, 0, s>>>(g, WM, WK, rc, un, wn, u, w, f);
+  if (dim == 2) launch_k(k_residual<2>, grd, 128, 0, s, g, WM, WK, rc, un, wn, u, w, f);
+  else launch_k(k_residual<3>, grd, 128, 0, s, g, WM, WK, rc, un, wn, u, w, f);
 }
 
 void launch_initw_rhs(int dim, const Geom& g, const double* WK, const ResidualCoefs& rc, const double* u,
                       double* out, cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) count_launch(), k_initw_rhs<2><<<grd, 128, 0, s>>>(g, WK, rc, u, out);
-  else count_launch(), k_initw_rhs<3><<<grd, 128, 0, s>>>(g, WK, rc, u, out);
+  if (dim == 2) launch_k(k_initw_rhs<2>, grd, 128, 0, s, g, WK, rc, u, out);
+  else launch_k(k_initw_rhs<3>, grd, 128, 0, s, g, WK, rc, u, out);
 }
 
 void launch_assemble_c(int dim, const Geom& g, const ResidualCoefs& rc, const double* u, double* coef,
                        float* coef32, cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) count_launch(), k_assemble_c<2><<<grd, 128, 0, s>>>(g, rc, u, coef, coef32);
-  else count_launch(), k_assemble_c<3><<<grd, 128, 0, s>>>(g, rc, u, coef, coef32);
+  if (dim == 2) launch_k(k_assemble_c<2>, grd, 128, 0, s, g, rc, u, coef, coef32);
+  else launch_k(k_assemble_c<3>, grd, 128, 0, s, g, rc, u, coef, coef32);
 }
 
 template <typename TZ>
 void launch_apply_j(int dim, const Geom& g, const double* WM, const double* WK, const JCoefs& jc,
                     const double* coef, const TZ* z, double* y, const double* y0, cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) count_launch(), k_apply_j<2, TZ><<<grd, 128, 0, s>>>(g, WM, WK, jc, coef, z, y, y0);
-  else count_launch(), k_apply_j<3, TZ><<<grd, 128, 0, s>>>(g, WM, WK, jc, coef, z, y, y0);
+  if (dim == 2) launch_k(k_apply_j<2, TZ>, grd, 128, 0, s, g, WM, WK, jc, coef, z, y, y0);
+  else launch_k(k_apply_j<3, TZ>, grd, 128, 0, s, g, WM, WK, jc, coef, z, y, y0);
 }
 template void launch_apply_j<double>(int, const Geom&, const double*, const double*, const JCoefs&,
                                      const double*, const double*, double*, const double*, cudaStream_t);
@@ -355,8 +361,8 @@ template <typename T, typename TV>
 void launch_cstep(int dim, const Geom& g, const T* coef, const TV* v2, T vscale, const T* y1, T yscale, T* t,
                   cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) count_launch(), k_cstep<2, T, TV><<<grd, 128, 0, s>>>(g, coef, v2, vscale, y1, yscale, t);
-  else count_launch(), k_cstep<3, T, TV><<<grd, 128, 0, s>>>(g, coef, v2, vscale, y1, yscale, t);
+  if (dim == 2) launch_k(k_cstep<2, T, TV>, grd, 128, 0, s, g, coef, v2, vscale, y1, yscale, t);
+  else launch_k(k_cstep<3, T, TV>, grd, 128, 0, s, g, coef, v2, vscale, y1, yscale, t);
 }
 template void launch_cstep<double, double>(int, const Geom&, const double*, const double*, double, const double*,
                                            double, double*, cudaStream_t);
@@ -367,8 +373,8 @@ template <typename T>
 void launch_schur_resid(int dim, const Geom& g, const T* WM, T hd, const T* coef, const T* t, const T* y,
                         const T* a, T ascale, T* out, cudaStream_t s) {
   dim3 grd = grid_of(dim, g, 128);
-  if (dim == 2) count_launch(), k_schur_resid<2, T><<<grd, 128, 0, s>>>(g, WM, hd, coef, t, y, a, ascale, out);
-  else count_launch(), k_schur_resid<3, T><<<grd, 128, 0, s>>>(g, WM, hd, coef, t, y, a, ascale, out);
+  if (dim == 2) launch_k(k_schur_resid<2, T>, grd, 128, 0, s, g, WM, hd, coef, t, y, a, ascale, out);
+  else launch_k(k_schur_resid<3, T>, grd, 128, 0, s, g, WM, hd, coef, t, y, a, ascale, out);
 }
 template void launch_schur_resid<double>(int, const Geom&, const double*, double, const double*, const double*,
                                          const double*, const double*, double, double*, cudaStream_t);

@@ -31,6 +31,33 @@ namespace okg {
 extern std::atomic<long long> g_launch_count;
 inline void count_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
 
+// Programmatic dependent launch: a kernel launched with launch_k may be
+// scheduled while its predecessor on the stream is still running; every
+// kernel therefore starts with pdl_entry(), which lets its own successor be
+// scheduled and then waits (in hardware) until the predecessor has completed
+// and its memory is visible.  Without the launch attribute both are no-ops.
+extern thread_local bool g_pdl;
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KP, typename... A>
+inline void launch_k(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+  count_launch();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = g_pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 // ---------------------------------------------------------------------------
 // compile-time topology
 // ---------------------------------------------------------------------------

@@ -71,9 +71,15 @@ void launch_restrict(int dim, const Geom& gf, const Geom& gc, const T* rf, T* bc
 // x_f += P x_c
 template <typename T>
 void launch_prolong_add(int dim, const Geom& gf, const Geom& gc, T* xf, const T* xc, cudaStream_t s);
-// x = Ainv b on the coarsest level (dense)
+// x = Ainv b on the coarsest level (dense, row stride nc), one thread block
 template <typename T>
 void launch_coarse_solve(long long nc, const T* Ainv, const T* b, T* x, cudaStream_t s);
+// the same by many blocks; Ainv has row stride ld = gemv_ld(nc) and zero padding
+long long gemv_ld(long long nc, size_t elem);
+template <typename T>
+void launch_coarse_gemv(long long nc, long long ld, const T* Ainv, const T* b, T* x, cudaStream_t s);
+template <typename T>
+cudaError_t prepare_coarse_gemv(long long nc);
 // y = alpha W x (+ beta y0 when y0 != null), first NO offsets: full (M-like) or axis (K)
 template <typename T, typename TX, typename TY>
 void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha,
@@ -103,14 +109,14 @@ void launch_coarse_vcycle(int dim, const CoarseArgs<T>& a, size_t smem, const T*
 template <typename T>
 cudaError_t prepare_coarse_vcycle(int dim, size_t smem);
 
-// ---- shared-memory tile kernels, 2D (ok_tile.cu) -------------------------
+// ---- register-strip tile kernels, 2D (ok_tile.cu) ------------------------
 template <typename T> struct TileSmooth {
   Geom g, gc;             // this level and the next coarser one
   const T* W;             // S_hat table of this level
   const T* dinv;
   const T* WM;            // M table of this level (post kernel's optional M x)
   T inv_th, c1, c2;       // smoother: 1/centre, coefficients of the middle step
-  int tile;               // owned vertices per tile side: 32, or 16 on small levels
+  int tile;               // window width: 64 (large levels) or 32 columns
 };
 template <typename T> struct TileMass {
   Geom g;
@@ -133,6 +139,9 @@ template <typename T, typename TZ>
 void launch_tile_amass(const TileMass<T>& a, const double* v, TZ* z1, T* t_out, cudaStream_t s);
 template <typename T>
 cudaError_t prepare_tiles(int q);
+// thread blocks of a pre-smoothing launch on level g with window width `tile`
+template <typename T>
+long long strip_blocks(const Geom& g, int tile);
 
 // dense matrix of a level operator (row-major nv x nv) from its class table
 void launch_dense_from_table(int dim, const Geom& g, const double* W, double* A, cudaStream_t s);

@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ V, l
                                                  const double* __restrict__ w, long long N,
                                                  double* __restrict__ partials, unsigned int* counter,
                                                  double* __restrict__ out) {
+  pdl_entry();
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(RT) k_update_multidot(const double* __restrict
                                                         const double* __restrict__ hin, double* __restrict__ w,
                                                         long long N, double* __restrict__ partials,
                                                         unsigned int* counter, double* __restrict__ out) {
+  pdl_entry();
   __shared__ double hs[K];
   if (threadIdx.x < K) hs[threadIdx.x] = hin[threadIdx.x];
   __syncthreads();
@@ -160,6 +162,7 @@ __global__ void __launch_bounds__(RT) k_update_norm_givens(const double* __restr
                                                            double* __restrict__ w, long long N,
                                                            double* __restrict__ partials, unsigned int* counter,
                                                            KrylovState* ks, int j, int K0) {
+  pdl_entry();
   __shared__ double hs[K];
   if (threadIdx.x < K) hs[threadIdx.x] = ks->h2[K0 + threadIdx.x];
   __syncthreads();
@@ -207,6 +210,7 @@ template <int K>
 __global__ void __launch_bounds__(RT) k_update_only(const double* __restrict__ V, long long ldv,
                                                     const double* __restrict__ h, double* __restrict__ w,
                                                     long long N) {
+  pdl_entry();
   __shared__ double hs[K];
   if (threadIdx.x < K) hs[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
@@ -236,6 +240,7 @@ static void with_k(int K, F&& f) {
 __global__ void __launch_bounds__(RT) k_sumsq(const double* __restrict__ x, long long N,
                                               double* __restrict__ partials, unsigned int* counter,
                                               double* __restrict__ out) {
+  pdl_entry();
   double acc[1] = {0.0};
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT)
     acc[0] = fma(x[e], x[e], acc[0]);
@@ -247,11 +252,13 @@ __global__ void __launch_bounds__(RT) k_sumsq(const double* __restrict__ x, long
 
 __global__ void __launch_bounds__(RT) k_scale_by(double* __restrict__ w, long long N,
                                                  const double* __restrict__ factor) {
+  pdl_entry();
   const double f = *factor;
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) w[e] *= f;
 }
 
 __global__ void k_cycle_start(KrylovState* ks, const double* __restrict__ beta) {
+  pdl_entry();
   if (threadIdx.x == 0) {
     const double b = *beta;
     ks->beta = b;
@@ -264,6 +271,7 @@ __global__ void k_cycle_start(KrylovState* ks, const double* __restrict__ beta) 
 
 // back substitution R y = g, R = rotated H (k x k upper triangular)
 __global__ void k_lsq(KrylovState* ks, int k) {
+  pdl_entry();
   if (threadIdx.x == 0) {
     const int ld = KRYLOV_MAX + 1;
     for (int i = k - 1; i >= 0; --i) {
@@ -279,6 +287,7 @@ template <typename TZ>
 __global__ void __launch_bounds__(RT) k_multi_axpy(const TZ* __restrict__ Z, long long ldz, int K,
                                                    const KrylovState* __restrict__ ks, double* __restrict__ x,
                                                    long long N) {
+  pdl_entry();
   __shared__ double ys[KRYLOV_MAX];
   if (threadIdx.x < KRYLOV_MAX) ys[threadIdx.x] = threadIdx.x < K ? ks->y[threadIdx.x] : 0.0;
   __syncthreads();
@@ -292,6 +301,7 @@ __global__ void __launch_bounds__(RT) k_multi_axpy(const TZ* __restrict__ Z, lon
 template <typename TX, typename TY>
 __global__ void __launch_bounds__(RT) k_axpby(long long N, double a, const TX* __restrict__ x, double b,
                                               TY* __restrict__ y) {
+  pdl_entry();
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
     double v = a * (double)x[e];
     if (b != 0.0) v = fma(b, (double)y[e], v);
@@ -300,6 +310,7 @@ __global__ void __launch_bounds__(RT) k_axpby(long long N, double a, const TX* _
 }
 
 __global__ void __launch_bounds__(RT) k_check_finite(const double* __restrict__ x, long long N, int* flag) {
+  pdl_entry();
   int bad = 0;
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT)
     bad |= !isfinite(x[e]);
@@ -315,7 +326,7 @@ void launch_multidot(const double* V, long long ldv, int K, const double* w, lon
   for (int k0 = 0; k0 < K; k0 += KC) {
     const int kk = K - k0 < KC ? K - k0 : KC;
     with_k(kk, [&](auto KK) {
-      count_launch(), k_multidot<decltype(KK)::value><<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, w, N,
+      launch_k(k_multidot<decltype(KK)::value>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, w, N,
                                                                                     rs.partials, rs.counter, out + k0);
     });
   }
@@ -325,7 +336,7 @@ void launch_update_multidot(const double* V, long long ldv, int K, const double*
                             RedScratch rs, double* h_out, cudaStream_t s) {
   if (K <= KC) {
     with_k(K, [&](auto KK) {
-      count_launch(), k_update_multidot<decltype(KK)::value><<<krylov_blocks(), RT, 0, s>>>(
+      launch_k(k_update_multidot<decltype(KK)::value>, krylov_blocks(), RT, 0, s, 
                           V, ldv, h_in, w, N, rs.partials, rs.counter, h_out);
     });
     return;
@@ -333,7 +344,7 @@ void launch_update_multidot(const double* V, long long ldv, int K, const double*
   for (int k0 = 0; k0 < K; k0 += KC) {   // all updates first, then the dots of the final w
     const int kk = K - k0 < KC ? K - k0 : KC;
     with_k(kk, [&](auto KK) {
-      count_launch(), k_update_only<decltype(KK)::value><<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, h_in + k0,
+      launch_k(k_update_only<decltype(KK)::value>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, h_in + k0,
                                                                                        w, N);
     });
   }
@@ -345,32 +356,32 @@ void launch_update_norm_givens(const double* V, long long ldv, int K, double* w,
   int k0 = 0;
   for (; K - k0 > KC; k0 += KC) {
     // h2 lives in device memory inside ks; chunk offsets index it directly
-    count_launch(), k_update_only<KC><<<krylov_blocks(), RT, 0, s>>>(V + k0 * ldv, ldv, ks->h2 + k0, w, N);
+    launch_k(k_update_only<KC>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, ks->h2 + k0, w, N);
   }
   with_k(K - k0, [&](auto KK) {
-    count_launch(), k_update_norm_givens<decltype(KK)::value><<<krylov_blocks(), RT, 0, s>>>(
+    launch_k(k_update_norm_givens<decltype(KK)::value>, krylov_blocks(), RT, 0, s, 
                         V + k0 * ldv, ldv, w, N, rs.partials, rs.counter, ks, j, k0);
   });
 }
 
 void launch_scale_by(double* w, long long N, const double* factor, cudaStream_t s) {
-  count_launch(), k_scale_by<<<krylov_blocks(), RT, 0, s>>>(w, N, factor);
+  launch_k(k_scale_by, krylov_blocks(), RT, 0, s, w, N, factor);
 }
 
 void launch_norm(const double* x, long long N, RedScratch rs, double* out, cudaStream_t s) {
-  count_launch(), k_sumsq<<<krylov_blocks(), RT, 0, s>>>(x, N, rs.partials, rs.counter, out);
+  launch_k(k_sumsq, krylov_blocks(), RT, 0, s, x, N, rs.partials, rs.counter, out);
 }
 
 void launch_cycle_start(KrylovState* ks, const double* beta, cudaStream_t s) {
-  count_launch(), k_cycle_start<<<1, 32, 0, s>>>(ks, beta);
+  launch_k(k_cycle_start, 1, 32, 0, s, ks, beta);
 }
 
-void launch_lsq(KrylovState* ks, int k, cudaStream_t s) { count_launch(), k_lsq<<<1, 32, 0, s>>>(ks, k); }
+void launch_lsq(KrylovState* ks, int k, cudaStream_t s) { launch_k(k_lsq, 1, 32, 0, s, ks, k); }
 
 template <typename TZ>
 void launch_multi_axpy(const TZ* Z, long long ldz, int K, const KrylovState* ks, double* x, long long N,
                        cudaStream_t s) {
-  count_launch(), k_multi_axpy<TZ><<<krylov_blocks(), RT, 0, s>>>(Z, ldz, K, ks, x, N);
+  launch_k(k_multi_axpy<TZ>, krylov_blocks(), RT, 0, s, Z, ldz, K, ks, x, N);
 }
 template void launch_multi_axpy<double>(const double*, long long, int, const KrylovState*, double*, long long,
                                         cudaStream_t);
@@ -379,7 +390,7 @@ template void launch_multi_axpy<float>(const float*, long long, int, const Krylo
 
 template <typename TX, typename TY>
 void launch_axpby(long long N, double a, const TX* x, double b, TY* y, cudaStream_t s) {
-  count_launch(), k_axpby<TX, TY><<<krylov_blocks(), RT, 0, s>>>(N, a, x, b, y);
+  launch_k(k_axpby<TX, TY>, krylov_blocks(), RT, 0, s, N, a, x, b, y);
 }
 template void launch_axpby<double, double>(long long, double, const double*, double, double*, cudaStream_t);
 template void launch_axpby<float, double>(long long, double, const float*, double, double*, cudaStream_t);
@@ -387,7 +398,7 @@ template void launch_axpby<double, float>(long long, double, const double*, doub
 template void launch_axpby<float, float>(long long, double, const float*, double, float*, cudaStream_t);
 
 void launch_check_finite(const double* x, long long N, int* flag, cudaStream_t s) {
-  count_launch(), k_check_finite<<<krylov_blocks(), RT, 0, s>>>(x, N, flag);
+  launch_k(k_check_finite, krylov_blocks(), RT, 0, s, x, N, flag);
 }
 
 }  // namespace okg

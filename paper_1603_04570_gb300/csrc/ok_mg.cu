@@ -35,6 +35,7 @@ static inline dim3 grid_of(int dim, const Geom& g) {
 template <int D, typename T, typename TB>
 __global__ void __launch_bounds__(BX) k_cheb_init(Geom g, const T* __restrict__ dinv, const TB* __restrict__ b,
                                                   T bscale, T* __restrict__ r, T* __restrict__ d, T inv_th) {
+  pdl_entry();
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   cheb_init_at<D, T, TB>(v, dinv, b, bscale, r, d, inv_th);
@@ -44,6 +45,7 @@ template <int D, typename T>
 __global__ void __launch_bounds__(BX) k_resid_init(Geom g, const T* __restrict__ W, const T* __restrict__ dinv,
                                                    const T* __restrict__ b, const T* __restrict__ x,
                                                    T* __restrict__ r, T* __restrict__ d, T inv_th) {
+  pdl_entry();
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   resid_init_at<D, T>(g, v, W, dinv, b, x, r, d, inv_th);
@@ -53,6 +55,7 @@ template <int D, typename T>
 __global__ void __launch_bounds__(BX) k_cheb_step(Geom g, const T* __restrict__ W, const T* __restrict__ dinv,
                                                   T* __restrict__ x, T* __restrict__ r, const T* __restrict__ din,
                                                   T* __restrict__ dout, T c1, T c2, int first) {
+  pdl_entry();
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   cheb_step_at<D, T>(g, v, W, dinv, x, r, din, dout, c1, c2, first != 0);
@@ -62,6 +65,7 @@ template <int D, typename T, typename TO>
 __global__ void __launch_bounds__(BX) k_cheb_last(Geom g, const T* __restrict__ W, T* __restrict__ x,
                                                   T* __restrict__ r, const T* __restrict__ din, int first,
                                                   TO* __restrict__ out, T oscale) {
+  pdl_entry();
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   cheb_last_at<D, T, TO>(g, v, W, x, r, din, first != 0, out, oscale);
@@ -69,6 +73,7 @@ __global__ void __launch_bounds__(BX) k_cheb_last(Geom g, const T* __restrict__ 
 
 template <int D, typename T>
 __global__ void __launch_bounds__(BX) k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ bc) {
+  pdl_entry();
   Vtx<D> v;                               // coarse vertex
   if (!vertex_of_thread<D>(gc, v)) return;
   restrict_at<D, T>(gf, v, rf, bc);
@@ -76,6 +81,7 @@ __global__ void __launch_bounds__(BX) k_restrict(Geom gf, Geom gc, const T* __re
 
 template <int D, typename T>
 __global__ void __launch_bounds__(BX) k_prolong_add(Geom gf, Geom gc, T* __restrict__ xf, const T* __restrict__ xc) {
+  pdl_entry();
   Vtx<D> v;                               // fine vertex
   if (!vertex_of_thread<D>(gf, v)) return;
   prolong_add_at<D, T>(gc, v, xf, xc);
@@ -85,6 +91,7 @@ __global__ void __launch_bounds__(BX) k_prolong_add(Geom gf, Geom gc, T* __restr
 template <typename T>
 __global__ void __launch_bounds__(512) k_coarse_solve(long long nc, const T* __restrict__ A, const T* __restrict__ b,
                                                       T* __restrict__ x) {
+  pdl_entry();
   coarse_rows<T>(nc, A, b, x, threadIdx.x >> 5, blockDim.x >> 5);
 }
 
@@ -191,7 +198,8 @@ __device__ void fused_smooth(const CoarseArgs<T>& a, int l, T* sm, bool x_zero, 
 
 template <int D, typename T>
 __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseArgs<T> a, const T* __restrict__ b_in,
-                                                        const T* x_in, T* x_out) {   // x_in may equal x_out
+                                                        const T* x_in, T* x_out) {
+  pdl_entry();   // x_in may equal x_out
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int L = a.nlev - 1;
@@ -256,6 +264,7 @@ template <int D, typename T, typename TX, typename TY>
 __global__ void __launch_bounds__(BX) k_op_apply(Geom g, const T* __restrict__ W, int axis_only,
                                                  const TX* __restrict__ x, TY* __restrict__ y, T alpha,
                                                  const TY* __restrict__ y0, T beta) {
+  pdl_entry();
   using Tp = Topo<D>;
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
@@ -269,6 +278,7 @@ __global__ void __launch_bounds__(BX) k_op_apply(Geom g, const T* __restrict__ W
 
 template <int D>
 __global__ void k_dense_from_table(Geom g, const double* __restrict__ W, double* __restrict__ A) {
+  pdl_entry();
   using Tp = Topo<D>;
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
@@ -282,6 +292,7 @@ __global__ void k_dense_from_table(Geom g, const double* __restrict__ W, double*
 // pivot p one single-block kernel scales row p and saves the column factors,
 // then one grid-wide kernel eliminates column p from every other row.
 __global__ void k_gj_init(long long n, const double* __restrict__ A, double* __restrict__ w) {
+  pdl_entry();
   const long long n2 = 2 * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n2;
        e += (long long)gridDim.x * blockDim.x) {
@@ -291,6 +302,7 @@ __global__ void k_gj_init(long long n, const double* __restrict__ A, double* __r
 }
 __global__ void __launch_bounds__(1024) k_gj_pivot(long long n, double* __restrict__ w, double* __restrict__ col,
                                                    long long p) {
+  pdl_entry();
   const long long n2 = 2 * n;
   const double piv = w[p * n2 + p];
   __syncthreads();
@@ -298,6 +310,7 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(long long n, double* __restri
   for (long long r = threadIdx.x; r < n; r += blockDim.x) col[r] = (r == p) ? 0.0 : w[r * n2 + p];
 }
 __global__ void k_gj_elim(long long n, double* __restrict__ w, const double* __restrict__ col, long long p) {
+  pdl_entry();
   const long long n2 = 2 * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n2;
        e += (long long)gridDim.x * blockDim.x) {
@@ -306,6 +319,7 @@ __global__ void k_gj_elim(long long n, double* __restrict__ w, const double* __r
   }
 }
 __global__ void k_gj_extract(long long n, const double* __restrict__ w, double* __restrict__ Ainv) {
+  pdl_entry();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n;
        e += (long long)gridDim.x * blockDim.x) {
     const long long r = e / n, c = e % n;
@@ -313,12 +327,78 @@ __global__ void k_gj_extract(long long n, const double* __restrict__ w, double* 
   }
 }
 
-// x = Ainv b by many blocks, a warp per row (the rows' arithmetic is that of
-// the one-block coarse solve)
+// x = Ainv b by many blocks, a warp per row.  Ainv is stored with a padded
+// row stride ld (a multiple of 16 bytes, zeros beyond column nc), so each lane
+// issues GEMV_NPL independent 16-byte loads before it multiplies; b is staged
+// in shared memory, zero-padded to the vector chunk.
+constexpr int GEMV_NPL = 8;          // 16-byte vectors per lane per chunk
+constexpr int GEMV_WARPS = 8;
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int E = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int E = 2; };
 template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_gemv(long long nc, const T* __restrict__ A, const T* __restrict__ b,
-                                                     T* __restrict__ x) {
-  coarse_rows<T>(nc, A, b, x, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), (int)((gridDim.x * blockDim.x) >> 5));
+__device__ __forceinline__ T vec_at(const typename Vec16<T>::type& v, int e);
+template <> __device__ __forceinline__ float vec_at<float>(const float4& v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+template <> __device__ __forceinline__ double vec_at<double>(const double2& v, int e) { return e == 0 ? v.x : v.y; }
+// 16-byte read-only loads kept in program order (volatile), so a lane's loads
+// of one chunk are all in flight before the first multiply
+__device__ __forceinline__ void ld16(const float4* p, float4& v) {
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+}
+__device__ __forceinline__ void ld16(const double2* p, double2& v) {
+  asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GEMV_WARPS * 32) k_coarse_gemv(long long nc, long long ld, const T* __restrict__ A,
+                                                                const T* __restrict__ b, T* __restrict__ x) {
+  pdl_entry();
+  using V = typename Vec16<T>::type;
+  constexpr int E = Vec16<T>::E;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sb = reinterpret_cast<T*>(smraw);
+  const long long nvec = ld / E;
+  const long long chunk = 32LL * GEMV_NPL;
+  const long long nb = ((nvec + chunk - 1) / chunk) * chunk * E;
+  for (long long i = threadIdx.x; i < nb; i += blockDim.x) sb[i] = i < nc ? b[i] : (T)0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long r = (long long)blockIdx.x * GEMV_WARPS + (threadIdx.x >> 5);
+  if (r >= nc) return;
+  const V* Ar = reinterpret_cast<const V*>(A + r * ld);
+  const V* sv = reinterpret_cast<const V*>(sb);
+  T acc = (T)0;
+  auto mac = [&](const V (&a)[GEMV_NPL], long long base) {
+#pragma unroll
+    for (int k = 0; k < GEMV_NPL; ++k) {
+      const V bv = sv[base + lane + 32 * k];
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc = fma(vec_at<T>(a[k], e), vec_at<T>(bv, e), acc);
+    }
+  };
+  long long base = 0;
+  for (; base + chunk <= nvec; base += chunk) {      // full chunks: all loads issued first
+    V a[GEMV_NPL];
+#pragma unroll
+    for (int k = 0; k < GEMV_NPL; ++k) ld16(Ar + base + lane + 32 * k, a[k]);
+    mac(a, base);
+  }
+  if (base < nvec) {                                 // ragged last chunk
+    V a[GEMV_NPL];
+#pragma unroll
+    for (int k = 0; k < GEMV_NPL; ++k) {
+      const long long c = base + lane + 32 * k;
+      a[k] = V{};
+      if (c < nvec) ld16(Ar + c, a[k]);
+    }
+    mac(a, base);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[r] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -333,57 +413,71 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(long long nc, const T* __re
 template <typename T, typename TB>
 void launch_cheb_init(int dim, const Geom& g, const T* dinv, const TB* b, T bscale, T* r, T* d, T inv_th,
                       cudaStream_t s) {
-  if (dim == 2) count_launch(), k_cheb_init<2, T, TB><<<grid_of(2, g), BX, 0, s>>>(g, dinv, b, bscale, r, d, inv_th);
-  else count_launch(), k_cheb_init<3, T, TB><<<grid_of(3, g), BX, 0, s>>>(g, dinv, b, bscale, r, d, inv_th);
+  if (dim == 2) launch_k(k_cheb_init<2, T, TB>, grid_of(2, g), BX, 0, s, g, dinv, b, bscale, r, d, inv_th);
+  else launch_k(k_cheb_init<3, T, TB>, grid_of(3, g), BX, 0, s, g, dinv, b, bscale, r, d, inv_th);
 }
 template <typename T>
 void launch_resid_init(int dim, const Geom& g, const T* W, const T* dinv, const T* b, const T* x, T* r, T* d,
                        T inv_th, cudaStream_t s) {
-  if (dim == 2) count_launch(), k_resid_init<2, T><<<grid_of(2, g), BX, 0, s>>>(g, W, dinv, b, x, r, d, inv_th);
-  else count_launch(), k_resid_init<3, T><<<grid_of(3, g), BX, 0, s>>>(g, W, dinv, b, x, r, d, inv_th);
+  if (dim == 2) launch_k(k_resid_init<2, T>, grid_of(2, g), BX, 0, s, g, W, dinv, b, x, r, d, inv_th);
+  else launch_k(k_resid_init<3, T>, grid_of(3, g), BX, 0, s, g, W, dinv, b, x, r, d, inv_th);
 }
 template <typename T>
 void launch_cheb_step(int dim, const Geom& g, const T* W, const T* dinv, T* x, T* r, const T* d_in, T* d_out,
                       T c1, T c2, bool first, cudaStream_t s) {
-  if (dim == 2) count_launch(), k_cheb_step<2, T><<<grid_of(2, g), BX, 0, s>>>(g, W, dinv, x, r, d_in, d_out, c1, c2, first);
-  else count_launch(), k_cheb_step<3, T><<<grid_of(3, g), BX, 0, s>>>(g, W, dinv, x, r, d_in, d_out, c1, c2, first);
+  if (dim == 2) launch_k(k_cheb_step<2, T>, grid_of(2, g), BX, 0, s, g, W, dinv, x, r, d_in, d_out, c1, c2, first);
+  else launch_k(k_cheb_step<3, T>, grid_of(3, g), BX, 0, s, g, W, dinv, x, r, d_in, d_out, c1, c2, first);
 }
 template <typename T, typename TO>
 void launch_cheb_last(int dim, const Geom& g, const T* W, T* x, T* r, const T* d_in, bool first, TO* out,
                       T oscale, cudaStream_t s) {
-  if (dim == 2) count_launch(), k_cheb_last<2, T, TO><<<grid_of(2, g), BX, 0, s>>>(g, W, x, r, d_in, first, out, oscale);
-  else count_launch(), k_cheb_last<3, T, TO><<<grid_of(3, g), BX, 0, s>>>(g, W, x, r, d_in, first, out, oscale);
+  if (dim == 2) launch_k(k_cheb_last<2, T, TO>, grid_of(2, g), BX, 0, s, g, W, x, r, d_in, first, out, oscale);
+  else launch_k(k_cheb_last<3, T, TO>, grid_of(3, g), BX, 0, s, g, W, x, r, d_in, first, out, oscale);
 }
 template <typename T>
 void launch_restrict(int dim, const Geom& gf, const Geom& gc, const T* rf, T* bc, cudaStream_t s) {
-  if (dim == 2) count_launch(), k_restrict<2, T><<<grid_of(2, gc), BX, 0, s>>>(gf, gc, rf, bc);
-  else count_launch(), k_restrict<3, T><<<grid_of(3, gc), BX, 0, s>>>(gf, gc, rf, bc);
+  if (dim == 2) launch_k(k_restrict<2, T>, grid_of(2, gc), BX, 0, s, gf, gc, rf, bc);
+  else launch_k(k_restrict<3, T>, grid_of(3, gc), BX, 0, s, gf, gc, rf, bc);
 }
 template <typename T>
 void launch_prolong_add(int dim, const Geom& gf, const Geom& gc, T* xf, const T* xc, cudaStream_t s) {
-  if (dim == 2) count_launch(), k_prolong_add<2, T><<<grid_of(2, gf), BX, 0, s>>>(gf, gc, xf, xc);
-  else count_launch(), k_prolong_add<3, T><<<grid_of(3, gf), BX, 0, s>>>(gf, gc, xf, xc);
+  if (dim == 2) launch_k(k_prolong_add<2, T>, grid_of(2, gf), BX, 0, s, gf, gc, xf, xc);
+  else launch_k(k_prolong_add<3, T>, grid_of(3, gf), BX, 0, s, gf, gc, xf, xc);
 }
 template <typename T>
 void launch_coarse_solve(long long nc, const T* Ainv, const T* b, T* x, cudaStream_t s) {
-  if (nc <= 512) {
-    count_launch(), k_coarse_solve<T><<<1, 512, 0, s>>>(nc, Ainv, b, x);
-    return;
-  }
-  const unsigned blocks = (unsigned)((nc + 7) / 8);   // 8 warps (rows) per block
-  count_launch(), k_coarse_gemv<T><<<blocks, 256, 0, s>>>(nc, Ainv, b, x);
+  launch_k(k_coarse_solve<T>, 1, 512, 0, s, nc, Ainv, b, x);
+}
+long long gemv_ld(long long nc, size_t elem) {
+  const long long e = 16 / (long long)elem;
+  return (nc + e - 1) / e * e;
+}
+template <typename T>
+size_t gemv_smem(long long nc) {
+  const long long E = Vec16<T>::E, chunk = 32LL * GEMV_NPL;
+  const long long nvec = gemv_ld(nc, sizeof(T)) / E;
+  return (size_t)(((nvec + chunk - 1) / chunk) * chunk * E) * sizeof(T);
+}
+template <typename T>
+void launch_coarse_gemv(long long nc, long long ld, const T* Ainv, const T* b, T* x, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((nc + GEMV_WARPS - 1) / GEMV_WARPS);
+  launch_k(k_coarse_gemv<T>, blocks, GEMV_WARPS * 32, gemv_smem<T>(nc), s, nc, ld, Ainv, b, x);
+}
+template <typename T>
+cudaError_t prepare_coarse_gemv(long long nc) {
+  return cudaFuncSetAttribute(k_coarse_gemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemv_smem<T>(nc));
 }
 template <typename T, typename TX, typename TY>
 void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha,
                      const TY* y0, T beta, cudaStream_t s) {
-  if (dim == 2) count_launch(), k_op_apply<2, T, TX, TY><<<grid_of(2, g), BX, 0, s>>>(g, W, axis_only, x, y, alpha, y0, beta);
-  else count_launch(), k_op_apply<3, T, TX, TY><<<grid_of(3, g), BX, 0, s>>>(g, W, axis_only, x, y, alpha, y0, beta);
+  if (dim == 2) launch_k(k_op_apply<2, T, TX, TY>, grid_of(2, g), BX, 0, s, g, W, axis_only, x, y, alpha, y0, beta);
+  else launch_k(k_op_apply<3, T, TX, TY>, grid_of(3, g), BX, 0, s, g, W, axis_only, x, y, alpha, y0, beta);
 }
 template <typename T>
 void launch_coarse_vcycle(int dim, const CoarseArgs<T>& a, size_t smem, const T* b_in, const T* x_in, T* x_out,
                           cudaStream_t s) {
-  if (dim == 2) count_launch(), k_coarse_vcycle<2, T><<<1, 1024, smem, s>>>(a, b_in, x_in, x_out);
-  else count_launch(), k_coarse_vcycle<3, T><<<1, 1024, smem, s>>>(a, b_in, x_in, x_out);
+  if (dim == 2) launch_k(k_coarse_vcycle<2, T>, 1, 1024, smem, s, a, b_in, x_in, x_out);
+  else launch_k(k_coarse_vcycle<3, T>, 1, 1024, smem, s, a, b_in, x_in, x_out);
 }
 template <typename T>
 cudaError_t prepare_coarse_vcycle(int dim, size_t smem) {
@@ -399,19 +493,19 @@ template cudaError_t prepare_coarse_vcycle<double>(int, size_t);
 template cudaError_t prepare_coarse_vcycle<float>(int, size_t);
 
 void launch_dense_from_table(int dim, const Geom& g, const double* W, double* A, cudaStream_t s) {
-  if (dim == 2) count_launch(), k_dense_from_table<2><<<grid_of(2, g), BX, 0, s>>>(g, W, A);
-  else count_launch(), k_dense_from_table<3><<<grid_of(3, g), BX, 0, s>>>(g, W, A);
+  if (dim == 2) launch_k(k_dense_from_table<2>, grid_of(2, g), BX, 0, s, g, W, A);
+  else launch_k(k_dense_from_table<3>, grid_of(3, g), BX, 0, s, g, W, A);
 }
 // work: n x 2n array followed by n column factors
 void launch_gauss_jordan(long long n, const double* A, double* work, double* Ainv, cudaStream_t s) {
   double* col = work + 2 * n * n;
   const unsigned blocks = (unsigned)std::min<long long>((2 * n * n + 255) / 256, 4096);
-  count_launch(), k_gj_init<<<blocks, 256, 0, s>>>(n, A, work);
+  launch_k(k_gj_init, blocks, 256, 0, s, n, A, work);
   for (long long p = 0; p < n; ++p) {
-    count_launch(), k_gj_pivot<<<1, 1024, 0, s>>>(n, work, col, p);
-    count_launch(), k_gj_elim<<<blocks, 256, 0, s>>>(n, work, col, p);
+    launch_k(k_gj_pivot, 1, 1024, 0, s, n, work, col, p);
+    launch_k(k_gj_elim, blocks, 256, 0, s, n, work, col, p);
   }
-  count_launch(), k_gj_extract<<<blocks, 256, 0, s>>>(n, work, Ainv);
+  launch_k(k_gj_extract, blocks, 256, 0, s, n, work, Ainv);
 }
 
 #define OK_INST_T(T)                                                                                          \
@@ -421,7 +515,9 @@ void launch_gauss_jordan(long long n, const double* A, double* work, double* Ain
                                     cudaStream_t);                                                             \
   template void launch_restrict<T>(int, const Geom&, const Geom&, const T*, T*, cudaStream_t);                 \
   template void launch_prolong_add<T>(int, const Geom&, const Geom&, T*, const T*, cudaStream_t);              \
-  template void launch_coarse_solve<T>(long long, const T*, const T*, T*, cudaStream_t);
+  template void launch_coarse_solve<T>(long long, const T*, const T*, T*, cudaStream_t);                  \
+  template void launch_coarse_gemv<T>(long long, long long, const T*, const T*, T*, cudaStream_t);        \
+  template cudaError_t prepare_coarse_gemv<T>(long long);
 
 OK_INST_T(double)
 OK_INST_T(float)

@@ -81,13 +81,21 @@ __device__ __forceinline__ void prolong_add_at(const Geom& gc, const Vtx<D>& v, 
   xf[v.idx] = mid ? fma((T)0.5, xc[ci] + xc[cj], xf[v.idx]) : xf[v.idx] + xc[ci];
 }
 
-// x[r] = sum_c A[r][c] b[c] for the rows of this warp (lane-strided, xor-reduced)
+// x[r] = sum_c A[r][c] b[c] for the rows of this warp, xor-reduced.  Lane l
+// takes the 16-byte groups l, l + 32, ... (E = 16 / sizeof(T) columns each, in
+// column order): the order of the many-block GEMV with vector loads.
 template <typename T>
 __device__ __forceinline__ void coarse_rows(long long nc, const T* A, const T* b, T* x, int warp, int nw) {
+  constexpr int E = 16 / sizeof(T);
   const int lane = threadIdx.x & 31;
   for (long long r = warp; r < nc; r += nw) {
     T acc = (T)0;
-    for (long long c = lane; c < nc; c += 32) acc = fma(A[r * nc + c], b[c], acc);
+    for (long long c4 = lane; c4 * E < nc; c4 += 32)
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const long long c = c4 * E + e;
+        if (c < nc) acc = fma(A[r * nc + c], b[c], acc);
+      }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) x[r] = acc;

@@ -1,421 +1,585 @@
-// ok_tile.cu -- shared-memory tile kernels with temporal blocking (2D grids).
+// ok_tile.cu -- register-strip kernels with temporal blocking (2D grids).
 //
-// One thread block owns a TILE x TILE square of vertices of one multigrid
-// level and loads it with a halo wide enough to take several dependent steps
-// without a grid-wide synchronisation: the halo points are recomputed by the
-// neighbouring blocks (redundant work) instead of exchanged.  Every point
-// update goes through the per-vertex bodies of ok_stencil.cuh, so the result
-// is bitwise the same as the one-kernel-per-step path.
+// One thread block computes a CW x CH window of vertices of one multigrid
+// level: the (CW - 2H) x (CH - 2H) vertices it owns and a halo of H on each
+// side, so that H dependent stencil steps run without a grid-wide
+// synchronisation (the halo is recomputed by the neighbouring blocks instead
+// of exchanged).  Thread (column lx, chunk ty) holds the RY vertices
+// lx x [ty RY, ty RY + RY) of every state vector in registers; before each
+// stencil step it writes its own values into a shared-memory exchange buffer
+// (two buffers, used alternately, so one barrier per step suffices) and reads
+// back only what lies in the columns lx - 1 and lx + 1 and the two rows
+// beyond its strip: 2 RY + 4 shared-memory reads and RY writes per RY
+// vertices, the rest of the 7-point stencil comes from its own registers.
+// Each step's result is garbage in one more ring of the window (the
+// outermost ring reads the never-written pad of the exchange buffer); H is
+// the number of dependent stencil steps, so the owned vertices stay exact.
 //
-//   k_tile_pre   two Chebyshev--Jacobi pre-smoothing steps on S_hat from x
-//                (or from zero), the residual, and its restriction P^T r to
-//                the coarser level (halo 4);
-//   k_tile_post  prolongation x += P x_c and two post-smoothing steps
-//                (halo 3), optionally M x (the middle factor of
-//                S~^{-1} = S_hat^{-1} M S_hat^{-1}) and a cast of x to an
-//                output vector;
-//   k_tile_amass q Chebyshev steps on M (A~^{-1} r1, Sec. 3) and the
-//                preconditioner's C-step t = r2 - C A~^{-1} r1 (eqn prec)
-//                (halo q).
-// x is read from one buffer and written to another (ping-pong), because
-// other blocks read the old x in their halos while this block writes.
+// Every vertex update is the arithmetic of the per-vertex bodies of
+// ok_stencil.cuh in the same order, so results are bitwise those of the
+// one-kernel-per-step path.
+//
+//   k_strip_pre   two Chebyshev--Jacobi pre-smoothing steps on S_hat from x
+//                 (or from zero), the residual, and its restriction P^T r to
+//                 the coarser level (H = 4);
+//   k_strip_post  prolongation x += P x_c and two post-smoothing steps, then
+//                 optionally M x (the middle factor of
+//                 S~^{-1} = S_hat^{-1} M S_hat^{-1}) and a cast of x (H = 3);
+//   k_strip_amass QTILE Chebyshev steps on M (A~^{-1} r1, Sec. 3) and the
+//                 preconditioner's C-step t = r2 - C A~^{-1} r1 (eqn prec)
+//                 (H = QTILE).
+// x is read from one buffer and written to another (ping-pong), because other
+// blocks read the old x in their halos while this block writes.
 #include "ok_internal.cuh"
 #include "ok_kernels.h"
 #include "ok_stencil.cuh"
 
 namespace okg {
 
-constexpr int TILE = 32;
-constexpr int TILE_THREADS = 256;
-constexpr int QTILE = 10;   // mass Chebyshev steps handled by the tile kernel
+constexpr int QTILE = 10;   // mass Chebyshev steps handled by the strip kernel
+constexpr int NTAB = Topo<2>::NCLASS * Topo<2>::NOFF;
 
-// A tile of side S = TILE + 2H around the block's owned TILE x TILE vertices.
-template <int TL, int S> struct Frame {
-  static constexpr int H = (S - TL) / 2;
-  int f0x, f0y;    // global coordinates of the first owned vertex
-  int n;           // cells per side of the level
-  long long gsy;   // global row stride
-  Geom lg;         // local geometry (row stride S) for the stencil bodies
+// Window geometry: CW columns, CH = RY * NCH rows, halo H.
+template <int CW_, int RY_, int NCH_, int H_> struct SG {
+  static constexpr int CW = CW_, RY = RY_, NCH = NCH_, H = H_;
+  static constexpr int CH = RY * NCH;
+  static constexpr int OW = CW - 2 * H, OH = CH - 2 * H;   // owned extents
+  static constexpr int SW = CW + 2;                        // exchange row stride (pad column each side)
+  static constexpr int SB = (CH + 2) * SW;                 // one exchange buffer (pad row above and below)
+  static constexpr int NT = CW * NCH;                      // threads
+  static_assert(OW > 0 && OH > 0, "halo too wide for the window");
+  static_assert(CW % 32 == 0, "a warp covers 32 consecutive columns of one chunk");
 };
 
-template <int TL, int S>
-__device__ __forceinline__ Frame<TL, S> make_frame(const Geom& g) {
-  Frame<TL, S> F;
-  F.f0x = blockIdx.x * TL;
-  F.f0y = blockIdx.y * TL;
-  F.n = g.n;
-  F.gsy = g.sy;
-  F.lg.n = g.n;
-  F.lg.n1 = S;
-  F.lg.nv = (long long)S * S;
-  F.lg.sy = S;
-  F.lg.sz = 0;
-  return F;
+// window sizes (CW, RY, NCH) per precision: large levels, small levels, the
+// mass kernel; the float ones may be set at compile time
+// (measured on the 1025^2 hierarchy: short strips and many threads win, the
+// kernels being latency- rather than throughput-bound)
+#ifndef OK_STRIP_F_BIG
+#define OK_STRIP_F_BIG 64, 8, 4
+#endif
+#ifndef OK_STRIP_F_SMALL
+#define OK_STRIP_F_SMALL 32, 2, 16
+#endif
+#ifndef OK_STRIP_F_MASS
+#define OK_STRIP_F_MASS 64, 4, 16
+#endif
+template <typename T> struct StripCfg;
+template <> struct StripCfg<float> {
+  template <int H> using Big = SG<OK_STRIP_F_BIG, H>;
+  template <int H> using Small = SG<OK_STRIP_F_SMALL, H>;
+  using Mass = SG<OK_STRIP_F_MASS, QTILE>;
+};
+template <> struct StripCfg<double> {
+  template <int H> using Big = SG<64, 4, 10, H>;
+  template <int H> using Small = SG<32, 4, 8, H>;
+  using Mass = SG<64, 4, 12, QTILE>;
+};
+
+// this thread's strip
+struct Pos {
+  int lx, ly0;     // local column, first local row
+  int gx, gy0;     // global coordinates of (lx, ly0)
+  int cx;          // axis class of the column
+  bool colin;      // 0 <= gx <= n
+};
+
+template <class G>
+__device__ __forceinline__ Pos strip_pos(int n) {
+  Pos p;
+  p.lx = threadIdx.x % G::CW;
+  p.ly0 = (threadIdx.x / G::CW) * G::RY;
+  p.gx = blockIdx.x * G::OW - G::H + p.lx;
+  p.gy0 = blockIdx.y * G::OH - G::H + p.ly0;
+  p.colin = p.gx >= 0 && p.gx <= n;
+  p.cx = axis_class(p.gx, n);
+  return p;
 }
 
-// Is every vertex of the tile (halo included) an interior vertex?
-template <int TL, int S>
-__device__ __forceinline__ bool tile_interior(const Frame<TL, S>& F) {
-  constexpr int H = Frame<TL, S>::H;
-  return F.f0x - H >= 1 && F.f0y - H >= 1 && F.f0x - H + S - 1 <= F.n - 1 && F.f0y - H + S - 1 <= F.n - 1;
+// every vertex of the window strictly inside the domain (interior class)?
+template <class G>
+__device__ __forceinline__ bool strip_interior(int n) {
+  const int x0 = blockIdx.x * G::OW - G::H, y0 = blockIdx.y * G::OH - G::H;
+  return x0 >= 1 && y0 >= 1 && x0 + G::CW - 1 <= n - 1 && y0 + G::CH - 1 <= n - 1;
 }
 
-// local (lx, ly) -> vertex record (local index, global coordinates, class);
-// INT: the tile is interior, so the class is the interior one everywhere
-template <int TL, int S, bool INT>
-__device__ __forceinline__ bool tile_vertex(const Frame<TL, S>& F, int lx, int ly, Vtx<2>& v) {
-  constexpr int H = Frame<TL, S>::H;
-  const int gx = F.f0x - H + lx, gy = F.f0y - H + ly;
-  if (!INT && (gx < 0 || gy < 0 || gx > F.n || gy > F.n)) return false;
-  v.idx = (long long)ly * S + lx;
-  v.p[0] = gx;
-  v.p[1] = gy;
-  v.p[2] = 0;
-  v.c[0] = INT ? 1 : axis_class(gx, F.n);
-  v.c[1] = INT ? 1 : axis_class(gy, F.n);
-  v.c[2] = 1;
-  v.cls = INT ? 4 : v.c[0] + 3 * v.c[1];
-  return true;
+__device__ __forceinline__ bool row_in(const Pos& p, int i, int n) {
+  const int gy = p.gy0 + i;
+  return p.colin && gy >= 0 && gy <= n;
 }
-template <int TL, int S>
-__device__ __forceinline__ long long gidx(const Frame<TL, S>& F, const Vtx<2>& v) {
-  return v.p[0] + F.gsy * v.p[1];
+template <class G>
+__device__ __forceinline__ bool owned(const Pos& p, int i) {
+  const int ly = p.ly0 + i;
+  return p.lx >= G::H && p.lx < G::CW - G::H && ly >= G::H && ly < G::CH - G::H;
 }
 
-// fn(v) for every in-domain vertex of the local square [LO, HI)^2, then a barrier
-template <int TL, int S, int LO, int HI, bool INT, typename Fn>
-__device__ __forceinline__ void tile_loop(const Frame<TL, S>& F, Fn&& fn) {
-  constexpr int W = HI - LO;
-  for (int t = threadIdx.x; t < W * W; t += TILE_THREADS) {
-    Vtx<2> v;
-    if (tile_vertex<TL, S, INT>(F, LO + t % W, LO + t / W, v)) fn(v);
+// ---- exchange of one state vector through shared memory -------------------
+template <class G, typename T>
+__device__ __forceinline__ void xput(T* buf, const Pos& p, const T (&v)[G::RY]) {
+#pragma unroll
+  for (int i = 0; i < G::RY; ++i) buf[(p.ly0 + i + 1) * G::SW + p.lx + 1] = v[i];
+}
+
+template <class G, typename T> struct Nb {
+  T dn, up;              // own column, rows ly0 - 1 and ly0 + RY
+  T L[G::RY + 1];        // column lx - 1, rows ly0 - 1 .. ly0 + RY - 1
+  T R[G::RY + 1];        // column lx + 1, rows ly0 .. ly0 + RY
+};
+
+template <class G, typename T>
+__device__ __forceinline__ void xget(const T* buf, const Pos& p, Nb<G, T>& nb) {
+  const T* c = buf + p.ly0 * G::SW + p.lx + 1;     // own column, local row ly0 - 1
+  nb.dn = c[0];
+  nb.up = c[(G::RY + 1) * G::SW];
+#pragma unroll
+  for (int j = 0; j <= G::RY; ++j) {
+    nb.L[j] = c[j * G::SW - 1];
+    nb.R[j] = c[(j + 1) * G::SW + 1];
   }
-  __syncthreads();
 }
 
-// copy a level's class tables into shared memory (read with warp-uniform addresses)
+// the 7 stencil values of row i in offset order (self, +x, -x, +y, -y, +xy,
+// -xy), zero outside the domain as load_nb gives them
+template <class G, typename T, bool INT>
+__device__ __forceinline__ void nb_row(const T (&v)[G::RY], const Nb<G, T>& nb, int i, int cx, int cy,
+                                       T (&xs)[Topo<2>::NOFF]) {
+  xs[0] = v[i];
+  xs[1] = nb.R[i];
+  xs[2] = nb.L[i + 1];
+  xs[3] = i + 1 < G::RY ? v[i + 1] : nb.up;
+  xs[4] = i > 0 ? v[i - 1] : nb.dn;
+  xs[5] = nb.R[i + 1];
+  xs[6] = nb.L[i];
+  if constexpr (!INT) {
+    const int c[3] = {cx, cy, 1};
+    static_for<1, Topo<2>::NOFF>([&](auto O) {
+      constexpr int o = decltype(O)::value;
+      if (!nb_valid<2, o>(c)) xs[o] = (T)0;
+    });
+  }
+}
+
+template <typename T, bool INT>
+__device__ __forceinline__ T sdot(const RegW<2, T>& rw, const T* sW, int cls, const T (&xs)[Topo<2>::NOFF]) {
+  if constexpr (INT) return dot_r<2, T>(rw, xs);
+  else return dot_w<2, Topo<2>::NOFF>(sW, cls, xs);
+}
+
+template <bool INT>
+__device__ __forceinline__ int row_class(const Pos& p, int i, int n, int& cy) {
+  cy = INT ? 1 : axis_class(p.gy0 + i, n);
+  return INT ? 4 : p.cx + 3 * cy;
+}
+
 template <typename T>
-__device__ __forceinline__ void load_tables(T* sW, T* sD, const T* W, const T* dinv) {
-  for (int i = threadIdx.x; i < Topo<2>::NCLASS * Topo<2>::NOFF; i += TILE_THREADS) sW[i] = W[i];
-  for (int i = threadIdx.x; i < Topo<2>::NCLASS; i += TILE_THREADS) sD[i] = dinv[i];
+__device__ __forceinline__ void load_table(T* s, const T* g, int count, int nt) {
+  for (int i = threadIdx.x; i < count; i += nt) s[i] = g[i];
 }
 
 // ---------------------------------------------------------------------------
 // pre-smoothing (2 steps) + restriction
 // ---------------------------------------------------------------------------
-template <typename T, int TL, bool INT>
-__device__ __forceinline__ void tile_pre_body(const TileSmooth<T>& a, const Frame<TL, TL + 8>& F, T* X, T* B, T* R, T* D0,
-                                              T* D1, const T* sW, const T* sD, const T* x_in, const T* b,
-                                              T* x_out, T* bc) {
-  constexpr int S = TL + 8;
+template <typename T, class G, bool INT>
+__device__ __forceinline__ void strip_pre_body(const TileSmooth<T>& a, const Pos& p, T* buf0, T* buf1,
+                                               const T* sW, const T* sD, const T* x_in, const T* b, T* x_out,
+                                               T* bc) {
+  constexpr int RY = G::RY;
+  const int n = a.g.n;
+  const long long sy = a.g.sy;
   const bool xz = (x_in == nullptr);
-  // all global loads of this thread first (in flight together), then the stores
-  constexpr int NL = (S * S + TILE_THREADS - 1) / TILE_THREADS;
-  T xr[NL], br[NL];
+  T bb[RY], x[RY], r[RY], d[RY];
 #pragma unroll
-  for (int k = 0; k < NL; ++k) {
-    const int t = threadIdx.x + k * TILE_THREADS;
-    Vtx<2> v;
-    xr[k] = (T)0;
-    br[k] = (T)0;
-    if (t < S * S && tile_vertex<TL, S, INT>(F, t % S, t / S, v)) {
-      const long long gi = gidx(F, v);
-      br[k] = b[gi];
-      if (!xz) xr[k] = x_in[gi];
+  for (int i = 0; i < RY; ++i) {
+    const bool in = INT || row_in(p, i, n);
+    const long long gi = p.gx + sy * (p.gy0 + i);
+    bb[i] = in ? b[gi] : (T)0;
+    x[i] = (in && !xz) ? x_in[gi] : (T)0;
+  }
+  if (!xz) xput<G>(buf0, p, x);
+  __syncthreads();                                  // tables (and x) visible
+  RegW<2, T> rw{};
+  if constexpr (INT) rw = reg_weights<2, T>(sW, sD, 4);
+  Nb<G, T> nb;
+  if (xz) {
+#pragma unroll
+    for (int i = 0; i < RY; ++i) {                  // cheb_init
+      int cy;
+      const int cls = row_class<INT>(p, i, n, cy);
+      const T dv = INT ? rw.dinv : sD[cls];
+      T rr = bb[i] * (T)1;
+      r[i] = rr;
+      d[i] = dv * rr * a.inv_th;
+    }
+  } else {
+    xget<G>(buf0, p, nb);
+#pragma unroll
+    for (int i = 0; i < RY; ++i) {                  // resid_init
+      int cy;
+      const int cls = row_class<INT>(p, i, n, cy);
+      const T dv = INT ? rw.dinv : sD[cls];
+      T xs[Topo<2>::NOFF];
+      nb_row<G, T, INT>(x, nb, i, p.cx, cy, xs);
+      T rr = bb[i] - sdot<T, INT>(rw, sW, cls, xs);
+      r[i] = rr;
+      d[i] = dv * rr * a.inv_th;
     }
   }
-#pragma unroll
-  for (int k = 0; k < NL; ++k) {
-    const int t = threadIdx.x + k * TILE_THREADS;
-    if (t < S * S) {
-      X[t] = xr[k];
-      B[t] = br[k];
-    }
-  }
+  // first smoothing step (cheb_step, first when x started from zero)
+  T dn[RY];
+  xput<G>(buf1, p, d);
   __syncthreads();
-  const Geom& lg = F.lg;
-  const RegW<2, T> rw = reg_weights<2, T>(sW, sD, 4);   // interior class, used when INT
-  if (xz)
-    tile_loop<TL, S, 1, S - 1, INT>(F, [&](const Vtx<2>& v) {
-      if constexpr (INT) cheb_init_r<2, T>(v, rw, B, R, D0, a.inv_th);
-      else cheb_init_at<2, T, T>(v, sD, B, (T)1, R, D0, a.inv_th);
-    });
-  else
-    tile_loop<TL, S, 1, S - 1, INT>(F, [&](const Vtx<2>& v) {
-      if constexpr (INT) resid_init_r<2, T>(lg, v, rw, B, X, R, D0, a.inv_th);
-      else resid_init_at<2, T>(lg, v, sW, sD, B, X, R, D0, a.inv_th);
-    });
-  tile_loop<TL, S, 2, S - 2, INT>(F, [&](const Vtx<2>& v) {
-    if constexpr (INT) cheb_step_r<2, T>(lg, v, rw, X, R, D0, D1, a.c1, a.c2, xz);
-    else cheb_step_at<2, T>(lg, v, sW, sD, X, R, D0, D1, a.c1, a.c2, xz);
-  });
-  tile_loop<TL, S, 3, S - 3, INT>(F, [&](const Vtx<2>& v) {
-    if constexpr (INT) cheb_last_r<2, T>(lg, v, rw, X, R, D1, false);
-    else cheb_last_at<2, T, T>(lg, v, sW, X, R, D1, false, (T*)nullptr, (T)1);
-  });
-  // restriction for the coarse vertices whose fine centre this block owns
-  const int nc = a.gc.n;
-  for (int t = threadIdx.x; t < (TL / 2) * (TL / 2); t += TILE_THREADS) {
-    const int cx = blockIdx.x * (TL / 2) + t % (TL / 2), cy = blockIdx.y * (TL / 2) + t / (TL / 2);
-    if (!INT && (cx > nc || cy > nc)) continue;
-    Vtx<2> vc;
-    vc.c[0] = INT ? 1 : axis_class(cx, nc);
-    vc.c[1] = INT ? 1 : axis_class(cy, nc);
-    vc.c[2] = 1;
-    const long long fc = (long long)(2 * cy - F.f0y + Frame<TL, S>::H) * S + (2 * cx - F.f0x + Frame<TL, S>::H);
-    T acc = (T)0;
-    static_for<1, Topo<2>::NOFF>([&](auto O) {
-      constexpr int o = decltype(O)::value;
-      if (nb_valid<2, o>(vc.c)) acc += R[fc + nb_delta<2, o>(lg)];
-    });
-    bc[cx + a.gc.sy * cy] = fma((T)0.5, acc, R[fc]);
+  xget<G>(buf1, p, nb);
+#pragma unroll
+  for (int i = 0; i < RY; ++i) {
+    int cy;
+    const int cls = row_class<INT>(p, i, n, cy);
+    const T dv = INT ? rw.dinv : sD[cls];
+    T xs[Topo<2>::NOFF];
+    nb_row<G, T, INT>(d, nb, i, p.cx, cy, xs);
+    x[i] = (xz ? (T)0 : x[i]) + xs[0];
+    T rr = r[i] - sdot<T, INT>(rw, sW, cls, xs);
+    r[i] = rr;
+    dn[i] = fma(a.c1, xs[0], a.c2 * (dv * rr));
   }
-  tile_loop<TL, S, Frame<TL, S>::H, Frame<TL, S>::H + TL, INT>(F, [&](const Vtx<2>& v) { x_out[gidx(F, v)] = X[v.idx]; });
+  // last smoothing step, keeping the residual (cheb_last with r)
+  xput<G>(buf0, p, dn);
+  __syncthreads();
+  xget<G>(buf0, p, nb);
+#pragma unroll
+  for (int i = 0; i < RY; ++i) {
+    int cy;
+    const int cls = row_class<INT>(p, i, n, cy);
+    T xs[Topo<2>::NOFF];
+    nb_row<G, T, INT>(dn, nb, i, p.cx, cy, xs);
+    T xx = x[i] + xs[0];
+    r[i] = r[i] - sdot<T, INT>(rw, sW, cls, xs);
+    x[i] = xx;
+  }
+  // restriction (restrict_at) at the coarse vertices whose fine centre this
+  // block owns, and the owned part of x
+  xput<G>(buf1, p, r);
+  __syncthreads();
+  xget<G>(buf1, p, nb);
+  const long long scy = a.gc.sy;
+#pragma unroll
+  for (int i = 0; i < RY; ++i) {
+    const int gy = p.gy0 + i;
+    if (!owned<G>(p, i) || !(INT || row_in(p, i, n))) continue;
+    x_out[p.gx + sy * gy] = x[i];
+    if ((p.gx & 1) || (gy & 1)) continue;
+    int cy;
+    row_class<INT>(p, i, n, cy);
+    T xs[Topo<2>::NOFF];
+    nb_row<G, T, INT>(r, nb, i, p.cx, cy, xs);
+    T acc = (T)0;
+#pragma unroll
+    for (int o = 1; o < Topo<2>::NOFF; ++o) acc += xs[o];     // zero where restrict_at skips
+    bc[(p.gx >> 1) + scy * (gy >> 1)] = fma((T)0.5, acc, xs[0]);
+  }
 }
 
-template <typename T, int TL>
-__global__ void __launch_bounds__(TILE_THREADS) k_tile_pre(TileSmooth<T> a, const T* __restrict__ x_in,
-                                                           const T* __restrict__ b, T* __restrict__ x_out,
-                                                           T* __restrict__ bc) {
+template <typename T, class G>
+__global__ void __launch_bounds__(G::NT) k_strip_pre(TileSmooth<T> a, const T* __restrict__ x_in,
+                                                      const T* __restrict__ b, T* __restrict__ x_out,
+                                                      T* __restrict__ bc) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int S = TL + 8, SS = S * S;
-  const Frame<TL, S> F = make_frame<TL, S>(a.g);
-  T* X = reinterpret_cast<T*>(smraw);
-  T* B = X + SS;
-  T* R = B + SS;
-  T* D0 = R + SS;
-  T* D1 = D0 + SS;
-  T* sW = D1 + SS;
-  T* sD = sW + Topo<2>::NCLASS * Topo<2>::NOFF;
-  load_tables<T>(sW, sD, a.W, a.dinv);
-  if (tile_interior(F)) tile_pre_body<T, TL, true>(a, F, X, B, R, D0, D1, sW, sD, x_in, b, x_out, bc);
-  else tile_pre_body<T, TL, false>(a, F, X, B, R, D0, D1, sW, sD, x_in, b, x_out, bc);
+  T* buf0 = reinterpret_cast<T*>(smraw);
+  T* buf1 = buf0 + G::SB;
+  T* sW = buf1 + G::SB;
+  T* sD = sW + NTAB;
+  load_table<T>(sW, a.W, NTAB, G::NT);
+  load_table<T>(sD, a.dinv, Topo<2>::NCLASS, G::NT);
+  const Pos p = strip_pos<G>(a.g.n);
+  if (strip_interior<G>(a.g.n)) strip_pre_body<T, G, true>(a, p, buf0, buf1, sW, sD, x_in, b, x_out, bc);
+  else strip_pre_body<T, G, false>(a, p, buf0, buf1, sW, sD, x_in, b, x_out, bc);
 }
 
 // ---------------------------------------------------------------------------
 // prolongation + post-smoothing (2 steps) [+ M x] [+ cast of x]
 // ---------------------------------------------------------------------------
-template <typename T, typename TO, int TL, bool INT>
-__device__ __forceinline__ void tile_post_body(const TileSmooth<T>& a, const Frame<TL, TL + 6>& F, T* X, T* B, T* R, T* D0,
-                                               T* D1, const T* sW, const T* sD, const T* sM, const T* x_in,
-                                               const T* xc, const T* b, T* x_out, T* mx_out, TO* out, T oscale) {
-  constexpr int S = TL + 6;
-  // all global loads of this thread first (in flight together), then the stores
-  constexpr int NL = (S * S + TILE_THREADS - 1) / TILE_THREADS;
-  T xr[NL], br[NL];
+template <typename T, typename TO, class G, bool INT>
+__device__ __forceinline__ void strip_post_body(const TileSmooth<T>& a, const Pos& p, T* buf0, T* buf1,
+                                                const T* sW, const T* sD, const T* sM, const T* x_in,
+                                                const T* xc, const T* b, T* x_out, T* mx_out, TO* out,
+                                                T oscale) {
+  constexpr int RY = G::RY;
+  const int n = a.g.n;
+  const long long sy = a.g.sy, scy = a.gc.sy;
+  T bb[RY], x[RY], r[RY], d[RY];
+  const int hx = p.gx >> 1, ox = p.gx & 1;
 #pragma unroll
-  for (int k = 0; k < NL; ++k) {
-    const int t = threadIdx.x + k * TILE_THREADS;
-    Vtx<2> v;
-    xr[k] = (T)0;
-    br[k] = (T)0;
-    if (t < S * S && tile_vertex<TL, S, INT>(F, t % S, t / S, v)) {
-      const long long gi = gidx(F, v);
-      br[k] = b[gi];
+  for (int i = 0; i < RY; ++i) {
+    const bool in = INT || row_in(p, i, n);
+    const int gy = p.gy0 + i;
+    const long long gi = p.gx + sy * gy;
+    bb[i] = (T)0;
+    x[i] = (T)0;
+    if (in) {
+      bb[i] = b[gi];
       const T xv = x_in[gi];
       // prolongation, as prolong_add_at
-      const long long ci = (long long)(v.p[0] >> 1) + a.gc.sy * (v.p[1] >> 1);
-      const long long cj = (long long)((v.p[0] >> 1) + (v.p[0] & 1)) + a.gc.sy * ((v.p[1] >> 1) + (v.p[1] & 1));
-      const bool mid = (v.p[0] & 1) || (v.p[1] & 1);
+      const int hy = gy >> 1, oy = gy & 1;
+      const long long ci = (long long)hx + scy * hy;
+      const long long cj = (long long)(hx + ox) + scy * (hy + oy);
+      const bool mid = ox || oy;
       const T xci = xc[ci], xcj = xc[cj];
-      xr[k] = mid ? fma((T)0.5, xci + xcj, xv) : xv + xci;
+      x[i] = mid ? fma((T)0.5, xci + xcj, xv) : xv + xci;
     }
+  }
+  xput<G>(buf0, p, x);
+  __syncthreads();                                  // tables and x visible
+  RegW<2, T> rw{};
+  if constexpr (INT) rw = reg_weights<2, T>(sW, sD, 4);
+  Nb<G, T> nb;
+  xget<G>(buf0, p, nb);
+#pragma unroll
+  for (int i = 0; i < RY; ++i) {                    // resid_init
+    int cy;
+    const int cls = row_class<INT>(p, i, n, cy);
+    const T dv = INT ? rw.dinv : sD[cls];
+    T xs[Topo<2>::NOFF];
+    nb_row<G, T, INT>(x, nb, i, p.cx, cy, xs);
+    T rr = bb[i] - sdot<T, INT>(rw, sW, cls, xs);
+    r[i] = rr;
+    d[i] = dv * rr * a.inv_th;
+  }
+  T dn[RY];
+  xput<G>(buf1, p, d);
+  __syncthreads();
+  xget<G>(buf1, p, nb);
+#pragma unroll
+  for (int i = 0; i < RY; ++i) {                    // cheb_step (not first)
+    int cy;
+    const int cls = row_class<INT>(p, i, n, cy);
+    const T dv = INT ? rw.dinv : sD[cls];
+    T xs[Topo<2>::NOFF];
+    nb_row<G, T, INT>(d, nb, i, p.cx, cy, xs);
+    x[i] = x[i] + xs[0];
+    T rr = r[i] - sdot<T, INT>(rw, sW, cls, xs);
+    r[i] = rr;
+    dn[i] = fma(a.c1, xs[0], a.c2 * (dv * rr));
   }
 #pragma unroll
-  for (int k = 0; k < NL; ++k) {
-    const int t = threadIdx.x + k * TILE_THREADS;
-    if (t < S * S) {
-      X[t] = xr[k];
-      B[t] = br[k];
+  for (int i = 0; i < RY; ++i) {                    // cheb_last without the residual
+    T xx = x[i] + dn[i];
+    x[i] = xx;
+  }
+#pragma unroll
+  for (int i = 0; i < RY; ++i) {
+    if (!owned<G>(p, i) || !(INT || row_in(p, i, n))) continue;
+    const long long gi = p.gx + sy * (p.gy0 + i);
+    x_out[gi] = x[i];
+    if (out) out[gi] = (TO)(x[i] * oscale);
+  }
+  if (mx_out) {                                     // M x (op_apply with alpha = 1)
+    xput<G>(buf0, p, x);
+    __syncthreads();
+    xget<G>(buf0, p, nb);
+#pragma unroll
+    for (int i = 0; i < RY; ++i) {
+      if (!owned<G>(p, i) || !(INT || row_in(p, i, n))) continue;
+      int cy;
+      const int cls = row_class<INT>(p, i, n, cy);
+      T xs[Topo<2>::NOFF];
+      nb_row<G, T, INT>(x, nb, i, p.cx, cy, xs);
+      T acc = dot_w<2, Topo<2>::NOFF>(sM, cls, xs);
+      acc *= (T)1;
+      mx_out[p.gx + sy * (p.gy0 + i)] = acc;
     }
   }
-  __syncthreads();
-  const Geom& lg = F.lg;
-  const RegW<2, T> rw = reg_weights<2, T>(sW, sD, 4);   // interior class, used when INT
-  tile_loop<TL, S, 1, S - 1, INT>(F, [&](const Vtx<2>& v) {
-    if constexpr (INT) resid_init_r<2, T>(lg, v, rw, B, X, R, D0, a.inv_th);
-    else resid_init_at<2, T>(lg, v, sW, sD, B, X, R, D0, a.inv_th);
-  });
-  tile_loop<TL, S, 2, S - 2, INT>(F, [&](const Vtx<2>& v) {
-    if constexpr (INT) cheb_step_r<2, T>(lg, v, rw, X, R, D0, D1, a.c1, a.c2, false);
-    else cheb_step_at<2, T>(lg, v, sW, sD, X, R, D0, D1, a.c1, a.c2, false);
-  });
-  tile_loop<TL, S, 2, S - 2, INT>(F, [&](const Vtx<2>& v) {
-    if constexpr (INT) cheb_last_r<2, T>(lg, v, rw, X, (T*)nullptr, D1, false);
-    else cheb_last_at<2, T, T>(lg, v, sW, X, (T*)nullptr, D1, false, (T*)nullptr, (T)1);
-  });
-  tile_loop<TL, S, Frame<TL, S>::H, Frame<TL, S>::H + TL, INT>(F, [&](const Vtx<2>& v) {
-    const long long gi = gidx(F, v);
-    x_out[gi] = X[v.idx];
-    if (out) out[gi] = (TO)(X[v.idx] * oscale);
-    if (mx_out) {
-      T xs[Topo<2>::NOFF];
-      load_nb<2>(X, lg, v, xs);
-      T acc = dot_w<2, Topo<2>::NOFF>(sM, v.cls, xs);
-      acc *= (T)1;
-      mx_out[gi] = acc;
-    }
-  });
 }
 
-template <typename T, typename TO, int TL>
-__global__ void __launch_bounds__(TILE_THREADS) k_tile_post(TileSmooth<T> a, const T* __restrict__ x_in,
-                                                            const T* __restrict__ xc, const T* __restrict__ b,
-                                                            T* __restrict__ x_out, T* __restrict__ mx_out,
-                                                            TO* __restrict__ out, T oscale) {
+template <typename T, typename TO, class G>
+__global__ void __launch_bounds__(G::NT) k_strip_post(TileSmooth<T> a, const T* __restrict__ x_in,
+                                                       const T* __restrict__ xc, const T* __restrict__ b,
+                                                       T* __restrict__ x_out, T* __restrict__ mx_out,
+                                                       TO* __restrict__ out, T oscale) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int S = TL + 6, SS = S * S;
-  const Frame<TL, S> F = make_frame<TL, S>(a.g);
-  T* X = reinterpret_cast<T*>(smraw);
-  T* B = X + SS;
-  T* R = B + SS;
-  T* D0 = R + SS;
-  T* D1 = D0 + SS;
-  T* sW = D1 + SS;
-  T* sD = sW + Topo<2>::NCLASS * Topo<2>::NOFF;
+  T* buf0 = reinterpret_cast<T*>(smraw);
+  T* buf1 = buf0 + G::SB;
+  T* sW = buf1 + G::SB;
+  T* sD = sW + NTAB;
   T* sM = sD + Topo<2>::NCLASS;
-  load_tables<T>(sW, sD, a.W, a.dinv);
-  if (mx_out)
-    for (int i = threadIdx.x; i < Topo<2>::NCLASS * Topo<2>::NOFF; i += TILE_THREADS) sM[i] = a.WM[i];
-  if (tile_interior(F)) tile_post_body<T, TO, TL, true>(a, F, X, B, R, D0, D1, sW, sD, sM, x_in, xc, b, x_out, mx_out, out, oscale);
-  else tile_post_body<T, TO, TL, false>(a, F, X, B, R, D0, D1, sW, sD, sM, x_in, xc, b, x_out, mx_out, out, oscale);
+  load_table<T>(sW, a.W, NTAB, G::NT);
+  load_table<T>(sD, a.dinv, Topo<2>::NCLASS, G::NT);
+  if (mx_out) load_table<T>(sM, a.WM, NTAB, G::NT);
+  const Pos p = strip_pos<G>(a.g.n);
+  if (strip_interior<G>(a.g.n))
+    strip_post_body<T, TO, G, true>(a, p, buf0, buf1, sW, sD, sM, x_in, xc, b, x_out, mx_out, out, oscale);
+  else
+    strip_post_body<T, TO, G, false>(a, p, buf0, buf1, sW, sD, sM, x_in, xc, b, x_out, mx_out, out, oscale);
 }
 
 // ---------------------------------------------------------------------------
 // QTILE Chebyshev steps on M + C-step:  z1 = A~^{-1} r1,  t = r2 - C z1
 // ---------------------------------------------------------------------------
-template <typename T, typename TZ, bool INT>
-__device__ __forceinline__ void tile_amass_body(const TileMass<T>& a, const Frame<TILE, TILE + 2 * QTILE>& F, T* X, T* B,
-                                                T* R, T* D0, T* D1, const T* sW, const T* sD, const double* v,
-                                                TZ* z1, T* t_out) {
-  constexpr int S = TILE + 2 * QTILE, Q = QTILE;
-  // all global loads of this thread first (in flight together), then the stores
-  constexpr int NL = (S * S + TILE_THREADS - 1) / TILE_THREADS;
-  double br[NL];
+template <typename T, typename TZ, class G, bool INT>
+__device__ __forceinline__ void strip_amass_body(const TileMass<T>& a, const Pos& p, T* buf0, T* buf1,
+                                                 const T* sW, const T* sD, const double* v, TZ* z1, T* t_out) {
+  constexpr int RY = G::RY, Q = QTILE;
+  const int n = a.g.n;
+  const long long sy = a.g.sy, nv = a.g.nv;
+  T x[RY], r[RY], d[RY];
 #pragma unroll
-  for (int k = 0; k < NL; ++k) {
-    const int t = threadIdx.x + k * TILE_THREADS;
-    Vtx<2> vv;
-    br[k] = 0.0;
-    if (t < S * S && tile_vertex<TILE, S, INT>(F, t % S, t / S, vv)) br[k] = v[gidx(F, vv)];
+  for (int i = 0; i < RY; ++i) {
+    const bool in = INT || row_in(p, i, n);
+    x[i] = (T)0;
+    r[i] = in ? (T)v[p.gx + sy * (p.gy0 + i)] : (T)0;    // b, held until the tables arrive
   }
+  __syncthreads();                                  // tables visible
+  RegW<2, T> rw{};
+  if constexpr (INT) rw = reg_weights<2, T>(sW, sD, 4);
 #pragma unroll
-  for (int k = 0; k < NL; ++k) {
-    const int t = threadIdx.x + k * TILE_THREADS;
-    if (t < S * S) {
-      X[t] = (T)0;
-      B[t] = (T)br[k];
-    }
+  for (int i = 0; i < RY; ++i) {                    // cheb_init (b scaled by 1)
+    int cy;
+    const int cls = row_class<INT>(p, i, n, cy);
+    const T dv = INT ? rw.dinv : sD[cls];
+    T rr = r[i] * (T)1;
+    r[i] = rr;
+    d[i] = dv * rr * a.inv_th;
   }
-  __syncthreads();
-  const Geom& lg = F.lg;
-  const RegW<2, T> rw = reg_weights<2, T>(sW, sD, 4);   // interior class, used when INT
-  tile_loop<TILE, S, 0, S, INT>(F, [&](const Vtx<2>& w) {
-    if constexpr (INT) cheb_init_r<2, T>(w, rw, B, R, D0, a.inv_th);
-    else cheb_init_at<2, T, T>(w, sD, B, (T)1, R, D0, a.inv_th);
-  });
-  T* Dd[2] = {D0, D1};
-  static_for<0, Q - 1>([&](auto Kc) {
+  Nb<G, T> nb;
+  static_for<0, Q - 1>([&](auto Kc) {               // cheb_step k (first at k = 0)
     constexpr int k = decltype(Kc)::value;
-    T* din = Dd[k & 1];
-    T* dout = Dd[(k + 1) & 1];
-    tile_loop<TILE, S, k + 1, S - k - 1, INT>(F, [&](const Vtx<2>& w) {
-      if constexpr (INT) cheb_step_r<2, T>(lg, w, rw, X, R, din, dout, a.c1[k], a.c2[k], k == 0);
-      else cheb_step_at<2, T>(lg, w, sW, sD, X, R, din, dout, a.c1[k], a.c2[k], k == 0);
-    });
+    T* buf = (k & 1) ? buf1 : buf0;
+    xput<G>(buf, p, d);
+    __syncthreads();
+    xget<G>(buf, p, nb);
+    T dn[RY];
+#pragma unroll
+    for (int i = 0; i < RY; ++i) {
+      int cy;
+      const int cls = row_class<INT>(p, i, n, cy);
+      const T dv = INT ? rw.dinv : sD[cls];
+      T xs[Topo<2>::NOFF];
+      nb_row<G, T, INT>(d, nb, i, p.cx, cy, xs);
+      x[i] = (k == 0 ? (T)0 : x[i]) + xs[0];
+      T rr = r[i] - sdot<T, INT>(rw, sW, cls, xs);
+      r[i] = rr;
+      dn[i] = fma(a.c1[k], xs[0], a.c2[k] * (dv * rr));
+    }
+#pragma unroll
+    for (int i = 0; i < RY; ++i) d[i] = dn[i];
   });
-  T* dl = Dd[(Q - 1) & 1];
-  tile_loop<TILE, S, Q - 1, S - Q + 1, INT>(F, [&](const Vtx<2>& w) {
-    if constexpr (INT) cheb_last_r<2, T>(lg, w, rw, X, (T*)nullptr, dl, Q == 1);
-    else cheb_last_at<2, T, T>(lg, w, sW, X, (T*)nullptr, dl, Q == 1, (T*)nullptr, (T)1);
-  });
-  const long long nv = a.g.nv;
-  tile_loop<TILE, S, Q, Q + TILE, INT>(F, [&](const Vtx<2>& w) {
-    const long long gi = gidx(F, w);
-    z1[gi] = (TZ)(X[w.idx] * a.inv_a11);
-    // C (inv_a11 X), as capply_at: self first, then +pos / -pos pairs
-    T acc = a.coef[gi] * X[w.idx] * a.inv_a11;
+#pragma unroll
+  for (int i = 0; i < RY; ++i) {                    // cheb_last without the residual
+    T xx = (Q == 1 ? (T)0 : x[i]) + d[i];
+    x[i] = xx;
+  }
+  // C-step at the owned vertices (capply_at on y = x, scaled by 1 / a11)
+  T* buf = ((Q - 1) & 1) ? buf1 : buf0;
+  xput<G>(buf, p, x);
+  __syncthreads();
+  xget<G>(buf, p, nb);
+#pragma unroll
+  for (int i = 0; i < RY; ++i) {
+    if (!owned<G>(p, i) || !(INT || row_in(p, i, n))) continue;
+    const long long gi = p.gx + sy * (p.gy0 + i);
+    int cy;
+    row_class<INT>(p, i, n, cy);
+    const int c[3] = {p.cx, cy, 1};
+    z1[gi] = (TZ)(x[i] * a.inv_a11);
+    T xs[Topo<2>::NOFF];
+    nb_row<G, T, INT>(x, nb, i, p.cx, cy, xs);
+    T acc = a.coef[gi] * xs[0] * a.inv_a11;
     static_for<0, Topo<2>::NPOS>([&](auto P) {
-      constexpr int p = decltype(P)::value;
-      constexpr int op = 2 * p + 1, om = 2 * p + 2;
-      if (nb_valid<2, op>(w.c))
-        acc = fma(a.coef[(1 + p) * nv + gi], X[w.idx + nb_delta<2, op>(lg)] * a.inv_a11, acc);
-      if (nb_valid<2, om>(w.c))
-        acc = fma(a.coef[(1 + p) * nv + gi + nb_delta<2, om>(a.g)], X[w.idx + nb_delta<2, om>(lg)] * a.inv_a11, acc);
+      constexpr int q = decltype(P)::value;
+      constexpr int op = 2 * q + 1, om = 2 * q + 2;
+      constexpr long long dxm = off_comp(2, om, 0), dym = off_comp(2, om, 1);
+      if (INT || nb_valid<2, op>(c)) acc = fma(a.coef[(1 + q) * nv + gi], xs[op] * a.inv_a11, acc);
+      if (INT || nb_valid<2, om>(c))
+        acc = fma(a.coef[(1 + q) * nv + gi + dxm + sy * dym], xs[om] * a.inv_a11, acc);
     });
     t_out[gi] = (T)v[gi + nv] * (T)1 - acc;
-  });
+  }
 }
 
-template <typename T, typename TZ>
-__global__ void __launch_bounds__(TILE_THREADS) k_tile_amass(TileMass<T> a, const double* __restrict__ v,
-                                                             TZ* __restrict__ z1, T* __restrict__ t_out) {
+template <typename T, typename TZ, class G>
+__global__ void __launch_bounds__(G::NT) k_strip_amass(TileMass<T> a, const double* __restrict__ v,
+                                                        TZ* __restrict__ z1, T* __restrict__ t_out) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int S = TILE + 2 * QTILE, SS = S * S;
-  const Frame<TILE, S> F = make_frame<TILE, S>(a.g);
-  T* X = reinterpret_cast<T*>(smraw);
-  T* B = X + SS;
-  T* R = B + SS;
-  T* D0 = R + SS;
-  T* D1 = D0 + SS;
-  T* sW = D1 + SS;
-  T* sD = sW + Topo<2>::NCLASS * Topo<2>::NOFF;
-  load_tables<T>(sW, sD, a.WM, a.dinvM);
-  if (tile_interior(F)) tile_amass_body<T, TZ, true>(a, F, X, B, R, D0, D1, sW, sD, v, z1, t_out);
-  else tile_amass_body<T, TZ, false>(a, F, X, B, R, D0, D1, sW, sD, v, z1, t_out);
+  T* buf0 = reinterpret_cast<T*>(smraw);
+  T* buf1 = buf0 + G::SB;
+  T* sW = buf1 + G::SB;
+  T* sD = sW + NTAB;
+  load_table<T>(sW, a.WM, NTAB, G::NT);
+  load_table<T>(sD, a.dinvM, Topo<2>::NCLASS, G::NT);
+  const Pos p = strip_pos<G>(a.g.n);
+  if (strip_interior<G>(a.g.n)) strip_amass_body<T, TZ, G, true>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
+  else strip_amass_body<T, TZ, G, false>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
 }
 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static inline dim3 tile_grid(const Geom& g, int tl) {
-  const int nb = (g.n1 + tl - 1) / tl;
-  return dim3(nb, nb, 1);
+template <class G>
+static inline dim3 strip_grid(const Geom& g) {
+  return dim3((g.n1 + G::OW - 1) / G::OW, (g.n1 + G::OH - 1) / G::OH, 1);
 }
-static inline size_t tile_smem(int tl, int H, size_t elem) {
-  const size_t S = tl + 2 * H;
-  return (5 * S * S + 2 * Topo<2>::NCLASS * Topo<2>::NOFF + Topo<2>::NCLASS) * elem;
+template <class G, typename T>
+static inline size_t strip_smem(bool with_m) {
+  return (2 * (size_t)G::SB + NTAB + Topo<2>::NCLASS + (with_m ? NTAB : 0)) * sizeof(T);
 }
 
 template <typename T>
 void launch_tile_pre(const TileSmooth<T>& a, const T* x_in, const T* b, T* x_out, T* bc, cudaStream_t s) {
-  if (a.tile == 16)
-    count_launch(), k_tile_pre<T, 16><<<tile_grid(a.g, 16), TILE_THREADS, tile_smem(16, 4, sizeof(T)), s>>>(
-                        a, x_in, b, x_out, bc);
+  using Big = typename StripCfg<T>::template Big<4>;
+  using Small = typename StripCfg<T>::template Small<4>;
+  if (a.tile == 64)
+    launch_k(k_strip_pre<T, Big>, strip_grid<Big>(a.g), Big::NT, strip_smem<Big, T>(false), s, a, x_in, b, x_out, bc);
   else
-    count_launch(), k_tile_pre<T, 32><<<tile_grid(a.g, 32), TILE_THREADS, tile_smem(32, 4, sizeof(T)), s>>>(
-                        a, x_in, b, x_out, bc);
+    launch_k(k_strip_pre<T, Small>, strip_grid<Small>(a.g), Small::NT, strip_smem<Small, T>(false), s, a, x_in, b,
+             x_out, bc);
 }
 template <typename T, typename TO>
 void launch_tile_post(const TileSmooth<T>& a, const T* x_in, const T* xc, const T* b, T* x_out, T* mx_out, TO* out,
                       T oscale, cudaStream_t s) {
-  if (a.tile == 16)
-    count_launch(), k_tile_post<T, TO, 16><<<tile_grid(a.g, 16), TILE_THREADS, tile_smem(16, 3, sizeof(T)), s>>>(
-                        a, x_in, xc, b, x_out, mx_out, out, oscale);
+  using Big = typename StripCfg<T>::template Big<3>;
+  using Small = typename StripCfg<T>::template Small<3>;
+  if (a.tile == 64)
+    launch_k(k_strip_post<T, TO, Big>, strip_grid<Big>(a.g), Big::NT, strip_smem<Big, T>(true), s, a, x_in, xc, b,
+             x_out, mx_out, out, oscale);
   else
-    count_launch(), k_tile_post<T, TO, 32><<<tile_grid(a.g, 32), TILE_THREADS, tile_smem(32, 3, sizeof(T)), s>>>(
-                        a, x_in, xc, b, x_out, mx_out, out, oscale);
+    launch_k(k_strip_post<T, TO, Small>, strip_grid<Small>(a.g), Small::NT, strip_smem<Small, T>(true), s, a, x_in,
+             xc, b, x_out, mx_out, out, oscale);
 }
 template <typename T, typename TZ>
 void launch_tile_amass(const TileMass<T>& a, const double* v, TZ* z1, T* t_out, cudaStream_t s) {
-  count_launch(), k_tile_amass<T, TZ><<<tile_grid(a.g, TILE), TILE_THREADS, tile_smem(TILE, QTILE, sizeof(T)), s>>>(
-                      a, v, z1, t_out);
+  using Mass = typename StripCfg<T>::Mass;
+  launch_k(k_strip_amass<T, TZ, Mass>, strip_grid<Mass>(a.g), Mass::NT, strip_smem<Mass, T>(false), s, a, v, z1,
+           t_out);
 }
 
 template <typename T>
 cudaError_t prepare_tiles(int q) {
   (void)q;
+  using Cfg = StripCfg<T>;
+  using BP = typename Cfg::template Big<4>;
+  using SP = typename Cfg::template Small<4>;
+  using BQ = typename Cfg::template Big<3>;
+  using SQ = typename Cfg::template Small<3>;
+  using MA = typename Cfg::Mass;
   const cudaFuncAttribute attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_tile_pre<T, 32>, attr, (int)tile_smem(32, 4, sizeof(T)));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile_pre<T, 16>, attr, (int)tile_smem(16, 4, sizeof(T)));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile_post<T, float, 32>, attr, (int)tile_smem(32, 3, sizeof(T)));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile_post<T, double, 32>, attr, (int)tile_smem(32, 3, sizeof(T)));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile_post<T, float, 16>, attr, (int)tile_smem(16, 3, sizeof(T)));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile_post<T, double, 16>, attr, (int)tile_smem(16, 3, sizeof(T)));
-  const int c = (int)tile_smem(TILE, QTILE, sizeof(T));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile_amass<T, float>, attr, c);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile_amass<T, double>, attr, c);
+  cudaError_t e = cudaFuncSetAttribute(k_strip_pre<T, BP>, attr, (int)strip_smem<BP, T>(false));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_pre<T, SP>, attr, (int)strip_smem<SP, T>(false));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, float, BQ>, attr, (int)strip_smem<BQ, T>(true));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, double, BQ>, attr, (int)strip_smem<BQ, T>(true));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, float, SQ>, attr, (int)strip_smem<SQ, T>(true));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, double, SQ>, attr, (int)strip_smem<SQ, T>(true));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, float, MA>, attr, (int)strip_smem<MA, T>(false));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, double, MA>, attr, (int)strip_smem<MA, T>(false));
   return e;
+}
+
+// blocks of the pre-smoothing kernel on a level with the large (64) or small (32) window
+template <typename T>
+long long strip_blocks(const Geom& g, int tile) {
+  const dim3 d = tile == 64 ? strip_grid<typename StripCfg<T>::template Big<4>>(g)
+                            : strip_grid<typename StripCfg<T>::template Small<4>>(g);
+  return (long long)d.x * d.y;
 }
 
 #define OK_TILE_INST(T)                                                                                       \
@@ -423,7 +587,8 @@ cudaError_t prepare_tiles(int q) {
   template void launch_tile_post<T, T>(const TileSmooth<T>&, const T*, const T*, const T*, T*, T*, T*, T,     \
                                        cudaStream_t);                                                         \
   template void launch_tile_amass<T, T>(const TileMass<T>&, const double*, T*, T*, cudaStream_t);             \
-  template cudaError_t prepare_tiles<T>(int);
+  template cudaError_t prepare_tiles<T>(int);                                                                 \
+  template long long strip_blocks<T>(const Geom&, int);
 OK_TILE_INST(float)
 OK_TILE_INST(double)
 template void launch_tile_post<float, double>(const TileSmooth<float>&, const float*, const float*, const float*,

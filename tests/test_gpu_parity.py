@@ -304,17 +304,38 @@ def test_fused_coarse_vcycle_is_bitwise_identical(dim, n, precision):
 @pytest.mark.parametrize("n", [100, 160, 256])
 @pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
 def test_tile_kernels_are_bitwise_identical(n, precision):
-    """2D shared-memory tile kernels (temporal blocking with redundant halos)
-    against the one-kernel-per-step path: same arithmetic, same bits.  n = 100
-    gives ragged tiles (101 vertices per row, 32-wide tiles)."""
+    """2D register-strip tile kernels (temporal blocking with redundant halos)
+    against the one-kernel-per-step path: same arithmetic, same bits, for the
+    automatic, the 32-column and the 64-column windows.  n = 100 gives ragged
+    windows at the domain edge on every level."""
     sysm, p, rng = make(2, n, seed=6, dt=1e-4)
     nv = sysm.mesh.nv
     u = dev(rng.uniform(-1.0, 1.0, nv))
     v = dev(rng.standard_normal(2 * nv))
     out = []
-    for tile in (0, 1):
+    for tile in (0, 1, 2, 3):
         with ok.Grid(2, n, **p, precision=precision, tile_fine=tile) as g:
             z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
             g.apply_preconditioner(u, v, z)
             out.append(host(z))
-    assert np.array_equal(out[0], out[1])
+    for k in range(1, len(out)):
+        assert np.array_equal(out[0], out[k]), k
+
+
+@pytest.mark.parametrize("dim,n", [(2, 128), (3, 16)])
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_programmatic_dependent_launch_is_bitwise_identical(dim, n, graphs):
+    """Kernels launched with programmatic stream serialization wait for their
+    predecessor (griddepcontrol.wait) before touching memory, so a timestep is
+    bitwise the same with the attribute on or off, in graphs or not."""
+    sysm, p, rng = make(dim, n, seed=8, dt=1e-4)
+    nv = sysm.mesh.nv
+    u0 = 0.1 * rng.uniform(-1.0, 1.0, nv)
+    out = []
+    for pdl in (0, 1):
+        with ok.Grid(dim, n, **p, precision=ok.OK_MIXED, use_graphs=graphs, use_pdl=pdl) as g:
+            u, w = dev(u0), torch.zeros(nv, dtype=torch.float64, device="cuda")
+            g.init_w(u, w)
+            g.timestep(u, w)
+            out.append((host(u), host(w)))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
