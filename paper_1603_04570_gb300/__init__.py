@@ -31,7 +31,7 @@ class Opts(Structure):
     _fields_ = [("restart", c_int), ("max_gmres", c_int), ("max_newton", c_int), ("newton_extra", c_int),
                 ("q_A", c_int), ("n_V", c_int), ("k_R", c_int), ("smooth_pre", c_int), ("smooth_post", c_int),
                 ("precision", c_int), ("coarse_max", c_int), ("use_graphs", c_int), ("fuse_coarse", c_int),
-                ("tile_fine", c_int), ("use_pdl", c_int),
+                ("tile_fine", c_int), ("use_pdl", c_int), ("reorth", c_int),
                 ("gmres_rtol", c_double), ("newton_atol", c_double), ("newton_rtol", c_double),
                 ("smooth_lo_frac", c_double)]
 

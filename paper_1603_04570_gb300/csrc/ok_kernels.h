@@ -156,14 +156,19 @@ struct RedScratch {
 };
 int krylov_blocks();
 // ks->h1[0..K) = V^T w       (V: K vectors with leading dimension ldv)
+// (skip: device flag, the launches return at once when it is set; nw0: also ||w||^2 there)
 void launch_multidot(const double* V, long long ldv, int K, const double* w, long long N, RedScratch rs,
-                     double* out, cudaStream_t s);
+                     double* out, cudaStream_t s, const int* skip = nullptr, double* nw0 = nullptr);
 // w -= V h_in; h_out = V^T w
 void launch_update_multidot(const double* V, long long ldv, int K, const double* h_in, double* w, long long N,
                             RedScratch rs, double* h_out, cudaStream_t s);
-// w -= V h2; then Arnoldi column j finalisation + Givens in the last block
+// w -= V h2; then Arnoldi column j finalisation (h1 + h2) + Givens in the last block
 void launch_update_norm_givens(const double* V, long long ldv, int K, double* w, long long N, RedScratch rs,
-                               KrylovState* ks, int j, cudaStream_t s);
+                               KrylovState* ks, int j, cudaStream_t s, const int* skip = nullptr);
+// w -= V h1; ||w||^2 against ks->nw0 decides the second pass (sets ks->skip2);
+// without it the column (h1) and its Givens rotation are finished here
+void launch_update_norm_check(const double* V, long long ldv, int K, double* w, long long N, RedScratch rs,
+                              KrylovState* ks, int j, cudaStream_t s);
 // w *= ks->inv_eta
 void launch_scale_by(double* w, long long N, const double* factor, cudaStream_t s);
 // out = ||x||_2 (device scalar)
@@ -189,5 +194,8 @@ double* ks_eta_ptr(KrylovState* ks);
 double* ks_beta_ptr(KrylovState* ks);
 double* ks_h1_ptr(KrylovState* ks);
 double* ks_h2_ptr(KrylovState* ks);
+double* ks_nw0_ptr(KrylovState* ks);
+int* ks_skip2_ptr(KrylovState* ks);
+int* ks_passes2_ptr(KrylovState* ks);
 
 }  // namespace okg

@@ -2,11 +2,16 @@
 //
 // Arnoldi step j (Saad, "A flexible inner-outer preconditioned GMRES
 // algorithm", SISC 14, 1993) with w = J z_j orthogonalised against
-// v_0..v_j by classical Gram--Schmidt applied twice (CGS2):
-//     h1 = V^T w;  w -= V h1;  h2 = V^T w;  w -= V h2;  H(:,j) = h1 + h2;
+// v_0..v_j by classical Gram--Schmidt with re-orthogonalisation:
+//     h1 = V^T w;  w -= V h1;  [h2 = V^T w;  w -= V h2;]  H(:,j) = h1 (+ h2);
 //     eta = ||w||;  H(j+1,j) = eta;  v_{j+1} = w / eta;
-// then the new column is reduced by Givens rotations and |g_{j+1}| is the
-// residual norm of the least-squares problem min || beta e_1 - H y ||.
+// the bracketed second pass runs always (CGS2) or, by the criterion of
+// Daniel, Gragg, Kaufman and Stewart (Math. Comp. 30, 1976), only when the
+// first pass cancelled more than half of ||w||^2 (||w_1||^2 < ||w_0||^2 / 2);
+// the decision is taken on the device and the second-pass kernels return at
+// once when it is not needed.  The new column is then reduced by Givens
+// rotations and |g_{j+1}| is the residual norm of the least-squares problem
+// min || beta e_1 - H y ||.
 //
 // Reductions are deterministic: a fixed grid, a fixed element-to-thread map,
 // per-block partials and an in-order sum by the last block to finish (found
@@ -26,6 +31,9 @@ struct KrylovState {
   double beta, inv_beta;
   double eta, inv_eta;
   double resid;
+  double nw0;         // ||w||^2 before the first Gram--Schmidt pass
+  int skip2;          // 1: the second pass is not needed this step
+  int passes2;        // second passes taken since the handle was created
 };
 
 size_t krylov_state_bytes() { return sizeof(KrylovState); }
@@ -34,6 +42,9 @@ double* ks_eta_ptr(KrylovState* ks) { return &ks->eta; }
 double* ks_beta_ptr(KrylovState* ks) { return &ks->beta; }
 double* ks_h1_ptr(KrylovState* ks) { return ks->h1; }
 double* ks_h2_ptr(KrylovState* ks) { return ks->h2; }
+int* ks_skip2_ptr(KrylovState* ks) { return &ks->skip2; }
+double* ks_nw0_ptr(KrylovState* ks) { return &ks->nw0; }
+int* ks_passes2_ptr(KrylovState* ks) { return &ks->passes2; }
 
 static constexpr int RT = 256;    // threads per reduction block
 static constexpr int KC = 16;     // vectors per multi-dot launch (register budget)
@@ -110,22 +121,36 @@ __device__ __forceinline__ void final_sums(const double* __restrict__ partials, 
 // The multi-dot and update kernels take the number of basis vectors K
 // (<= KC) as a template argument, so that every V load of an element is
 // unconditional and can be in flight at once.
-template <int K>
+// out[k] = v_k . w (k < K); with NORM also *nrm = w . w.  A kernel given a
+// skip flag returns at once when the flag is set.
+template <int K, bool NORM>
 __global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ V, long long ldv,
                                                  const double* __restrict__ w, long long N,
                                                  double* __restrict__ partials, unsigned int* counter,
-                                                 double* __restrict__ out) {
+                                                 double* __restrict__ out, const int* __restrict__ skip,
+                                                 double* __restrict__ nrm) {
   pdl_entry();
-  double acc[K];
+  if (skip && *skip) return;
+  constexpr int NA = K + (NORM ? 1 : 0);
+  double acc[NA];
 #pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
     const double we = w[e];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = fma(V[k * ldv + e], we, acc[k]);
+    if constexpr (NORM) acc[K] = fma(we, we, acc[K]);
   }
-  block_partials<K>(acc, K, partials);
-  if (last_block(counter)) final_sums(partials, K, out);
+  block_partials<NA>(acc, NA, partials);
+  if (!last_block(counter)) return;
+  const int warp = threadIdx.x >> 5;
+  for (int k = warp; k < NA; k += RT / 32) {
+    const double a = warp_sum_partials(partials, k);
+    if ((threadIdx.x & 31) == 0) {
+      if (k < K) out[k] = a;
+      else *nrm = a;
+    }
+  }
 }
 
 template <int K>
@@ -155,14 +180,44 @@ __global__ void __launch_bounds__(RT) k_update_multidot(const double* __restrict
   if (last_block(counter)) final_sums(partials, K, out);
 }
 
-// w -= V h2 (h2 = ks->h2[K0..K0+K)), ||w||^2; last block: column j of H,
-// Givens rotations, residual estimate.
+// Column j of H from h1 (+ h2 when `two`), eta = sqrt(s); Givens rotations
+// and the residual estimate.  One thread.
+__device__ void arnoldi_column(KrylovState* ks, int j, double s, bool two) {
+  const int ld = KRYLOV_MAX + 1;
+  double* Hj = ks->H + (long long)ld * j;
+  for (int i = 0; i <= j; ++i) Hj[i] = two ? ks->h1[i] + ks->h2[i] : ks->h1[i];
+  const double eta = sqrt(s);
+  Hj[j + 1] = eta;
+  ks->eta = eta;
+  ks->inv_eta = eta > 0.0 ? 1.0 / eta : 0.0;
+  for (int i = 0; i < j; ++i) {                       // previous rotations
+    const double a = Hj[i], b = Hj[i + 1];
+    Hj[i] = ks->cs[i] * a + ks->sn[i] * b;
+    Hj[i + 1] = -ks->sn[i] * a + ks->cs[i] * b;
+  }
+  const double a = Hj[j], b = Hj[j + 1];
+  const double r = hypot(a, b);
+  const double c = r > 0.0 ? a / r : 1.0, sn = r > 0.0 ? b / r : 0.0;
+  ks->cs[j] = c;
+  ks->sn[j] = sn;
+  Hj[j] = r;
+  Hj[j + 1] = 0.0;
+  ks->g[j + 1] = -sn * ks->g[j];
+  ks->g[j] = c * ks->g[j];
+  ks->resid = fabs(ks->g[j + 1]);
+}
+
+// w -= V h2 (h2 = ks->h2[K0..K0+K)), ||w||^2; last block: column j of H
+// (h1 + h2), Givens rotations, residual estimate.  Returns at once when
+// `skip` is set.
 template <int K>
 __global__ void __launch_bounds__(RT) k_update_norm_givens(const double* __restrict__ V, long long ldv,
                                                            double* __restrict__ w, long long N,
                                                            double* __restrict__ partials, unsigned int* counter,
-                                                           KrylovState* ks, int j, int K0) {
+                                                           KrylovState* ks, int j, int K0,
+                                                           const int* __restrict__ skip) {
   pdl_entry();
+  if (skip && *skip) return;
   __shared__ double hs[K];
   if (threadIdx.x < K) hs[threadIdx.x] = ks->h2[K0 + threadIdx.x];
   __syncthreads();
@@ -181,36 +236,50 @@ __global__ void __launch_bounds__(RT) k_update_norm_givens(const double* __restr
   if (!last_block(counter) || threadIdx.x >= 32) return;
   const double s = warp_sum_partials(partials, 0);
   if (threadIdx.x == 0) {
-    const int ld = KRYLOV_MAX + 1;
-    double* Hj = ks->H + (long long)ld * j;
-    for (int i = 0; i <= j; ++i) Hj[i] = ks->h1[i] + ks->h2[i];
-    const double eta = sqrt(s);
-    Hj[j + 1] = eta;
-    ks->eta = eta;
-    ks->inv_eta = eta > 0.0 ? 1.0 / eta : 0.0;
-    for (int i = 0; i < j; ++i) {                       // previous rotations
-      const double a = Hj[i], b = Hj[i + 1];
-      Hj[i] = ks->cs[i] * a + ks->sn[i] * b;
-      Hj[i + 1] = -ks->sn[i] * a + ks->cs[i] * b;
-    }
-    const double a = Hj[j], b = Hj[j + 1];
-    const double r = hypot(a, b);
-    const double c = r > 0.0 ? a / r : 1.0, sn = r > 0.0 ? b / r : 0.0;
-    ks->cs[j] = c;
-    ks->sn[j] = sn;
-    Hj[j] = r;
-    Hj[j + 1] = 0.0;
-    ks->g[j + 1] = -sn * ks->g[j];
-    ks->g[j] = c * ks->g[j];
-    ks->resid = fabs(ks->g[j + 1]);
+    if (skip) ks->passes2 += 1;
+    arnoldi_column(ks, j, s, true);
+  }
+}
+
+// First-pass update w -= V h1 (h1 = ks->h1[K0..K0+K)), ||w||^2; last block:
+// the re-orthogonalisation test against ks->nw0.  Without a second pass the
+// column is finished here (H(:,j) = h1).
+template <int K>
+__global__ void __launch_bounds__(RT) k_update_norm_check(const double* __restrict__ V, long long ldv,
+                                                          double* __restrict__ w, long long N,
+                                                          double* __restrict__ partials, unsigned int* counter,
+                                                          KrylovState* ks, int j, int K0) {
+  pdl_entry();
+  __shared__ double hs[K];
+  if (threadIdx.x < K) hs[threadIdx.x] = ks->h1[K0 + threadIdx.x];
+  __syncthreads();
+  double acc[1] = {0.0};
+  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
+    double vals[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) vals[k] = V[k * ldv + e];
+    double we = w[e];
+#pragma unroll
+    for (int k = 0; k < K; ++k) we = fma(-hs[k], vals[k], we);
+    w[e] = we;
+    acc[0] = fma(we, we, acc[0]);
+  }
+  block_partials<1>(acc, 1, partials);
+  if (!last_block(counter) || threadIdx.x >= 32) return;
+  const double s = warp_sum_partials(partials, 0);
+  if (threadIdx.x == 0) {
+    const bool second = !(s >= 0.5 * ks->nw0);      // also taken when s or nw0 is NaN
+    ks->skip2 = second ? 0 : 1;
+    if (!second) arnoldi_column(ks, j, s, false);
   }
 }
 
 template <int K>
 __global__ void __launch_bounds__(RT) k_update_only(const double* __restrict__ V, long long ldv,
                                                     const double* __restrict__ h, double* __restrict__ w,
-                                                    long long N) {
+                                                    long long N, const int* __restrict__ skip) {
   pdl_entry();
+  if (skip && *skip) return;
   __shared__ double hs[K];
   if (threadIdx.x < K) hs[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
@@ -321,13 +390,19 @@ __global__ void __launch_bounds__(RT) k_check_finite(const double* __restrict__ 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// out[0..K) = V^T w (chunks of KC vectors); with nw0, also ||w||^2 there (first chunk)
 void launch_multidot(const double* V, long long ldv, int K, const double* w, long long N, RedScratch rs,
-                     double* out, cudaStream_t s) {
+                     double* out, cudaStream_t s, const int* skip, double* nw0) {
   for (int k0 = 0; k0 < K; k0 += KC) {
     const int kk = K - k0 < KC ? K - k0 : KC;
     with_k(kk, [&](auto KK) {
-      launch_k(k_multidot<decltype(KK)::value>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, w, N,
-                                                                                    rs.partials, rs.counter, out + k0);
+      constexpr int KV = decltype(KK)::value;
+      if (k0 == 0 && nw0)
+        launch_k(k_multidot<KV, true>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, w, N, rs.partials,
+                 rs.counter, out + k0, skip, nw0);
+      else
+        launch_k(k_multidot<KV, false>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, w, N, rs.partials,
+                 rs.counter, out + k0, skip, (double*)nullptr);
     });
   }
 }
@@ -345,22 +420,34 @@ void launch_update_multidot(const double* V, long long ldv, int K, const double*
     const int kk = K - k0 < KC ? K - k0 : KC;
     with_k(kk, [&](auto KK) {
       launch_k(k_update_only<decltype(KK)::value>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, h_in + k0,
-                                                                                       w, N);
+                                                                                       w, N, (const int*)nullptr);
     });
   }
-  launch_multidot(V, ldv, K, w, N, rs, h_out, s);
+  launch_multidot(V, ldv, K, w, N, rs, h_out, s, nullptr, nullptr);
 }
 
 void launch_update_norm_givens(const double* V, long long ldv, int K, double* w, long long N, RedScratch rs,
-                               KrylovState* ks, int j, cudaStream_t s) {
+                               KrylovState* ks, int j, cudaStream_t s, const int* skip) {
   int k0 = 0;
   for (; K - k0 > KC; k0 += KC) {
     // h2 lives in device memory inside ks; chunk offsets index it directly
-    launch_k(k_update_only<KC>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, ks->h2 + k0, w, N);
+    launch_k(k_update_only<KC>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, ks->h2 + k0, w, N, skip);
   }
   with_k(K - k0, [&](auto KK) {
     launch_k(k_update_norm_givens<decltype(KK)::value>, krylov_blocks(), RT, 0, s, 
-                        V + k0 * ldv, ldv, w, N, rs.partials, rs.counter, ks, j, k0);
+                        V + k0 * ldv, ldv, w, N, rs.partials, rs.counter, ks, j, k0, skip);
+  });
+}
+
+void launch_update_norm_check(const double* V, long long ldv, int K, double* w, long long N, RedScratch rs,
+                              KrylovState* ks, int j, cudaStream_t s) {
+  int k0 = 0;
+  for (; K - k0 > KC; k0 += KC)
+    launch_k(k_update_only<KC>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, ks->h1 + k0, w, N,
+             (const int*)nullptr);
+  with_k(K - k0, [&](auto KK) {
+    launch_k(k_update_norm_check<decltype(KK)::value>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, w, N,
+             rs.partials, rs.counter, ks, j, k0);
   });
 }
 

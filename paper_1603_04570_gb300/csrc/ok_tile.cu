@@ -52,7 +52,7 @@ template <int CW_, int RY_, int NCH_, int H_> struct SG {
 };
 
 // window sizes (CW, RY, NCH) per precision: large levels, small levels, the
-// mass kernel; the float ones may be set at compile time
+// mass kernel; each may be set at compile time
 // (measured on the 1025^2 hierarchy: short strips and many threads win, the
 // kernels being latency- rather than throughput-bound)
 #ifndef OK_STRIP_F_BIG
@@ -70,10 +70,19 @@ template <> struct StripCfg<float> {
   template <int H> using Small = SG<OK_STRIP_F_SMALL, H>;
   using Mass = SG<OK_STRIP_F_MASS, QTILE>;
 };
+#ifndef OK_STRIP_D_BIG
+#define OK_STRIP_D_BIG 64, 2, 16
+#endif
+#ifndef OK_STRIP_D_SMALL
+#define OK_STRIP_D_SMALL 32, 2, 8
+#endif
+#ifndef OK_STRIP_D_MASS
+#define OK_STRIP_D_MASS 64, 4, 16
+#endif
 template <> struct StripCfg<double> {
-  template <int H> using Big = SG<64, 4, 10, H>;
-  template <int H> using Small = SG<32, 4, 8, H>;
-  using Mass = SG<64, 4, 12, QTILE>;
+  template <int H> using Big = SG<OK_STRIP_D_BIG, H>;
+  template <int H> using Small = SG<OK_STRIP_D_SMALL, H>;
+  using Mass = SG<OK_STRIP_D_MASS, QTILE>;
 };
 
 // this thread's strip
