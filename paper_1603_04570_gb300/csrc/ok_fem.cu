@@ -15,7 +15,17 @@
 //                                      (p1^2 + p2 + 2 p1 (u_a + u_b) + 2 (u_a^2 + u_a u_b + u_b^2))
 // with p_k = sum_c u_c^k over the simplex's vertices.  (Each follows from
 // expanding prod k! as the number of label-preserving permutations of the
-// integrand's factors.)
+// integrand's factors.)  With s_k = sum of u_c^k over the vertices other than
+// a (so p_k = u_a^k + s_k) the first two become
+//   p1^3 + 3 p1 p2 + 2 p3 + ... = 24 a^3 + 18 a^2 s1 + 6 a (s1^2 + s2) + (s1^3 + 3 s1 s2 + 2 s3),
+//   (a = b):  p1^2 + p2 + 4 p1 a + 6 a^2 = 12 a^2 + 6 a s1 + s1^2 + s2,
+//   (a != b): p1^2 + p2 + 2 p1 (a + b) + 2 (a^2 + a b + b^2)
+//             = 6 m^2 - 4 a b + 4 m r1 + r1^2 + r2,   m = a + b,
+// r_k the power sums over the vertices other than a and b.  These are linear
+// in the per-simplex sums (s1, s1^2 + s2, s1^3 + 3 s1 s2 + 2 s3, r1, r1^2 + r2),
+// so a vertex sums those over its incident simplices and evaluates the
+// polynomial in a once: about half the float64 operations of evaluating each
+// simplex's integral separately (float64 is the bound of these kernels).
 #include "ok_internal.cuh"
 #include "ok_kernels.h"
 
@@ -58,6 +68,68 @@ void reference_tables(int dim, double* WM, double* WK) {
 }
 
 // ---------------------------------------------------------------------------
+// per-vertex simplex sums shared by N(u) and M_E(u)
+// ---------------------------------------------------------------------------
+template <int D> struct SimplexSums {
+  double n;        // incident simplices inside the domain
+  double A;        // sum s1
+  double B;        // sum (s1^2 + s2)
+  double C;        // sum (s1^3 + 3 s1 s2 + 2 s3)
+};
+
+// sq[o], cu[o]: squares and cubes of the neighbour values (o >= 1)
+template <int D, bool CUBES>
+__device__ __forceinline__ SimplexSums<D> simplex_sums(const Vtx<D>& v, const double (&us)[Topo<D>::NOFF],
+                                                       const double (&sq)[Topo<D>::NOFF],
+                                                       const double (&cu)[Topo<D>::NOFF]) {
+  using Tp = Topo<D>;
+  SimplexSums<D> z{0.0, 0.0, 0.0, 0.0};
+  int n = 0;
+  static_for<0, Tp::NINC>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (inc_valid<D, i>(v.c)) {
+      constexpr int k = inc_pos(D, i);
+      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      static_for<0, D + 1>([&](auto Tt) {
+        constexpr int t = decltype(Tt)::value;
+        if constexpr (t != k) {
+          constexpr int o = inc_off(D, i, t);
+          s1 += us[o];
+          s2 += sq[o];
+          if constexpr (CUBES) s3 += cu[o];
+        }
+      });
+      ++n;
+      z.A += s1;
+      z.B += fma(s1, s1, s2);
+      if constexpr (CUBES) z.C += fma(s1, fma(s1, s1, 3.0 * s2), 2.0 * s3);
+    }
+  });
+  z.n = (double)n;
+  return z;
+}
+
+// N(u)_v / (|T| d!): sum over the incident simplices of
+//   a4 int u^3 lambda_v - a2 int u lambda_v  (a4, a2 the moment factors)
+template <int D>
+__device__ __forceinline__ double nonlinear_at(const Vtx<D>& v, const double (&us)[Topo<D>::NOFF], double a4,
+                                               double a2) {
+  using Tp = Topo<D>;
+  double sq[Tp::NOFF], cu[Tp::NOFF];
+#pragma unroll
+  for (int o = 1; o < Tp::NOFF; ++o) {
+    sq[o] = us[o] * us[o];
+    cu[o] = sq[o] * us[o];
+  }
+  sq[0] = cu[0] = 0.0;
+  const SimplexSums<D> z = simplex_sums<D, true>(v, us, sq, cu);
+  const double a = us[0];
+  const double t3 = fma(fma(fma(24.0 * z.n, a, 18.0 * z.A), a, 6.0 * z.B), a, z.C);
+  const double lin = fma(2.0 * z.n, a, z.A);      // sum of (p1 + u_a)
+  return a4 * t3 - a2 * lin;
+}
+
+// ---------------------------------------------------------------------------
 // residual  f = -F(u, w)
 // ---------------------------------------------------------------------------
 // F1 = M g1 + K g2 with g1 = a11 u - bn u_n - dt sigma m,
@@ -88,28 +160,8 @@ __global__ void __launch_bounds__(128) k_residual(Geom g, const double* __restri
   const double hd = rc.hd, hk = rc.hk;
   double F1 = hd * dot_w<D, Tp::NOFF>(WM, v.cls, g1) + hk * dot_w<D, Tp::NAX>(WK, v.cls, g2);
   double F2 = hd * dot_w<D, Tp::NOFF>(WM, v.cls, ws) - rc.eps2 * hk * dot_w<D, Tp::NAX>(WK, v.cls, us);
-  // N(u)_v: gather over the incident simplices
-  double nacc = 0.0;
-  static_for<0, Tp::NINC>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    if (inc_valid<D, i>(v.c)) {
-      constexpr int k = inc_pos(D, i);
-      double p1 = 0.0, p2 = 0.0, p3 = 0.0;
-      static_for<0, D + 1>([&](auto Tt) {
-        constexpr int o = inc_off(D, i, decltype(Tt)::value);
-        double x = us[o];
-        p1 += x;
-        p2 = fma(x, x, p2);
-        p3 = fma(x * x, x, p3);
-      });
-      double ua = us[0];
-      (void)k;
-      double t3 = p1 * p1 * p1 + 3.0 * p1 * p2 + 2.0 * p3 + 3.0 * ua * (p1 * p1 + p2) +
-                  6.0 * ua * ua * p1 + 6.0 * ua * ua * ua;
-      nacc += rc.a4 * t3 - rc.a2 * (p1 + ua);
-    }
-  });
-  F2 -= rc.vol * nacc;
+  // N(u)_v: sums over the incident simplices
+  F2 -= rc.vol * nonlinear_at<D>(v, us, rc.a4, rc.a2);
   f[v.idx] = -F1;
   f[v.idx + g.nv] = -F2;
 }
@@ -125,25 +177,7 @@ __global__ void __launch_bounds__(128) k_initw_rhs(Geom g, const double* __restr
   double us[Tp::NOFF];
   load_nb<D>(u, g, v, us);
   double acc = rc.eps2 * rc.hk * dot_w<D, Tp::NAX>(WK, v.cls, us);
-  double nacc = 0.0;
-  static_for<0, Tp::NINC>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    if (inc_valid<D, i>(v.c)) {
-      double p1 = 0.0, p2 = 0.0, p3 = 0.0;
-      static_for<0, D + 1>([&](auto Tt) {
-        constexpr int o = inc_off(D, i, decltype(Tt)::value);
-        double x = us[o];
-        p1 += x;
-        p2 = fma(x, x, p2);
-        p3 = fma(x * x, x, p3);
-      });
-      double ua = us[0];
-      double t3 = p1 * p1 * p1 + 3.0 * p1 * p2 + 2.0 * p3 + 3.0 * ua * (p1 * p1 + p2) +
-                  6.0 * ua * ua * p1 + 6.0 * ua * ua * ua;
-      nacc += rc.a4 * t3 - rc.a2 * (p1 + ua);
-    }
-  });
-  out[v.idx] = acc + rc.vol * nacc;
+  out[v.idx] = acc + rc.vol * nonlinear_at<D>(v, us, rc.a4, rc.a2);
 }
 
 // ---------------------------------------------------------------------------
@@ -160,41 +194,67 @@ __global__ void __launch_bounds__(128) k_assemble_c(Geom g, ResidualCoefs rc, co
   if (!vertex_of_thread<D>(g, v)) return;
   double us[Tp::NOFF];
   load_nb<D>(u, g, v, us);
-  double acc[Tp::NSLOT];
+  double sq[Tp::NOFF];
 #pragma unroll
-  for (int s = 0; s < Tp::NSLOT; ++s) acc[s] = 0.0;
+  for (int o = 0; o < Tp::NOFF; ++o) sq[o] = us[o] * us[o];
   const double kscale = rc.eps2 * rc.hk * (1.0 / Tp::FACT);   // eps^2 h^(d-2) / d!
+  const double a = us[0];
+  // per positive offset p: simplices holding the edge, sum r1, sum (r1^2 + r2),
+  // and the summed path-Laplacian entries of K
+  double R1[Tp::NPOS], R2[Tp::NPOS];
+  int ne[Tp::NPOS], kl[Tp::NPOS + 1];
+#pragma unroll
+  for (int q = 0; q < Tp::NPOS; ++q) R1[q] = R2[q] = 0.0, ne[q] = 0;
+#pragma unroll
+  for (int q = 0; q <= Tp::NPOS; ++q) kl[q] = 0;
+  int n = 0;
+  double A = 0.0, B = 0.0;
   static_for<0, Tp::NINC>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if (inc_valid<D, i>(v.c)) {
       constexpr int k = inc_pos(D, i);
-      double p1 = 0.0, p2 = 0.0;
+      double s1 = 0.0, s2 = 0.0;
       static_for<0, D + 1>([&](auto Tt) {
-        constexpr int o = inc_off(D, i, decltype(Tt)::value);
-        p1 += us[o];
-        p2 = fma(us[o], us[o], p2);
+        constexpr int t = decltype(Tt)::value;
+        if constexpr (t != k) {
+          constexpr int o = inc_off(D, i, t);
+          s1 += us[o];
+          s2 += sq[o];
+        }
       });
-      const double ua = us[0];
-      const double base = p1 * p1 + p2 + 2.0 * p1 * ua + 2.0 * ua * ua;
+      ++n;
+      A += s1;
+      B += fma(s1, s1, s2);
+      kl[0] += path_lap(D, k, k);
       static_for<0, D + 1>([&](auto Tt) {
         constexpr int t = decltype(Tt)::value;
         constexpr int o = inc_off(D, i, t);
-        if constexpr (o == 0 || (o & 1)) {
-          constexpr int slot = (o + 1) / 2;
-          const double ub = us[o];
-          const double P = base + 2.0 * p1 * ub + 2.0 * (ua * ub + ub * ub);
-          const double dlt = (t == k) ? 2.0 : 1.0;
-          // M_E entry: 3 int u^2 l_a l_b - int l_a l_b
-          const double me = rc.vol * dlt * (3.0 * rc.a4 * P - rc.a2);
-          acc[slot] += -kscale * path_lap(D, k, t) - me;
+        if constexpr (t != k && (o & 1)) {          // a positive offset: C(v, v + pos) is stored here
+          constexpr int q = (o - 1) / 2;
+          const double r1 = s1 - us[o];
+          const double r2 = s2 - sq[o];
+          R1[q] += r1;
+          R2[q] += fma(r1, r1, r2);
+          ne[q] += 1;
+          kl[q + 1] += path_lap(D, k, t);
         }
       });
     }
   });
+  // M_E entries: 3 int u^2 l_a l_b - int l_a l_b  (times vol, 2x on the diagonal)
+  const double nd = (double)n;
+  const double Paa = fma(fma(12.0 * nd, a, 6.0 * A), a, B);
+  const double diag = -kscale * kl[0] - rc.vol * 2.0 * (3.0 * rc.a4 * Paa - rc.a2 * nd);
+  coef[v.idx] = diag;
+  coef32[v.idx] = (float)diag;
 #pragma unroll
-  for (int s = 0; s < Tp::NSLOT; ++s) {
-    coef[s * g.nv + v.idx] = acc[s];
-    coef32[s * g.nv + v.idx] = (float)acc[s];
+  for (int q = 0; q < Tp::NPOS; ++q) {
+    const double b = us[2 * q + 1];
+    const double m = a + b, nq = (double)ne[q];
+    const double P = fma(nq, fma(6.0 * m, m, -4.0 * a * b), fma(4.0 * m, R1[q], R2[q]));
+    const double c = -kscale * kl[q + 1] - rc.vol * (3.0 * rc.a4 * P - rc.a2 * nq);
+    coef[(1 + q) * g.nv + v.idx] = c;
+    coef32[(1 + q) * g.nv + v.idx] = (float)c;
   }
 }
 
