@@ -67,6 +67,19 @@ void reference_tables(int dim, double* WM, double* WK) {
   else reference_tables_d<3>(WM, WK);
 }
 
+// Copy the M and K class tables into shared memory (one load per block
+// instead of one per vertex and weight); call before any early return.
+template <int D>
+__device__ __forceinline__ void stage_tables(double* sWM, double* sWK, const double* __restrict__ WM,
+                                             const double* __restrict__ WK) {
+  constexpr int NT = Topo<D>::NCLASS * Topo<D>::NOFF;
+  for (int i = threadIdx.x; i < NT; i += blockDim.x) {
+    sWM[i] = WM[i];
+    sWK[i] = WK[i];
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // per-vertex simplex sums shared by N(u) and M_E(u)
 // ---------------------------------------------------------------------------
@@ -144,6 +157,8 @@ __global__ void __launch_bounds__(128) k_residual(Geom g, const double* __restri
                                                   double* __restrict__ f) {
   pdl_entry();
   using Tp = Topo<D>;
+  __shared__ double sWM[Tp::NCLASS * Tp::NOFF], sWK[Tp::NCLASS * Tp::NOFF];
+  stage_tables<D>(sWM, sWK, WM, WK);
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   double us[Tp::NOFF], g1[Tp::NOFF], g2[Tp::NAX], ws[Tp::NOFF];
@@ -158,8 +173,8 @@ __global__ void __launch_bounds__(128) k_residual(Geom g, const double* __restri
     if constexpr (o < Tp::NAX) g2[o] = ok ? (rc.dth * ww + rc.dth1 * wn[j]) : 0.0;
   });
   const double hd = rc.hd, hk = rc.hk;
-  double F1 = hd * dot_w<D, Tp::NOFF>(WM, v.cls, g1) + hk * dot_w<D, Tp::NAX>(WK, v.cls, g2);
-  double F2 = hd * dot_w<D, Tp::NOFF>(WM, v.cls, ws) - rc.eps2 * hk * dot_w<D, Tp::NAX>(WK, v.cls, us);
+  double F1 = hd * dot_w<D, Tp::NOFF>(sWM, v.cls, g1) + hk * dot_w<D, Tp::NAX>(sWK, v.cls, g2);
+  double F2 = hd * dot_w<D, Tp::NOFF>(sWM, v.cls, ws) - rc.eps2 * hk * dot_w<D, Tp::NAX>(sWK, v.cls, us);
   // N(u)_v: sums over the incident simplices
   F2 -= rc.vol * nonlinear_at<D>(v, us, rc.a4, rc.a2);
   f[v.idx] = -F1;
@@ -295,19 +310,6 @@ __device__ __forceinline__ T capply_from(const Geom& g, const Vtx<D>& v, const T
   return acc;
 }
 
-// float -> double without the float64 pipe (which runs at 1/58 of the float32
-// rate on this GPU): for normal numbers the IEEE-754 binary32 fields map to
-// binary64 by re-biasing the exponent (+1023-127) and widening the fraction;
-// zero, subnormals, inf and nan take the conversion instruction.  Exact.
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const unsigned long long r = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e + 896u) << 52) |
-                               ((unsigned long long)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)r);
-}
 
 template <int D, typename TX>
 __device__ __forceinline__ void load_nb_d(const TX* __restrict__ x, const Geom& g, const Vtx<D>& v,
@@ -332,13 +334,15 @@ __global__ void __launch_bounds__(128) k_apply_j(Geom g, const double* __restric
                                                  double* __restrict__ y, const double* __restrict__ y0) {
   pdl_entry();
   using Tp = Topo<D>;
+  __shared__ double sWM[Tp::NCLASS * Tp::NOFF], sWK[Tp::NCLASS * Tp::NOFF];
+  stage_tables<D>(sWM, sWK, WM, WK);
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   double z1[Tp::NOFF], z2[Tp::NOFF];
   load_nb_d<D, TZ>(z, g, v, z1);
   load_nb_d<D, TZ>(z + g.nv, g, v, z2);
-  double y1 = jc.a11hd * dot_w<D, Tp::NOFF>(WM, v.cls, z1) + jc.dthhk * dot_w<D, Tp::NAX>(WK, v.cls, z2);
-  double y2 = jc.hd * dot_w<D, Tp::NOFF>(WM, v.cls, z2) + capply_from<D, double>(g, v, coef, z1);
+  double y1 = jc.a11hd * dot_w<D, Tp::NOFF>(sWM, v.cls, z1) + jc.dthhk * dot_w<D, Tp::NAX>(sWK, v.cls, z2);
+  double y2 = jc.hd * dot_w<D, Tp::NOFF>(sWM, v.cls, z2) + capply_from<D, double>(g, v, coef, z1);
   if (y0) {
     y1 = jc.beta * y0[v.idx] + jc.alpha * y1;
     y2 = jc.beta * y0[v.idx + g.nv] + jc.alpha * y2;

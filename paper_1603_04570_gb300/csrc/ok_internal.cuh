@@ -212,6 +212,26 @@ template <> __device__ __forceinline__ double to_d<__half>(__half x) { return (d
 template <typename T> __device__ __forceinline__ T from_d(double x) { return (T)x; }
 template <> __device__ __forceinline__ __half from_d<__half>(double x) { return __float2half((float)x); }
 
+// float -> double by integer operations only (exact; zeros, infinities, NaNs
+// and subnormals included).  The hardware conversion runs on the float64 pipe,
+// which bounds the float64 kernels that widen float32 inputs.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned m = u & 0x7fffffu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  unsigned long long ex, mm;
+  if (e != 0u) {                       // normal (rebias the exponent), or inf / NaN
+    ex = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+    mm = (unsigned long long)m << 29;
+  } else {                             // zero, or subnormal m 2^-149: normalise
+    const int p = 31 - __clz(m | 1u);  // leading one of m
+    ex = m ? (unsigned long long)(p + 874) : 0ull;
+    mm = m ? (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull) : 0ull;
+  }
+  return __longlong_as_double((long long)(sgn | (ex << 52) | mm));
+}
+
 // Load all NOFF neighbour values of x (zero outside the domain).
 template <int D, typename TX, typename T>
 __device__ __forceinline__ void load_nb(const TX* __restrict__ x, const Geom& g, const Vtx<D>& v,

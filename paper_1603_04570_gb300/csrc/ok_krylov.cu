@@ -362,7 +362,12 @@ __global__ void __launch_bounds__(RT) k_multi_axpy(const TZ* __restrict__ Z, lon
   __syncthreads();
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
     double acc = x[e];
-    for (int k = 0; k < K; ++k) acc = fma(ys[k], (double)Z[k * ldz + e], acc);
+    for (int k = 0; k < K; ++k) {
+      double zk;
+      if constexpr (std::is_same<TZ, float>::value) zk = f2d_exact(Z[k * ldz + e]);
+      else zk = Z[k * ldz + e];
+      acc = fma(ys[k], zk, acc);
+    }
     x[e] = acc;
   }
 }
