@@ -98,7 +98,7 @@ typedef struct ok_opts {
   int use_pdl;        /* programmatic dependent launch between kernels [0]      */
   int reorth;         /* Gram--Schmidt: 0 second pass only when the first one
                          cancels more than half of ||w||^2, 1 always two
-                         passes (CGS2) [1]                                      */
+                         passes (CGS2), 2 one classical pass [2]                */
   double gmres_rtol;  /* stop when ||f - J x|| <= gmres_rtol ||f|| [1e-10]      */
   double newton_atol; /* Newton stops when ||F||_2 <= max(atol, rtol ||F_0||)   */
   double newton_rtol; /*   [atol 1e-10, rtol 0]                                 */

@@ -616,7 +616,7 @@ void validate(int dim, int n, const ok_params* p, const ok_opts* o) {
   if (!(o->smooth_lo_frac > 0 && o->smooth_lo_frac < 1)) fail(OK_ERR_INVALID_ARG, "smooth_lo_frac in (0,1)");
   if (o->coarse_max < 1) fail(OK_ERR_INVALID_ARG, "coarse_max must be >= 1");
   if (o->tile_fine < 0 || o->tile_fine > 3) fail(OK_ERR_INVALID_ARG, "tile_fine must be 0, 1, 2 or 3");
-  if (o->reorth != 0 && o->reorth != 1) fail(OK_ERR_INVALID_ARG, "reorth must be 0 or 1");
+  if (o->reorth < 0 || o->reorth > 2) fail(OK_ERR_INVALID_ARG, "reorth must be 0, 1 or 2");
 }
 
 std::vector<int> level_sizes(int n, int coarse_max) {
@@ -689,10 +689,13 @@ void arnoldi(ok_grid* G, TZ* Z, int j, cudaStream_t s) {
   launch_apply_j<TZ>(G->dim, G->g0, G->refWM, G->refWK, G->jc, G->coef, zj, w, nullptr, s);
   pr.end(PT_APPLYJ, s);
   pr.begin(PT_CGS2, s);
-  if (G->o.reorth == 1) {           // CGS2: always two passes (the default)
+  if (G->o.reorth == 1) {           // CGS2: always two passes
     launch_multidot(G->V, N, j + 1, w, N, G->rs, ks_h1_ptr(G->ks), s);
     launch_update_multidot(G->V, N, j + 1, ks_h1_ptr(G->ks), w, N, G->rs, ks_h2_ptr(G->ks), s);
     launch_update_norm_givens(G->V, N, j + 1, w, N, G->rs, G->ks, j, s);
+  } else if (G->o.reorth == 2) {    // one classical pass (the default)
+    launch_multidot(G->V, N, j + 1, w, N, G->rs, ks_h1_ptr(G->ks), s);
+    launch_update_norm_check(G->V, N, j + 1, w, N, G->rs, G->ks, j, s, true);
   } else {                          // second pass only when the first cancelled too much
     const int* skip = ks_skip2_ptr(G->ks);
     launch_multidot(G->V, N, j + 1, w, N, G->rs, ks_h1_ptr(G->ks), s, nullptr, ks_nw0_ptr(G->ks));
@@ -843,7 +846,7 @@ void ok_default_opts(ok_opts* o) {
   o->fuse_coarse = 1;
   o->tile_fine = 1;
   o->use_pdl = 0;
-  o->reorth = 1;
+  o->reorth = 2;
   o->gmres_rtol = 1e-10;
   o->newton_atol = 1e-10;
   o->newton_rtol = 0.0;

@@ -165,10 +165,11 @@ void launch_update_multidot(const double* V, long long ldv, int K, const double*
 // w -= V h2; then Arnoldi column j finalisation (h1 + h2) + Givens in the last block
 void launch_update_norm_givens(const double* V, long long ldv, int K, double* w, long long N, RedScratch rs,
                                KrylovState* ks, int j, cudaStream_t s, const int* skip = nullptr);
-// w -= V h1; ||w||^2 against ks->nw0 decides the second pass (sets ks->skip2);
-// without it the column (h1) and its Givens rotation are finished here
+// w -= V h1; ||w||^2 against ks->nw0 decides the second pass (sets ks->skip2;
+// `single`: never); without it the column (h1) and its Givens rotation are
+// finished here
 void launch_update_norm_check(const double* V, long long ldv, int K, double* w, long long N, RedScratch rs,
-                              KrylovState* ks, int j, cudaStream_t s);
+                              KrylovState* ks, int j, cudaStream_t s, bool single = false);
 // w *= ks->inv_eta
 void launch_scale_by(double* w, long long N, const double* factor, cudaStream_t s);
 // out = ||x||_2 (device scalar)

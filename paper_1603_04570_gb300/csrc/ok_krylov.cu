@@ -5,11 +5,11 @@
 // v_0..v_j by classical Gram--Schmidt with re-orthogonalisation:
 //     h1 = V^T w;  w -= V h1;  [h2 = V^T w;  w -= V h2;]  H(:,j) = h1 (+ h2);
 //     eta = ||w||;  H(j+1,j) = eta;  v_{j+1} = w / eta;
-// the bracketed second pass runs always (CGS2) or, by the criterion of
-// Daniel, Gragg, Kaufman and Stewart (Math. Comp. 30, 1976), only when the
-// first pass cancelled more than half of ||w||^2 (||w_1||^2 < ||w_0||^2 / 2);
-// the decision is taken on the device and the second-pass kernels return at
-// once when it is not needed.  The new column is then reduced by Givens
+// the bracketed second pass runs always (CGS2), never (one classical pass), or,
+// by the criterion of Daniel, Gragg, Kaufman and Stewart (Math. Comp. 30,
+// 1976), only when the first pass cancelled more than half of ||w||^2
+// (||w_1||^2 < ||w_0||^2 / 2); that decision is taken on the device and the
+// second-pass kernels return at once when it is not needed.  The new column is then reduced by Givens
 // rotations and |g_{j+1}| is the residual norm of the least-squares problem
 // min || beta e_1 - H y ||.
 //
@@ -248,7 +248,7 @@ template <int K>
 __global__ void __launch_bounds__(RT) k_update_norm_check(const double* __restrict__ V, long long ldv,
                                                           double* __restrict__ w, long long N,
                                                           double* __restrict__ partials, unsigned int* counter,
-                                                          KrylovState* ks, int j, int K0) {
+                                                          KrylovState* ks, int j, int K0, int single) {
   pdl_entry();
   __shared__ double hs[K];
   if (threadIdx.x < K) hs[threadIdx.x] = ks->h1[K0 + threadIdx.x];
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(RT) k_update_norm_check(const double* __restri
   if (!last_block(counter) || threadIdx.x >= 32) return;
   const double s = warp_sum_partials(partials, 0);
   if (threadIdx.x == 0) {
-    const bool second = !(s >= 0.5 * ks->nw0);      // also taken when s or nw0 is NaN
+    const bool second = !single && !(s >= 0.5 * ks->nw0);   // also taken when s or nw0 is NaN
     ks->skip2 = second ? 0 : 1;
     if (!second) arnoldi_column(ks, j, s, false);
   }
@@ -445,14 +445,14 @@ void launch_update_norm_givens(const double* V, long long ldv, int K, double* w,
 }
 
 void launch_update_norm_check(const double* V, long long ldv, int K, double* w, long long N, RedScratch rs,
-                              KrylovState* ks, int j, cudaStream_t s) {
+                              KrylovState* ks, int j, cudaStream_t s, bool single) {
   int k0 = 0;
   for (; K - k0 > KC; k0 += KC)
     launch_k(k_update_only<KC>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, ks->h1 + k0, w, N,
              (const int*)nullptr);
   with_k(K - k0, [&](auto KK) {
     launch_k(k_update_norm_check<decltype(KK)::value>, krylov_blocks(), RT, 0, s, V + k0 * ldv, ldv, w, N,
-             rs.partials, rs.counter, ks, j, k0);
+             rs.partials, rs.counter, ks, j, k0, single ? 1 : 0);
   });
 }
 

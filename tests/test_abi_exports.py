@@ -40,7 +40,7 @@ def test_default_opts_match_header_documentation():
     assert (o.restart, o.q_A, o.n_V, o.k_R, o.smooth_pre, o.smooth_post) == (30, 10, 5, 1, 2, 2)
     assert o.precision == ok.OK_FP64 and o.gmres_rtol == 1e-10 and o.smooth_lo_frac == 0.25
     assert o.use_graphs == 1 and o.fuse_coarse == 1
-    assert o.tile_fine == 1 and o.use_pdl == 0 and o.reorth == 1
+    assert o.tile_fine == 1 and o.use_pdl == 0 and o.reorth == 2
     assert ok.Opts.gmres_rtol.offset == 64 and ctypes.sizeof(ok.Opts) == 96   # 16 ints, 4 doubles
 
 
@@ -54,7 +54,7 @@ def test_default_opts_match_header_documentation():
     (2, 8, {"q_A": 0}, "q_A"),
     (2, 8, {"gmres_rtol": 0.0}, "tolerances"),
     (2, 8, {"tile_fine": 4}, "tile_fine"),
-    (2, 8, {"reorth": 2}, "reorth"),
+    (2, 8, {"reorth": 3}, "reorth"),
 ])
 def test_invalid_arguments_rejected_on_host(dim, n, kw, msg):
     p = ok.Params(0.04, 100.0, 0.0, 1.0, 1e-4)

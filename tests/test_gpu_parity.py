@@ -191,9 +191,10 @@ def test_solve_linear_meets_tolerance():
 
 @pytest.mark.parametrize("restart,K", [(8, 8), (40, 40)])
 def test_gram_schmidt_variants_agree(restart, K):
-    """Second Gram--Schmidt pass only when needed (reorth = 0) against always
-    two passes (reorth = 1): both meet the true-residual tolerance with the
-    same iteration count, and the solutions agree far below the tolerance.
+    """Second Gram--Schmidt pass only when needed (reorth = 0) and one pass
+    (reorth = 2) against always two passes (reorth = 1): all meet the
+    true-residual tolerance with (nearly) the same iteration count, and the
+    solutions agree far below the tolerance.
     restart 40 takes more than 16 basis vectors per step (chunked kernels)."""
     sysm, p, rng = make(2, 48, seed=9, dt=1e-4)
     nv = sysm.mesh.nv
@@ -201,7 +202,7 @@ def test_gram_schmidt_variants_agree(restart, K):
     f = rng.standard_normal(2 * nv)
     J = sysm.jacobian(u)
     xs, its = [], []
-    for reorth in (0, 1):
+    for reorth in (0, 1, 2):
         with ok.Grid(2, 48, **p, gmres_rtol=1e-12, restart=restart, reorth=reorth, q_A=2, n_V=1) as g:
             x = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
             info = g.solve_linear(dev(u), dev(f), x)
@@ -209,8 +210,9 @@ def test_gram_schmidt_variants_agree(restart, K):
             assert np.linalg.norm(f - J @ xh) <= 1.01e-12 * np.linalg.norm(f)
             xs.append(xh)
             its.append(info.gmres_its)
-    assert abs(its[0] - its[1]) <= 1 and its[0] > min(K, 17)
-    assert np.linalg.norm(xs[0] - xs[1]) <= 1e-9 * np.linalg.norm(xs[1])
+    assert abs(its[0] - its[1]) <= 1 and abs(its[2] - its[1]) <= 2 and its[0] > min(K, 17)
+    for k in (0, 2):
+        assert np.linalg.norm(xs[k] - xs[1]) <= 1e-9 * np.linalg.norm(xs[1])
 
 
 def test_graphs_and_streams_are_bitwise_identical():
