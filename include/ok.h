@@ -91,7 +91,12 @@ typedef struct ok_opts {
   int precision;      /* OK_FP64 or OK_MIXED [OK_FP64]                          */
   int coarse_max;     /* halve the grid while n is even and > coarse_max [4]    */
   int use_graphs;     /* capture each Arnoldi step in a CUDA graph [1]          */
-  int fuse_coarse;    /* run the coarse multigrid levels in one kernel [1]      */
+  int fuse_coarse;    /* coarse multigrid levels in one launch: 0 off; 1 the
+                         suffix of levels that fits one block's shared memory
+                         in one block; 2 with the 2D tile kernels the levels
+                         of <= 129 vertices per side and the coarsest solve as
+                         one thread-block cluster (when the device supports
+                         it), otherwise as 1 [1]                                 */
   int tile_fine;      /* 2D: register-strip tile kernels on the fine levels:
                          0 off, 1 automatic window width, 2 / 3 force 32 / 64
                          columns [1]                                            */

@@ -97,12 +97,12 @@ thread_local bool okg::g_pdl = false;
 // ---------------------------------------------------------------------------
 enum ProfTag {
   PT_PRECOND = 0, PT_APPLYJ, PT_CGS2, PT_SMOOTH0, PT_CHEBM, PT_TPRE0, PT_TPOST0, PT_TAMASS,
-  PT_TPRE1, PT_TPOST1, PT_TPRE2, PT_TPOST2, PT_TPRE3, PT_TPOST3, PT_TPRE4, PT_TPOST4, PT_COARSE, PT_COUNT
+  PT_TPRE1, PT_TPOST1, PT_TPRE2, PT_TPOST2, PT_TPRE3, PT_TPOST3, PT_TPRE4, PT_TPOST4, PT_COARSE, PT_LOW, PT_COUNT
 };
 static const char* const kProfNames[PT_COUNT] = {
     "precond", "apply_j", "cgs2", "mg_smooth_l0", "cheb_mass_step", "mg_tile_pre_l0", "mg_tile_post_l0",
     "tile_mass_cstep", "mg_tile_pre_l1", "mg_tile_post_l1", "mg_tile_pre_l2", "mg_tile_post_l2",
-    "mg_tile_pre_l3", "mg_tile_post_l3", "mg_tile_pre_l4", "mg_tile_post_l4", "mg_coarse"};
+    "mg_tile_pre_l3", "mg_tile_post_l3", "mg_tile_pre_l4", "mg_tile_post_l4", "mg_coarse", "mg_low"};
 // tags of the tile kernels of level l (pre, post); -1 below level 4
 static inline int tile_tag(int l, bool post) {
   if (l == 0) return post ? PT_TPOST0 : PT_TPRE0;
@@ -204,6 +204,10 @@ template <typename T> struct Prec {
   T* gemv_inv = nullptr;       // nc > GEMV_MIN: the inverse with padded row stride gemv_ldA
   long long gemv_ldA = 0;
   static constexpr long long GEMV_MIN = 512;   // above: many-block GEMV, else one block
+#ifndef OK_LOW_N1
+#define OK_LOW_N1 129
+#endif
+  static constexpr int LOW_N1 = OK_LOW_N1;      // cluster kernel: levels of at most this many vertices per side
 
   void coarse_solve(const T* rhs, T* x, cudaStream_t s) {
     if (gemv_inv) launch_coarse_gemv<T>(nc, gemv_ldA, gemv_inv, rhs, x, s);
@@ -221,6 +225,9 @@ template <typename T> struct Prec {
   int Lc = 0;
   CoarseArgs<T> ca{};
   size_t csmem = 0;
+  bool low = false;            // 2D tiles: levels Lf.. and the coarsest solve in one cluster launch
+  int Lf = 0, low_cluster = 0;
+  LowArgs<T> la{};
   bool tiled = false;          // 2D: levels above Lc by shared-memory tile kernels
   std::vector<TileSmooth<T>> ts;
   TileMass<T> tm{};
@@ -233,6 +240,12 @@ template <typename T> struct Prec {
   // V-cycle with tile kernels on the levels above Lc (x ping-pongs between x and xa)
   template <typename TO>
   void vcycle_t(int l, bool x_zero, const T* rhs, TO* out, T* mx, cudaStream_t s) {
+    if (low && l == Lf) {               // x from zero on rhs = lv[Lf].b; result in lv[Lf].x
+      if (prof) prof->begin(PT_LOW, s);
+      launch_low_vcycle<T>(la, low_cluster, s);
+      if (prof) prof->end(PT_LOW, s);
+      return;
+    }
     if (fused && l == Lc) {
       if (prof) prof->begin(PT_COARSE, s);
       launch_coarse_vcycle<T>(dim, ca, csmem, rhs, x_zero ? (const T*)nullptr : X(l), X(l), s);
@@ -522,7 +535,23 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
     tot += need;
     Lc = l;
   }
-  if (G->o.fuse_coarse && nl - Lc >= 2) {
+  // fuse_coarse == 2 with the 2D tile kernels: the levels of at most LOW_N1
+  // vertices per side (from level 1 down) and the coarsest solve run as one
+  // thread-block cluster when the device supports it; otherwise (and with
+  // fuse_coarse == 1) the single-block coarse V-cycle for the suffix above.
+  // (On GB300 at 1025^2 the cluster launch is slower than separate launches:
+  // 16 SMs leave most of each phase's windows serialised.)
+  int low_cluster = 0, Lf = nl - 1;
+  if (tiles_ok && G->o.fuse_coarse == 2 && nl >= 3) {
+    for (int l = 1; l < nl - 1; ++l)
+      if (P.lv[l].g.n1 <= Prec<T>::LOW_N1) {
+        Lf = l;
+        break;
+      }
+    const int nlow = nl - 1 - Lf;
+    if (nlow >= 1 && nlow <= LOW_MAXLEV) low_cluster = prepare_low_vcycle<T>(nc);
+  }
+  if (G->o.fuse_coarse && low_cluster == 0 && nl - Lc >= 2) {
     CoarseArgs<T>& ca = P.ca;
     ca.nlev = nl - Lc;
     long long off = 0;
@@ -592,6 +621,31 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
     P.b2 = A.alloc<T>(P.lv[0].g.nv);
     CK(prepare_tiles<T>(P.q_A));
     P.tiled = true;
+    if (low_cluster > 0) {
+      LowArgs<T>& la = P.la;
+      la.nl = nl - 1 - Lf;
+      for (int i = 0; i < la.nl; ++i) {
+        la.ts[i] = P.ts[Lf + i];
+        la.P[i] = P.lv[Lf + i].xa;       // the iterate buffers never swap below Lf (x from zero, two
+        la.Q[i] = P.lv[Lf + i].x;        // swaps per V-cycle), so the launch arguments are fixed
+        la.rhs[i] = P.lv[Lf + i].b;
+      }
+      la.rhs[la.nl] = P.lv[nl - 1].b;
+      la.xc = P.lv[nl - 1].x;
+      if (!P.gemv_inv) {
+        P.gemv_ldA = gemv_ld(nc, sizeof(T));
+        P.gemv_inv = A.alloc<T>(nc * P.gemv_ldA);
+        CK(cudaMemset(P.gemv_inv, 0, nc * P.gemv_ldA * sizeof(T)));
+        CK(cudaMemcpy2D(P.gemv_inv, P.gemv_ldA * sizeof(T), P.coarse_inv, nc * sizeof(T), nc * sizeof(T), nc,
+                        cudaMemcpyDeviceToDevice));
+      }
+      la.nc = nc;
+      la.ldA = P.gemv_ldA;
+      la.A = P.gemv_inv;
+      P.low = true;
+      P.Lf = Lf;
+      P.low_cluster = low_cluster;
+    }
   }
 }
 
@@ -617,6 +671,7 @@ void validate(int dim, int n, const ok_params* p, const ok_opts* o) {
   if (o->coarse_max < 1) fail(OK_ERR_INVALID_ARG, "coarse_max must be >= 1");
   if (o->tile_fine < 0 || o->tile_fine > 3) fail(OK_ERR_INVALID_ARG, "tile_fine must be 0, 1, 2 or 3");
   if (o->reorth < 0 || o->reorth > 2) fail(OK_ERR_INVALID_ARG, "reorth must be 0, 1 or 2");
+  if (o->fuse_coarse < 0 || o->fuse_coarse > 2) fail(OK_ERR_INVALID_ARG, "fuse_coarse must be 0, 1 or 2");
 }
 
 std::vector<int> level_sizes(int n, int coarse_max) {

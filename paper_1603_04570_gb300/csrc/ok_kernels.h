@@ -143,6 +143,31 @@ cudaError_t prepare_tiles(int q);
 template <typename T>
 long long strip_blocks(const Geom& g, int tile);
 
+// The bottom of a 2D V-cycle in one launch of one thread-block cluster: the
+// pre-smoothing kernels' work on levels 0..nl-1 of the argument (finest
+// first), the dense solve of the coarsest level, then the post-smoothing
+// kernels' work back up, phases separated by cluster barriers.  Level i
+// pre-smooths from zero on rhs[i] into P[i] and restricts into rhs[i+1];
+// rhs[nl] is the coarsest level's right-hand side, xc its solution; level i
+// post-smooths P[i] + prolongated (i == nl-1 ? xc : Q[i+1]) into Q[i].
+constexpr int LOW_MAXLEV = 6;
+template <typename T> struct LowArgs {
+  int nl;
+  TileSmooth<T> ts[LOW_MAXLEV];
+  T* P[LOW_MAXLEV];
+  T* Q[LOW_MAXLEV];
+  T* rhs[LOW_MAXLEV + 1];
+  long long nc, ldA;       // coarsest level: unknowns, padded row stride of its inverse
+  const T* A;              // zero-padded dense inverse
+  T* xc;
+};
+// cluster size usable for the kernel on this device (16, 8, or 0: none); sets
+// the kernel's attributes for a coarsest level of nc unknowns
+template <typename T>
+int prepare_low_vcycle(long long nc);
+template <typename T>
+void launch_low_vcycle(const LowArgs<T>& a, int cluster, cudaStream_t s);
+
 // dense matrix of a level operator (row-major nv x nv) from its class table
 void launch_dense_from_table(int dim, const Geom& g, const double* W, double* A, cudaStream_t s);
 // in-place Gauss--Jordan inverse of an SPD matrix (single block); work: n x 2n

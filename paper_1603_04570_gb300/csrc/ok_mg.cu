@@ -327,78 +327,22 @@ __global__ void k_gj_extract(long long n, const double* __restrict__ w, double* 
   }
 }
 
-// x = Ainv b by many blocks, a warp per row.  Ainv is stored with a padded
-// row stride ld (a multiple of 16 bytes, zeros beyond column nc), so each lane
-// issues GEMV_NPL independent 16-byte loads before it multiplies; b is staged
-// in shared memory, zero-padded to the vector chunk.
-constexpr int GEMV_NPL = 8;          // 16-byte vectors per lane per chunk
+// x = Ainv b by many blocks, a warp per row (gemv_row of ok_stencil.cuh on the
+// zero-padded inverse; b staged in shared memory).
 constexpr int GEMV_WARPS = 8;
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { using type = float4; static constexpr int E = 4; };
-template <> struct Vec16<double> { using type = double2; static constexpr int E = 2; };
-template <typename T>
-__device__ __forceinline__ T vec_at(const typename Vec16<T>::type& v, int e);
-template <> __device__ __forceinline__ float vec_at<float>(const float4& v, int e) {
-  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
-}
-template <> __device__ __forceinline__ double vec_at<double>(const double2& v, int e) { return e == 0 ? v.x : v.y; }
-// 16-byte read-only loads kept in program order (volatile), so a lane's loads
-// of one chunk are all in flight before the first multiply
-__device__ __forceinline__ void ld16(const float4* p, float4& v) {
-  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-}
-__device__ __forceinline__ void ld16(const double2* p, double2& v) {
-  asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
-}
 
 template <typename T>
 __global__ void __launch_bounds__(GEMV_WARPS * 32) k_coarse_gemv(long long nc, long long ld, const T* __restrict__ A,
                                                                 const T* __restrict__ b, T* __restrict__ x) {
   pdl_entry();
-  using V = typename Vec16<T>::type;
-  constexpr int E = Vec16<T>::E;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sb = reinterpret_cast<T*>(smraw);
-  const long long nvec = ld / E;
-  const long long chunk = 32LL * GEMV_NPL;
-  const long long nb = ((nvec + chunk - 1) / chunk) * chunk * E;
-  for (long long i = threadIdx.x; i < nb; i += blockDim.x) sb[i] = i < nc ? b[i] : (T)0;
+  gemv_stage_b<T, false>(nc, ld, b, sb);
   __syncthreads();
-  const int lane = threadIdx.x & 31;
   const long long r = (long long)blockIdx.x * GEMV_WARPS + (threadIdx.x >> 5);
   if (r >= nc) return;
-  const V* Ar = reinterpret_cast<const V*>(A + r * ld);
-  const V* sv = reinterpret_cast<const V*>(sb);
-  T acc = (T)0;
-  auto mac = [&](const V (&a)[GEMV_NPL], long long base) {
-#pragma unroll
-    for (int k = 0; k < GEMV_NPL; ++k) {
-      const V bv = sv[base + lane + 32 * k];
-#pragma unroll
-      for (int e = 0; e < E; ++e) acc = fma(vec_at<T>(a[k], e), vec_at<T>(bv, e), acc);
-    }
-  };
-  long long base = 0;
-  for (; base + chunk <= nvec; base += chunk) {      // full chunks: all loads issued first
-    V a[GEMV_NPL];
-#pragma unroll
-    for (int k = 0; k < GEMV_NPL; ++k) ld16(Ar + base + lane + 32 * k, a[k]);
-    mac(a, base);
-  }
-  if (base < nvec) {                                 // ragged last chunk
-    V a[GEMV_NPL];
-#pragma unroll
-    for (int k = 0; k < GEMV_NPL; ++k) {
-      const long long c = base + lane + 32 * k;
-      a[k] = V{};
-      if (c < nvec) ld16(Ar + c, a[k]);
-    }
-    mac(a, base);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) x[r] = acc;
+  const T acc = gemv_row<T>(ld, A, sb, r);
+  if ((threadIdx.x & 31) == 0) x[r] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -453,19 +397,14 @@ long long gemv_ld(long long nc, size_t elem) {
   return (nc + e - 1) / e * e;
 }
 template <typename T>
-size_t gemv_smem(long long nc) {
-  const long long E = Vec16<T>::E, chunk = 32LL * GEMV_NPL;
-  const long long nvec = gemv_ld(nc, sizeof(T)) / E;
-  return (size_t)(((nvec + chunk - 1) / chunk) * chunk * E) * sizeof(T);
-}
-template <typename T>
 void launch_coarse_gemv(long long nc, long long ld, const T* Ainv, const T* b, T* x, cudaStream_t s) {
   const unsigned blocks = (unsigned)((nc + GEMV_WARPS - 1) / GEMV_WARPS);
-  launch_k(k_coarse_gemv<T>, blocks, GEMV_WARPS * 32, gemv_smem<T>(nc), s, nc, ld, Ainv, b, x);
+  launch_k(k_coarse_gemv<T>, blocks, GEMV_WARPS * 32, gemv_staged<T>(ld) * sizeof(T), s, nc, ld, Ainv, b, x);
 }
 template <typename T>
 cudaError_t prepare_coarse_gemv(long long nc) {
-  return cudaFuncSetAttribute(k_coarse_gemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemv_smem<T>(nc));
+  return cudaFuncSetAttribute(k_coarse_gemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(gemv_staged<T>(gemv_ld(nc, sizeof(T))) * sizeof(T)));
 }
 template <typename T, typename TX, typename TY>
 void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha,

@@ -103,6 +103,89 @@ __device__ __forceinline__ void coarse_rows(long long nc, const T* A, const T* b
 }
 
 // ---------------------------------------------------------------------------
+// Dense coarsest-level GEMV with 16-byte loads.  The inverse has a padded row
+// stride ld (a multiple of 16 bytes, zeros beyond column nc); b is staged in
+// shared memory, zero-padded to whole chunks of 32 * GEMV_NPL vectors.  Lane l
+// takes the vectors l, l + 32, ... in order, so the sum is that of coarse_rows.
+// ---------------------------------------------------------------------------
+constexpr int GEMV_NPL = 8;          // 16-byte vectors per lane per chunk
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int E = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int E = 2; };
+template <typename T>
+__device__ __forceinline__ T vec_at(const typename Vec16<T>::type& v, int e);
+template <> __device__ __forceinline__ float vec_at<float>(const float4& v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+template <> __device__ __forceinline__ double vec_at<double>(const double2& v, int e) { return e == 0 ? v.x : v.y; }
+// 16-byte read-only loads kept in program order (volatile), so a lane's loads
+// of one chunk are all in flight before the first multiply
+__device__ __forceinline__ void ld16(const float4* p, float4& v) {
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+}
+__device__ __forceinline__ void ld16(const double2* p, double2& v) {
+  asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+}
+
+// elements of the staged b (padded to whole chunks)
+template <typename T>
+__host__ __device__ inline long long gemv_staged(long long ld) {
+  const long long E = Vec16<T>::E, chunk = 32LL * GEMV_NPL;
+  const long long nvec = ld / E;
+  return ((nvec + chunk - 1) / chunk) * chunk * E;
+}
+
+// sb[i] = b[i] (i < nc), 0 up to the padded length; CG: b may have been written
+// by other blocks of the same launch (load through L2)
+template <typename T, bool CG>
+__device__ __forceinline__ void gemv_stage_b(long long nc, long long ld, const T* b, T* sb) {
+  const long long nb = gemv_staged<T>(ld);
+  for (long long i = threadIdx.x; i < nb; i += blockDim.x) sb[i] = i < nc ? (CG ? __ldcg(b + i) : b[i]) : (T)0;
+}
+
+// row r of A times the staged b, by one warp (result in every lane)
+template <typename T>
+__device__ __forceinline__ T gemv_row(long long ld, const T* __restrict__ A, const T* sb, long long r) {
+  using V = typename Vec16<T>::type;
+  constexpr int E = Vec16<T>::E;
+  const int lane = threadIdx.x & 31;
+  const long long nvec = ld / E;
+  const long long chunk = 32LL * GEMV_NPL;
+  const V* Ar = reinterpret_cast<const V*>(A + r * ld);
+  const V* sv = reinterpret_cast<const V*>(sb);
+  T acc = (T)0;
+  auto mac = [&](const V (&a)[GEMV_NPL], long long base) {
+#pragma unroll
+    for (int k = 0; k < GEMV_NPL; ++k) {
+      const V bv = sv[base + lane + 32 * k];
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc = fma(vec_at<T>(a[k], e), vec_at<T>(bv, e), acc);
+    }
+  };
+  long long base = 0;
+  for (; base + chunk <= nvec; base += chunk) {      // full chunks: all loads issued first
+    V a[GEMV_NPL];
+#pragma unroll
+    for (int k = 0; k < GEMV_NPL; ++k) ld16(Ar + base + lane + 32 * k, a[k]);
+    mac(a, base);
+  }
+  if (base < nvec) {                                 // ragged last chunk
+    V a[GEMV_NPL];
+#pragma unroll
+    for (int k = 0; k < GEMV_NPL; ++k) {
+      const long long c = base + lane + 32 * k;
+      a[k] = V{};
+      if (c < nvec) ld16(Ar + c, a[k]);
+    }
+    mac(a, base);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
 // The same bodies with one class's weights held in registers (vertices all of
 // that class, e.g. the interior of a tile): identical arithmetic and order.
 // ---------------------------------------------------------------------------

@@ -69,6 +69,7 @@ template <> struct StripCfg<float> {
   template <int H> using Big = SG<OK_STRIP_F_BIG, H>;
   template <int H> using Small = SG<OK_STRIP_F_SMALL, H>;
   using Mass = SG<OK_STRIP_F_MASS, QTILE>;
+  template <int H> using Low = SG<64, 4, 16, H>;       // one window per block of the cluster kernel
 };
 #ifndef OK_STRIP_D_BIG
 #define OK_STRIP_D_BIG 64, 2, 16
@@ -83,6 +84,7 @@ template <> struct StripCfg<double> {
   template <int H> using Big = SG<OK_STRIP_D_BIG, H>;
   template <int H> using Small = SG<OK_STRIP_D_SMALL, H>;
   using Mass = SG<OK_STRIP_D_MASS, QTILE>;
+  template <int H> using Low = SG<64, 2, 16, H>;
 };
 
 // this thread's strip
@@ -93,13 +95,14 @@ struct Pos {
   bool colin;      // 0 <= gx <= n
 };
 
+// window (wx, wy) of a level: owned vertices [wx OW, wx OW + OW) x [wy OH, wy OH + OH)
 template <class G>
-__device__ __forceinline__ Pos strip_pos(int n) {
+__device__ __forceinline__ Pos strip_pos(int n, int wx, int wy) {
   Pos p;
   p.lx = threadIdx.x % G::CW;
   p.ly0 = (threadIdx.x / G::CW) * G::RY;
-  p.gx = blockIdx.x * G::OW - G::H + p.lx;
-  p.gy0 = blockIdx.y * G::OH - G::H + p.ly0;
+  p.gx = wx * G::OW - G::H + p.lx;
+  p.gy0 = wy * G::OH - G::H + p.ly0;
   p.colin = p.gx >= 0 && p.gx <= n;
   p.cx = axis_class(p.gx, n);
   return p;
@@ -107,9 +110,17 @@ __device__ __forceinline__ Pos strip_pos(int n) {
 
 // every vertex of the window strictly inside the domain (interior class)?
 template <class G>
-__device__ __forceinline__ bool strip_interior(int n) {
-  const int x0 = blockIdx.x * G::OW - G::H, y0 = blockIdx.y * G::OH - G::H;
+__device__ __forceinline__ bool strip_interior(int n, int wx, int wy) {
+  const int x0 = wx * G::OW - G::H, y0 = wy * G::OH - G::H;
   return x0 >= 1 && y0 >= 1 && x0 + G::CW - 1 <= n - 1 && y0 + G::CH - 1 <= n - 1;
+}
+
+// Global load of data that other thread blocks of the same launch may have
+// written (CG: through L2, never a stale L1 line or the read-only path).
+template <bool CG, typename T>
+__device__ __forceinline__ T ldg(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
 }
 
 __device__ __forceinline__ bool row_in(const Pos& p, int i, int n) {
@@ -188,7 +199,7 @@ __device__ __forceinline__ void load_table(T* s, const T* g, int count, int nt) 
 // ---------------------------------------------------------------------------
 // pre-smoothing (2 steps) + restriction
 // ---------------------------------------------------------------------------
-template <typename T, class G, bool INT>
+template <typename T, class G, bool INT, bool CG = false>
 __device__ __forceinline__ void strip_pre_body(const TileSmooth<T>& a, const Pos& p, T* buf0, T* buf1,
                                                const T* sW, const T* sD, const T* x_in, const T* b, T* x_out,
                                                T* bc) {
@@ -201,8 +212,8 @@ __device__ __forceinline__ void strip_pre_body(const TileSmooth<T>& a, const Pos
   for (int i = 0; i < RY; ++i) {
     const bool in = INT || row_in(p, i, n);
     const long long gi = p.gx + sy * (p.gy0 + i);
-    bb[i] = in ? b[gi] : (T)0;
-    x[i] = (in && !xz) ? x_in[gi] : (T)0;
+    bb[i] = in ? ldg<CG>(b + gi) : (T)0;
+    x[i] = (in && !xz) ? ldg<CG>(x_in + gi) : (T)0;
   }
   if (!xz) xput<G>(buf0, p, x);
   __syncthreads();                                  // tables (and x) visible
@@ -299,15 +310,17 @@ __global__ void __launch_bounds__(G::NT) k_strip_pre(TileSmooth<T> a, const T* _
   T* sD = sW + NTAB;
   load_table<T>(sW, a.W, NTAB, G::NT);
   load_table<T>(sD, a.dinv, Topo<2>::NCLASS, G::NT);
-  const Pos p = strip_pos<G>(a.g.n);
-  if (strip_interior<G>(a.g.n)) strip_pre_body<T, G, true>(a, p, buf0, buf1, sW, sD, x_in, b, x_out, bc);
-  else strip_pre_body<T, G, false>(a, p, buf0, buf1, sW, sD, x_in, b, x_out, bc);
+  const Pos p = strip_pos<G>(a.g.n, blockIdx.x, blockIdx.y);
+  if (strip_interior<G>(a.g.n, blockIdx.x, blockIdx.y))
+    strip_pre_body<T, G, true>(a, p, buf0, buf1, sW, sD, x_in, b, x_out, bc);
+  else
+    strip_pre_body<T, G, false>(a, p, buf0, buf1, sW, sD, x_in, b, x_out, bc);
 }
 
 // ---------------------------------------------------------------------------
 // prolongation + post-smoothing (2 steps) [+ M x] [+ cast of x]
 // ---------------------------------------------------------------------------
-template <typename T, typename TO, class G, bool INT>
+template <typename T, typename TO, class G, bool INT, bool CG = false>
 __device__ __forceinline__ void strip_post_body(const TileSmooth<T>& a, const Pos& p, T* buf0, T* buf1,
                                                 const T* sW, const T* sD, const T* sM, const T* x_in,
                                                 const T* xc, const T* b, T* x_out, T* mx_out, TO* out,
@@ -325,14 +338,14 @@ __device__ __forceinline__ void strip_post_body(const TileSmooth<T>& a, const Po
     bb[i] = (T)0;
     x[i] = (T)0;
     if (in) {
-      bb[i] = b[gi];
-      const T xv = x_in[gi];
+      bb[i] = ldg<CG>(b + gi);
+      const T xv = ldg<CG>(x_in + gi);
       // prolongation, as prolong_add_at
       const int hy = gy >> 1, oy = gy & 1;
       const long long ci = (long long)hx + scy * hy;
       const long long cj = (long long)(hx + ox) + scy * (hy + oy);
       const bool mid = ox || oy;
-      const T xci = xc[ci], xcj = xc[cj];
+      const T xci = ldg<CG>(xc + ci), xcj = ldg<CG>(xc + cj);
       x[i] = mid ? fma((T)0.5, xci + xcj, xv) : xv + xci;
     }
   }
@@ -414,8 +427,8 @@ __global__ void __launch_bounds__(G::NT) k_strip_post(TileSmooth<T> a, const T* 
   load_table<T>(sW, a.W, NTAB, G::NT);
   load_table<T>(sD, a.dinv, Topo<2>::NCLASS, G::NT);
   if (mx_out) load_table<T>(sM, a.WM, NTAB, G::NT);
-  const Pos p = strip_pos<G>(a.g.n);
-  if (strip_interior<G>(a.g.n))
+  const Pos p = strip_pos<G>(a.g.n, blockIdx.x, blockIdx.y);
+  if (strip_interior<G>(a.g.n, blockIdx.x, blockIdx.y))
     strip_post_body<T, TO, G, true>(a, p, buf0, buf1, sW, sD, sM, x_in, xc, b, x_out, mx_out, out, oscale);
   else
     strip_post_body<T, TO, G, false>(a, p, buf0, buf1, sW, sD, sM, x_in, xc, b, x_out, mx_out, out, oscale);
@@ -516,9 +529,138 @@ __global__ void __launch_bounds__(G::NT) k_strip_amass(TileMass<T> a, const doub
   T* sD = sW + NTAB;
   load_table<T>(sW, a.WM, NTAB, G::NT);
   load_table<T>(sD, a.dinvM, Topo<2>::NCLASS, G::NT);
-  const Pos p = strip_pos<G>(a.g.n);
-  if (strip_interior<G>(a.g.n)) strip_amass_body<T, TZ, G, true>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
+  const Pos p = strip_pos<G>(a.g.n, blockIdx.x, blockIdx.y);
+  if (strip_interior<G>(a.g.n, blockIdx.x, blockIdx.y))
+    strip_amass_body<T, TZ, G, true>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
   else strip_amass_body<T, TZ, G, false>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
+}
+
+// ---------------------------------------------------------------------------
+// bottom of the V-cycle in one cluster (see LowArgs in ok_kernels.h)
+// ---------------------------------------------------------------------------
+// all threads of all blocks of the cluster (every thread reaches every call:
+// the phase loops are uniform); release/acquire at cluster scope orders the
+// global-memory writes of one phase before the reads of the next.  The
+// non-.aligned forms do not require the warp to be converged.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+template <typename T, class GP, class GQ>
+__global__ void __launch_bounds__(GP::NT, 1) k_low_vcycle(LowArgs<T> a) {
+  static_assert(GP::NT == GQ::NT && GP::SB == GQ::SB, "pre and post windows share the block shape");
+  pdl_entry();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* buf0 = reinterpret_cast<T*>(smraw);
+  T* buf1 = buf0 + GP::SB;
+  T* sW = buf1 + GP::SB;
+  T* sD = sW + NTAB;
+  for (int i = 0; i < a.nl; ++i) {                  // pre-smoothing and restriction, finest first
+    const TileSmooth<T>& ts = a.ts[i];
+    const int nx = (ts.g.n1 + GP::OW - 1) / GP::OW, ny = (ts.g.n1 + GP::OH - 1) / GP::OH;
+    for (int w = blockIdx.x; w < nx * ny; w += gridDim.x) {
+      load_table<T>(sW, ts.W, NTAB, GP::NT);
+      load_table<T>(sD, ts.dinv, Topo<2>::NCLASS, GP::NT);
+      const int wx = w % nx, wy = w / nx;
+      const Pos p = strip_pos<GP>(ts.g.n, wx, wy);
+      if (strip_interior<GP>(ts.g.n, wx, wy))
+        strip_pre_body<T, GP, true, true>(ts, p, buf0, buf1, sW, sD, (const T*)nullptr, a.rhs[i], a.P[i],
+                                          a.rhs[i + 1]);
+      else
+        strip_pre_body<T, GP, false, true>(ts, p, buf0, buf1, sW, sD, (const T*)nullptr, a.rhs[i], a.P[i],
+                                           a.rhs[i + 1]);
+      __syncthreads();                              // exchange buffers and tables are reused
+    }
+    cluster_barrier();
+  }
+  {                                                 // coarsest level: xc = A rhs[nl]
+    T* sb = buf0;
+    gemv_stage_b<T, true>(a.nc, a.ldA, a.rhs[a.nl], sb);
+    __syncthreads();
+    constexpr int W = GP::NT / 32;
+    for (long long r = (long long)blockIdx.x * W + (threadIdx.x >> 5); r < a.nc; r += (long long)gridDim.x * W) {
+      const T v = gemv_row<T>(a.ldA, a.A, sb, r);
+      if ((threadIdx.x & 31) == 0) a.xc[r] = v;
+    }
+  }
+  cluster_barrier();
+  for (int i = a.nl - 1; i >= 0; --i) {             // prolongation and post-smoothing, coarsest first
+    const TileSmooth<T>& ts = a.ts[i];
+    const T* xcoarse = i == a.nl - 1 ? a.xc : a.Q[i + 1];
+    const int nx = (ts.g.n1 + GQ::OW - 1) / GQ::OW, ny = (ts.g.n1 + GQ::OH - 1) / GQ::OH;
+    for (int w = blockIdx.x; w < nx * ny; w += gridDim.x) {
+      load_table<T>(sW, ts.W, NTAB, GQ::NT);
+      load_table<T>(sD, ts.dinv, Topo<2>::NCLASS, GQ::NT);
+      const int wx = w % nx, wy = w / nx;
+      const Pos p = strip_pos<GQ>(ts.g.n, wx, wy);
+      if (strip_interior<GQ>(ts.g.n, wx, wy))
+        strip_post_body<T, T, GQ, true, true>(ts, p, buf0, buf1, sW, sD, (const T*)nullptr, a.P[i], xcoarse,
+                                              a.rhs[i], a.Q[i], (T*)nullptr, (T*)nullptr, (T)1);
+      else
+        strip_post_body<T, T, GQ, false, true>(ts, p, buf0, buf1, sW, sD, (const T*)nullptr, a.P[i], xcoarse,
+                                               a.rhs[i], a.Q[i], (T*)nullptr, (T*)nullptr, (T)1);
+      __syncthreads();
+    }
+    if (i > 0) cluster_barrier();
+  }
+}
+
+template <typename T>
+static size_t low_smem(long long nc) {
+  using GP = typename StripCfg<T>::template Low<4>;
+  const size_t win = (2 * (size_t)GP::SB + NTAB + Topo<2>::NCLASS) * sizeof(T);
+  const size_t gem = (size_t)gemv_staged<T>(gemv_ld(nc, sizeof(T))) * sizeof(T);
+  return win > gem ? win : gem;
+}
+
+template <typename T>
+int prepare_low_vcycle(long long nc) {
+  using GP = typename StripCfg<T>::template Low<4>;
+  using GQ = typename StripCfg<T>::template Low<3>;
+  auto kern = k_low_vcycle<T, GP, GQ>;
+  const size_t smem = low_smem<T>(nc);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  for (int c : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c, 1, 1);
+    cfg.blockDim = dim3(GP::NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1) return c;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+template <typename T>
+void launch_low_vcycle(const LowArgs<T>& a, int cluster, cudaStream_t s) {
+  using GP = typename StripCfg<T>::template Low<4>;
+  using GQ = typename StripCfg<T>::template Low<3>;
+  count_launch();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster, 1, 1);
+  cfg.blockDim = dim3(GP::NT, 1, 1);
+  cfg.dynamicSmemBytes = low_smem<T>(a.nc);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_low_vcycle<T, GP, GQ>, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -597,7 +739,9 @@ long long strip_blocks(const Geom& g, int tile) {
                                        cudaStream_t);                                                         \
   template void launch_tile_amass<T, T>(const TileMass<T>&, const double*, T*, T*, cudaStream_t);             \
   template cudaError_t prepare_tiles<T>(int);                                                                 \
-  template long long strip_blocks<T>(const Geom&, int);
+  template long long strip_blocks<T>(const Geom&, int);                                                       \
+  template int prepare_low_vcycle<T>(long long);                                                              \
+  template void launch_low_vcycle<T>(const LowArgs<T>&, int, cudaStream_t);
 OK_TILE_INST(float)
 OK_TILE_INST(double)
 template void launch_tile_post<float, double>(const TileSmooth<float>&, const float*, const float*, const float*,

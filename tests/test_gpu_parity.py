@@ -309,22 +309,40 @@ def test_profiling_samples_and_launch_count(tile):
         assert launched > 20 * info.gmres_its        # preconditioner + Arnoldi kernels per iteration
 
 
+def test_cluster_bottom_of_the_vcycle_runs():
+    """fuse_coarse = 2 with the 2D tile kernels runs the levels 65^2 .. 5^2 of a
+    129^2 hierarchy and the coarsest solve as one cluster launch per V-cycle."""
+    wl = oi.scaled(oi.SMALL_2D, 128)
+    u0 = oi.initial_u(wl)
+    with ok.Grid(2, 128, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, fuse_coarse=2) as g:
+        u, w = dev(u0), torch.zeros(g.nv, dtype=torch.float64, device="cuda")
+        g.init_w(u, w)
+        ok.ok_profile(g.handle, True)
+        info = g.timestep(u, w)
+        stats = ok.ok_profile_read(g.handle)
+        ok.ok_profile(g.handle, False)
+        assert stats["mg_low"][0] == info.gmres_its and info.converged
+
+
 @pytest.mark.parametrize("dim,n", [(2, 64), (2, 160), (2, 12), (3, 24), (3, 16), (3, 6)])
 @pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
 def test_fused_coarse_vcycle_is_bitwise_identical(dim, n, precision):
-    """The one-block shared-memory coarse V-cycle takes the same steps as the
-    one-kernel-per-step path, so the preconditioner outputs agree bitwise."""
+    """The fused bottoms of the V-cycle take the same steps as the
+    one-kernel-per-step path, so the preconditioner outputs agree bitwise:
+    fuse_coarse 1 (the one-block shared-memory coarse V-cycle) and 2 (2D: the
+    thread-block-cluster launch over the levels of at most 129^2 vertices and
+    the coarsest solve) against 0."""
     sysm, p, rng = make(dim, n, seed=5, dt=1e-4)
     nv = sysm.mesh.nv
     u = dev(rng.uniform(-1.0, 1.0, nv))
     v = dev(rng.standard_normal(2 * nv))
     out = []
-    for fuse in (0, 1):
+    for fuse in (0, 1, 2):
         with ok.Grid(dim, n, **p, n_V=2, precision=precision, fuse_coarse=fuse) as g:
             z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
             g.apply_preconditioner(u, v, z)
             out.append(host(z))
-    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
 
 
 @pytest.mark.parametrize("n", [100, 160, 256])
