@@ -100,7 +100,7 @@ typedef struct ok_opts {
   int tile_fine;      /* 2D: register-strip tile kernels on the fine levels:
                          0 off, 1 automatic window width, 2 / 3 force 32 / 64
                          columns [1]                                            */
-  int use_pdl;        /* programmatic dependent launch between kernels [0]      */
+  int use_pdl;        /* programmatic dependent launch between kernels [1]      */
   int reorth;         /* Gram--Schmidt: 0 second pass only when the first one
                          cancels more than half of ||w||^2, 1 always two
                          passes (CGS2), 2 one classical pass [2]                */

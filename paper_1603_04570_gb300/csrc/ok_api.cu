@@ -600,11 +600,12 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
       t.inv_th = (T)(1.0 / P.thS);
       t.c1 = (T)P.cS1[0];
       t.c2 = (T)P.cS2[0];
-      // 64-column windows on levels of at least 512 vertices per side (less
-      // redundant halo work), 32-column windows below (more, shorter blocks);
-      // tile_fine = 2 or 3 forces 32 or 64 on every tiled level
+      // 64-column windows on levels of at least 1000 vertices per side (less
+      // redundant halo work), 32-column windows below (more, shorter blocks;
+      // measured faster from 513^2 down); tile_fine = 2 or 3 forces 32 or 64
+      // on every tiled level
       const int tf = G->o.tile_fine;
-      t.tile = tf == 2 ? 32 : (tf == 3 ? 64 : (t.g.n1 >= 512 ? 64 : 32));
+      t.tile = tf == 2 ? 32 : (tf == 3 ? 64 : (t.g.n1 >= 1000 ? 64 : 32));
     }
     TileMass<T>& m = P.tm;
     m.g = P.lv[0].g;
@@ -900,7 +901,7 @@ void ok_default_opts(ok_opts* o) {
   o->use_graphs = 1;
   o->fuse_coarse = 1;
   o->tile_fine = 1;
-  o->use_pdl = 0;
+  o->use_pdl = 1;
   o->reorth = 2;
   o->gmres_rtol = 1e-10;
   o->newton_atol = 1e-10;

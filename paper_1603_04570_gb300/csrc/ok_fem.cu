@@ -155,10 +155,11 @@ __global__ void __launch_bounds__(128) k_residual(Geom g, const double* __restri
                                                   const double* __restrict__ un, const double* __restrict__ wn,
                                                   const double* __restrict__ u, const double* __restrict__ w,
                                                   double* __restrict__ f) {
-  pdl_entry();
+  pdl_launch_dependents();
   using Tp = Topo<D>;
   __shared__ double sWM[Tp::NCLASS * Tp::NOFF], sWK[Tp::NCLASS * Tp::NOFF];
   stage_tables<D>(sWM, sWK, WM, WK);
+  pdl_wait();
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   double us[Tp::NOFF], g1[Tp::NOFF], g2[Tp::NAX], ws[Tp::NOFF];
@@ -332,10 +333,11 @@ __global__ void __launch_bounds__(128) k_apply_j(Geom g, const double* __restric
                                                  const double* __restrict__ WK, JCoefs jc,
                                                  const double* __restrict__ coef, const TZ* __restrict__ z,
                                                  double* __restrict__ y, const double* __restrict__ y0) {
-  pdl_entry();
+  pdl_launch_dependents();
   using Tp = Topo<D>;
   __shared__ double sWM[Tp::NCLASS * Tp::NOFF], sWK[Tp::NCLASS * Tp::NOFF];
   stage_tables<D>(sWM, sWK, WM, WK);
+  pdl_wait();
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   double z1[Tp::NOFF], z2[Tp::NOFF];

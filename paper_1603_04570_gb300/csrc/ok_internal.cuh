@@ -37,10 +37,17 @@ inline void count_launch() { g_launch_count.fetch_add(1, std::memory_order_relax
 // scheduled and then waits (in hardware) until the predecessor has completed
 // and its memory is visible.  Without the launch attribute both are no-ops.
 extern thread_local bool g_pdl;
-__device__ __forceinline__ void pdl_entry() {
+__device__ __forceinline__ void pdl_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_entry() {
+  pdl_launch_dependents();
+  pdl_wait();
+}
+// Kernels that read data fixed at setup (class tables, the coarse inverse)
+// call pdl_launch_dependents() first, issue those reads, and only then
+// pdl_wait() before touching what the previous kernel wrote.
 
 template <typename... KP, typename... A>
 inline void launch_k(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {

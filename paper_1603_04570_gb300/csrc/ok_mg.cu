@@ -334,14 +334,17 @@ constexpr int GEMV_WARPS = 8;
 template <typename T>
 __global__ void __launch_bounds__(GEMV_WARPS * 32) k_coarse_gemv(long long nc, long long ld, const T* __restrict__ A,
                                                                 const T* __restrict__ b, T* __restrict__ x) {
-  pdl_entry();
+  pdl_launch_dependents();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sb = reinterpret_cast<T*>(smraw);
+  const long long r = (long long)blockIdx.x * GEMV_WARPS + (threadIdx.x >> 5);
+  typename Vec16<T>::type a0[GEMV_NPL];               // first chunk of the row: A is fixed at setup
+  if (r < nc) gemv_load<T>(reinterpret_cast<const typename Vec16<T>::type*>(A + r * ld), ld / Vec16<T>::E, 0, a0);
+  pdl_wait();
   gemv_stage_b<T, false>(nc, ld, b, sb);
   __syncthreads();
-  const long long r = (long long)blockIdx.x * GEMV_WARPS + (threadIdx.x >> 5);
   if (r >= nc) return;
-  const T acc = gemv_row<T>(ld, A, sb, r);
+  const T acc = gemv_finish<T>(ld, A, sb, r, a0);
   if ((threadIdx.x & 31) == 0) x[r] = acc;
 }
 

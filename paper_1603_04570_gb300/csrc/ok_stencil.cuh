@@ -108,7 +108,7 @@ __device__ __forceinline__ void coarse_rows(long long nc, const T* A, const T* b
 // shared memory, zero-padded to whole chunks of 32 * GEMV_NPL vectors.  Lane l
 // takes the vectors l, l + 32, ... in order, so the sum is that of coarse_rows.
 // ---------------------------------------------------------------------------
-constexpr int GEMV_NPL = 8;          // 16-byte vectors per lane per chunk
+constexpr int GEMV_NPL = 9;          // 16-byte vectors per lane per chunk (a 1089-wide float row in one)
 template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int E = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int E = 2; };
@@ -144,45 +144,62 @@ __device__ __forceinline__ void gemv_stage_b(long long nc, long long ld, const T
   for (long long i = threadIdx.x; i < nb; i += blockDim.x) sb[i] = i < nc ? (CG ? __ldcg(b + i) : b[i]) : (T)0;
 }
 
-// row r of A times the staged b, by one warp (result in every lane)
+// 16-byte vectors [base, base + 32 GEMV_NPL) of row Ar for this lane (zero beyond nvec)
 template <typename T>
-__device__ __forceinline__ T gemv_row(long long ld, const T* __restrict__ A, const T* sb, long long r) {
+__device__ __forceinline__ void gemv_load(const typename Vec16<T>::type* Ar, long long nvec, long long base,
+                                          typename Vec16<T>::type (&a)[GEMV_NPL]) {
   using V = typename Vec16<T>::type;
-  constexpr int E = Vec16<T>::E;
   const int lane = threadIdx.x & 31;
-  const long long nvec = ld / E;
-  const long long chunk = 32LL * GEMV_NPL;
-  const V* Ar = reinterpret_cast<const V*>(A + r * ld);
-  const V* sv = reinterpret_cast<const V*>(sb);
-  T acc = (T)0;
-  auto mac = [&](const V (&a)[GEMV_NPL], long long base) {
-#pragma unroll
-    for (int k = 0; k < GEMV_NPL; ++k) {
-      const V bv = sv[base + lane + 32 * k];
-#pragma unroll
-      for (int e = 0; e < E; ++e) acc = fma(vec_at<T>(a[k], e), vec_at<T>(bv, e), acc);
-    }
-  };
-  long long base = 0;
-  for (; base + chunk <= nvec; base += chunk) {      // full chunks: all loads issued first
-    V a[GEMV_NPL];
+  if (base + 32LL * GEMV_NPL <= nvec) {               // full chunk: all loads issued first
 #pragma unroll
     for (int k = 0; k < GEMV_NPL; ++k) ld16(Ar + base + lane + 32 * k, a[k]);
-    mac(a, base);
-  }
-  if (base < nvec) {                                 // ragged last chunk
-    V a[GEMV_NPL];
+  } else {                                            // ragged last chunk
 #pragma unroll
     for (int k = 0; k < GEMV_NPL; ++k) {
       const long long c = base + lane + 32 * k;
       a[k] = V{};
       if (c < nvec) ld16(Ar + c, a[k]);
     }
-    mac(a, base);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void gemv_mac(const typename Vec16<T>::type (&a)[GEMV_NPL], const T* sb, long long base,
+                                         T& acc) {
+  using V = typename Vec16<T>::type;
+  constexpr int E = Vec16<T>::E;
+  const int lane = threadIdx.x & 31;
+  const V* sv = reinterpret_cast<const V*>(sb);
+#pragma unroll
+  for (int k = 0; k < GEMV_NPL; ++k) {
+    const V bv = sv[base + lane + 32 * k];
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc = fma(vec_at<T>(a[k], e), vec_at<T>(bv, e), acc);
+  }
+}
+// the chunks after the first (a0: the first, already loaded), then the warp sum
+template <typename T>
+__device__ __forceinline__ T gemv_finish(long long ld, const T* __restrict__ A, const T* sb, long long r,
+                                         const typename Vec16<T>::type (&a0)[GEMV_NPL]) {
+  using V = typename Vec16<T>::type;
+  const long long nvec = ld / Vec16<T>::E;
+  const V* Ar = reinterpret_cast<const V*>(A + r * ld);
+  T acc = (T)0;
+  gemv_mac<T>(a0, sb, 0, acc);
+  for (long long base = 32LL * GEMV_NPL; base < nvec; base += 32LL * GEMV_NPL) {
+    V a[GEMV_NPL];
+    gemv_load<T>(Ar, nvec, base, a);
+    gemv_mac<T>(a, sb, base, acc);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   return acc;
+}
+// row r of A times the staged b, by one warp (result in every lane)
+template <typename T>
+__device__ __forceinline__ T gemv_row(long long ld, const T* __restrict__ A, const T* sb, long long r) {
+  typename Vec16<T>::type a0[GEMV_NPL];
+  gemv_load<T>(reinterpret_cast<const typename Vec16<T>::type*>(A + r * ld), ld / Vec16<T>::E, 0, a0);
+  return gemv_finish<T>(ld, A, sb, r, a0);
 }
 
 // ---------------------------------------------------------------------------

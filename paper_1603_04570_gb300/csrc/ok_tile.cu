@@ -302,7 +302,7 @@ template <typename T, class G>
 __global__ void __launch_bounds__(G::NT) k_strip_pre(TileSmooth<T> a, const T* __restrict__ x_in,
                                                       const T* __restrict__ b, T* __restrict__ x_out,
                                                       T* __restrict__ bc) {
-  pdl_entry();
+  pdl_launch_dependents();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
   T* buf1 = buf0 + G::SB;
@@ -310,6 +310,7 @@ __global__ void __launch_bounds__(G::NT) k_strip_pre(TileSmooth<T> a, const T* _
   T* sD = sW + NTAB;
   load_table<T>(sW, a.W, NTAB, G::NT);
   load_table<T>(sD, a.dinv, Topo<2>::NCLASS, G::NT);
+  pdl_wait();                                      // tables are fixed at setup; the rest is not
   const Pos p = strip_pos<G>(a.g.n, blockIdx.x, blockIdx.y);
   if (strip_interior<G>(a.g.n, blockIdx.x, blockIdx.y))
     strip_pre_body<T, G, true>(a, p, buf0, buf1, sW, sD, x_in, b, x_out, bc);
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(G::NT) k_strip_post(TileSmooth<T> a, const T* 
                                                        const T* __restrict__ xc, const T* __restrict__ b,
                                                        T* __restrict__ x_out, T* __restrict__ mx_out,
                                                        TO* __restrict__ out, T oscale) {
-  pdl_entry();
+  pdl_launch_dependents();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
   T* buf1 = buf0 + G::SB;
@@ -427,6 +428,7 @@ __global__ void __launch_bounds__(G::NT) k_strip_post(TileSmooth<T> a, const T* 
   load_table<T>(sW, a.W, NTAB, G::NT);
   load_table<T>(sD, a.dinv, Topo<2>::NCLASS, G::NT);
   if (mx_out) load_table<T>(sM, a.WM, NTAB, G::NT);
+  pdl_wait();                                      // tables are fixed at setup; the rest is not
   const Pos p = strip_pos<G>(a.g.n, blockIdx.x, blockIdx.y);
   if (strip_interior<G>(a.g.n, blockIdx.x, blockIdx.y))
     strip_post_body<T, TO, G, true>(a, p, buf0, buf1, sW, sD, sM, x_in, xc, b, x_out, mx_out, out, oscale);
@@ -521,7 +523,7 @@ __device__ __forceinline__ void strip_amass_body(const TileMass<T>& a, const Pos
 template <typename T, typename TZ, class G>
 __global__ void __launch_bounds__(G::NT) k_strip_amass(TileMass<T> a, const double* __restrict__ v,
                                                         TZ* __restrict__ z1, T* __restrict__ t_out) {
-  pdl_entry();
+  pdl_launch_dependents();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
   T* buf1 = buf0 + G::SB;
@@ -529,6 +531,7 @@ __global__ void __launch_bounds__(G::NT) k_strip_amass(TileMass<T> a, const doub
   T* sD = sW + NTAB;
   load_table<T>(sW, a.WM, NTAB, G::NT);
   load_table<T>(sD, a.dinvM, Topo<2>::NCLASS, G::NT);
+  pdl_wait();                                      // tables are fixed at setup; the rest is not
   const Pos p = strip_pos<G>(a.g.n, blockIdx.x, blockIdx.y);
   if (strip_interior<G>(a.g.n, blockIdx.x, blockIdx.y))
     strip_amass_body<T, TZ, G, true>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
