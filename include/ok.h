@@ -64,8 +64,11 @@ enum ok_status {
 };
 
 enum ok_precision {
-  OK_FP64 = 0,    /* every step in float64                                      */
-  OK_MIXED = 1    /* preconditioner in float32 under float64 FGMRES, J, residual */
+  OK_FP64 = 0,       /* every step in float64                                      */
+  OK_MIXED = 1,      /* preconditioner in float32 under float64 FGMRES, J, residual */
+  OK_MIXED_HALF = 2  /* as OK_MIXED, the preconditioned vectors Z of the flexible
+                        basis stored in float16 (half the Z memory); J z_j and the
+                        update use the stored values, so FGMRES stays consistent */
 };
 
 /* Physical and time-stepping parameters of eqns oka/okb and the theta-method. */
@@ -88,7 +91,7 @@ typedef struct ok_opts {
   int k_R;            /* 1: S~^{-1}; 2: two Richardson steps on S [1]           */
   int smooth_pre;     /* Chebyshev--Jacobi pre-smoothing steps per level [2]    */
   int smooth_post;    /* post-smoothing steps per level [2]                     */
-  int precision;      /* OK_FP64 or OK_MIXED [OK_FP64]                          */
+  int precision;      /* OK_FP64, OK_MIXED or OK_MIXED_HALF [OK_FP64]           */
   int coarse_max;     /* halve the grid while n is even and > coarse_max [4]    */
   int use_graphs;     /* capture each Arnoldi step in a CUDA graph [1]          */
   int fuse_coarse;    /* coarse multigrid levels in one launch: 0 off; 1 the

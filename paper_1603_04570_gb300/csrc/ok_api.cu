@@ -401,6 +401,7 @@ struct ok_grid {
   double* V = nullptr;
   double* Zd = nullptr;
   float* Zf = nullptr;
+  __half* Zh = nullptr;
   KrylovState* ks = nullptr;
   RedScratch rs;
   double* dsc = nullptr;      // device scalars
@@ -664,7 +665,8 @@ void validate(int dim, int n, const ok_params* p, const ok_opts* o) {
       o->smooth_post > 16 || o->n_V > 32)
     fail(OK_ERR_INVALID_ARG, "q_A, n_V, smooth_pre, smooth_post must be >= 1 (and q_A <= 64, n_V <= 32, smoothing <= 16)");
   if (o->k_R != 1 && o->k_R != 2) fail(OK_ERR_INVALID_ARG, "k_R must be 1 or 2");
-  if (o->precision != OK_FP64 && o->precision != OK_MIXED) fail(OK_ERR_INVALID_ARG, "precision must be OK_FP64 or OK_MIXED");
+  if (o->precision != OK_FP64 && o->precision != OK_MIXED && o->precision != OK_MIXED_HALF)
+    fail(OK_ERR_INVALID_ARG, "precision must be OK_FP64, OK_MIXED or OK_MIXED_HALF");
   if (o->max_gmres < 1 || o->max_newton < 0 || o->newton_extra < 0) fail(OK_ERR_INVALID_ARG, "iteration caps");
   if (!(o->gmres_rtol > 0) || !(o->newton_atol >= 0) || !(o->newton_rtol >= 0))
     fail(OK_ERR_INVALID_ARG, "tolerances must be positive");
@@ -727,8 +729,12 @@ void assemble_c(ok_grid* G, const double* uk) {
 // z = P^{-1} v with the configured precision (z: 2 nv, Z-slot type)
 template <typename TZ>
 void precond(ok_grid* G, const double* v, TZ* z, cudaStream_t s) {
-  if (G->o.precision == OK_MIXED) G->pf.apply<TZ>(v, z, s);
-  else G->pd.apply<TZ>(v, z, s);
+  if constexpr (std::is_same<TZ, __half>::value) {
+    G->pf.apply<TZ>(v, z, s);                     // float16 Z: float32 preconditioner
+  } else {
+    if (G->o.precision != OK_FP64) G->pf.apply<TZ>(v, z, s);
+    else G->pd.apply<TZ>(v, z, s);
+  }
 }
 
 template <typename TZ>
@@ -842,6 +848,7 @@ void fgmres(ok_grid* G, TZ* Z, const double* f, double* x, int& its, double& rel
 
 void linear_solve(ok_grid* G, const double* f, double* x, int& its, double& rel) {
   if (G->o.precision == OK_MIXED) fgmres<float>(G, G->Zf, f, x, its, rel);
+  else if (G->o.precision == OK_MIXED_HALF) fgmres<__half>(G, G->Zh, f, x, its, rel);
   else fgmres<double>(G, G->Zd, f, x, its, rel);
 }
 
@@ -994,6 +1001,7 @@ int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid
     G->coef32 = A.alloc<float>(NSLOT * nv);
     G->V = A.alloc<double>((size_t)(od.restart + 1) * N);
     if (od.precision == OK_MIXED) G->Zf = A.alloc<float>((size_t)od.restart * N);
+    else if (od.precision == OK_MIXED_HALF) G->Zh = A.alloc<__half>((size_t)od.restart * N);
     else G->Zd = A.alloc<double>((size_t)od.restart * N);
     G->ks = (KrylovState*)A.alloc<char>(krylov_state_bytes());
     CK(cudaMemset(G->ks, 0, krylov_state_bytes()));
@@ -1005,7 +1013,7 @@ int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid
     void* hp = nullptr;
     CK(cudaMallocHost(&hp, 64));
     G->hpin = (double*)hp;
-    if (od.precision == OK_MIXED) {
+    if (od.precision != OK_FP64) {
       build_prec<float>(G, G->pf, sizes, refM, refK);
       G->pf.coef = G->coef32;
       G->pf.tm.coef = G->coef32;

@@ -320,6 +320,11 @@ __device__ __forceinline__ void load_nb_d(const TX* __restrict__ x, const Geom& 
       constexpr int o = decltype(O)::value;
       out[o] = nb_valid<D, o>(v.c) ? f2d_exact(x[v.idx + nb_delta<D, o>(g)]) : 0.0;
     });
+  } else if constexpr (std::is_same<TX, __half>::value) {   // half -> float (exact) -> double
+    static_for<0, Topo<D>::NOFF>([&](auto O) {
+      constexpr int o = decltype(O)::value;
+      out[o] = nb_valid<D, o>(v.c) ? f2d_exact(__half2float(x[v.idx + nb_delta<D, o>(g)])) : 0.0;
+    });
   } else {
     load_nb<D>(x, g, v, out);
   }
@@ -422,6 +427,8 @@ template void launch_apply_j<double>(int, const Geom&, const double*, const doub
                                      const double*, const double*, double*, const double*, cudaStream_t);
 template void launch_apply_j<float>(int, const Geom&, const double*, const double*, const JCoefs&,
                                     const double*, const float*, double*, const double*, cudaStream_t);
+template void launch_apply_j<__half>(int, const Geom&, const double*, const double*, const JCoefs&,
+                                     const double*, const __half*, double*, const double*, cudaStream_t);
 
 template <typename T, typename TV>
 void launch_cstep(int dim, const Geom& g, const T* coef, const TV* v2, T vscale, const T* y1, T yscale, T* t,

@@ -365,6 +365,7 @@ __global__ void __launch_bounds__(RT) k_multi_axpy(const TZ* __restrict__ Z, lon
     for (int k = 0; k < K; ++k) {
       double zk;
       if constexpr (std::is_same<TZ, float>::value) zk = f2d_exact(Z[k * ldz + e]);
+      else if constexpr (std::is_same<TZ, __half>::value) zk = f2d_exact(__half2float(Z[k * ldz + e]));
       else zk = Z[k * ldz + e];
       acc = fma(ys[k], zk, acc);
     }
@@ -378,8 +379,13 @@ __global__ void __launch_bounds__(RT) k_axpby(long long N, double a, const TX* _
   pdl_entry();
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
     double v = a * (double)x[e];
-    if (b != 0.0) v = fma(b, (double)y[e], v);
-    y[e] = (TY)v;
+    if constexpr (std::is_same<TY, __half>::value) {
+      if (b != 0.0) v = fma(b, (double)__half2float(y[e]), v);
+      y[e] = __float2half_rn((float)v);
+    } else {
+      if (b != 0.0) v = fma(b, (double)y[e], v);
+      y[e] = (TY)v;
+    }
   }
 }
 
@@ -479,6 +485,8 @@ template void launch_multi_axpy<double>(const double*, long long, int, const Kry
                                         cudaStream_t);
 template void launch_multi_axpy<float>(const float*, long long, int, const KrylovState*, double*, long long,
                                        cudaStream_t);
+template void launch_multi_axpy<__half>(const __half*, long long, int, const KrylovState*, double*, long long,
+                                        cudaStream_t);
 
 template <typename TX, typename TY>
 void launch_axpby(long long N, double a, const TX* x, double b, TY* y, cudaStream_t s) {
@@ -488,6 +496,7 @@ template void launch_axpby<double, double>(long long, double, const double*, dou
 template void launch_axpby<float, double>(long long, double, const float*, double, double*, cudaStream_t);
 template void launch_axpby<double, float>(long long, double, const double*, double, float*, cudaStream_t);
 template void launch_axpby<float, float>(long long, double, const float*, double, float*, cudaStream_t);
+template void launch_axpby<float, __half>(long long, double, const float*, double, __half*, cudaStream_t);
 
 void launch_check_finite(const double* x, long long N, int* flag, cudaStream_t s) {
   launch_k(k_check_finite, krylov_blocks(), RT, 0, s, x, N, flag);

@@ -32,43 +32,64 @@ static inline dim3 grid_of(int dim, const Geom& g) {
 // ---------------------------------------------------------------------------
 // one kernel per step
 // ---------------------------------------------------------------------------
+// The level's class tables (fixed at setup) are copied into shared memory
+// before the wait on the previous kernel; every vertex then reads its weights
+// there instead of from global memory.
+template <int D, typename T>
+__device__ __forceinline__ void stage_level(T* sW, T* sD, const T* __restrict__ W, const T* __restrict__ dinv) {
+  constexpr int NT = Topo<D>::NCLASS * Topo<D>::NOFF;
+  pdl_launch_dependents();
+  if (W)
+    for (int i = threadIdx.x; i < NT; i += blockDim.x) sW[i] = W[i];
+  if (dinv)
+    for (int i = threadIdx.x; i < Topo<D>::NCLASS; i += blockDim.x) sD[i] = dinv[i];
+  __syncthreads();
+  pdl_wait();
+}
+#define OK_LEVEL_SMEM(D, T)                                  \
+  __shared__ T sW[Topo<D>::NCLASS * Topo<D>::NOFF];          \
+  __shared__ T sD[Topo<D>::NCLASS]
 template <int D, typename T, typename TB>
 __global__ void __launch_bounds__(BX) k_cheb_init(Geom g, const T* __restrict__ dinv, const TB* __restrict__ b,
                                                   T bscale, T* __restrict__ r, T* __restrict__ d, T inv_th) {
-  pdl_entry();
+  OK_LEVEL_SMEM(D, T);
+  stage_level<D, T>(sW, sD, (const T*)nullptr, dinv);
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
-  cheb_init_at<D, T, TB>(v, dinv, b, bscale, r, d, inv_th);
+  cheb_init_at<D, T, TB>(v, sD, b, bscale, r, d, inv_th);
 }
 
 template <int D, typename T>
 __global__ void __launch_bounds__(BX) k_resid_init(Geom g, const T* __restrict__ W, const T* __restrict__ dinv,
                                                    const T* __restrict__ b, const T* __restrict__ x,
                                                    T* __restrict__ r, T* __restrict__ d, T inv_th) {
-  pdl_entry();
+  OK_LEVEL_SMEM(D, T);
+  stage_level<D, T>(sW, sD, W, dinv);
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
-  resid_init_at<D, T>(g, v, W, dinv, b, x, r, d, inv_th);
+  resid_init_at<D, T>(g, v, sW, sD, b, x, r, d, inv_th);
 }
 
 template <int D, typename T>
 __global__ void __launch_bounds__(BX) k_cheb_step(Geom g, const T* __restrict__ W, const T* __restrict__ dinv,
                                                   T* __restrict__ x, T* __restrict__ r, const T* __restrict__ din,
                                                   T* __restrict__ dout, T c1, T c2, int first) {
-  pdl_entry();
+  OK_LEVEL_SMEM(D, T);
+  stage_level<D, T>(sW, sD, W, dinv);
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
-  cheb_step_at<D, T>(g, v, W, dinv, x, r, din, dout, c1, c2, first != 0);
+  cheb_step_at<D, T>(g, v, sW, sD, x, r, din, dout, c1, c2, first != 0);
 }
 
 template <int D, typename T, typename TO>
 __global__ void __launch_bounds__(BX) k_cheb_last(Geom g, const T* __restrict__ W, T* __restrict__ x,
                                                   T* __restrict__ r, const T* __restrict__ din, int first,
                                                   TO* __restrict__ out, T oscale) {
-  pdl_entry();
+  OK_LEVEL_SMEM(D, T);
+  stage_level<D, T>(sW, sD, r ? W : (const T*)nullptr, (const T*)nullptr);
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
-  cheb_last_at<D, T, TO>(g, v, W, x, r, din, first != 0, out, oscale);
+  cheb_last_at<D, T, TO>(g, v, sW, x, r, din, first != 0, out, oscale);
 }
 
 template <int D, typename T>
@@ -264,13 +285,14 @@ template <int D, typename T, typename TX, typename TY>
 __global__ void __launch_bounds__(BX) k_op_apply(Geom g, const T* __restrict__ W, int axis_only,
                                                  const TX* __restrict__ x, TY* __restrict__ y, T alpha,
                                                  const TY* __restrict__ y0, T beta) {
-  pdl_entry();
   using Tp = Topo<D>;
+  OK_LEVEL_SMEM(D, T);
+  stage_level<D, T>(sW, sD, W, (const T*)nullptr);
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   T xs[Tp::NOFF];
   load_nb<D>(x, g, v, xs);
-  T acc = axis_only ? dot_w<D, Tp::NAX>(W, v.cls, xs) : dot_w<D, Tp::NOFF>(W, v.cls, xs);
+  T acc = axis_only ? dot_w<D, Tp::NAX>(sW, v.cls, xs) : dot_w<D, Tp::NOFF>(sW, v.cls, xs);
   acc *= alpha;
   if (y0) acc = fma(beta, (T)y0[v.idx], acc);
   y[v.idx] = (TY)acc;
@@ -474,6 +496,8 @@ template void launch_cheb_last<double, double>(int, const Geom&, const double*, 
                                                bool, double*, double, cudaStream_t);
 template void launch_cheb_last<float, float>(int, const Geom&, const float*, float*, float*, const float*, bool,
                                              float*, float, cudaStream_t);
+template void launch_cheb_last<float, __half>(int, const Geom&, const float*, float*, float*, const float*, bool,
+                                              __half*, float, cudaStream_t);
 template void launch_cheb_last<double, float>(int, const Geom&, const double*, double*, double*, const double*,
                                               bool, float*, double, cudaStream_t);
 template void launch_cheb_last<float, double>(int, const Geom&, const float*, float*, float*, const float*, bool,

@@ -725,6 +725,11 @@ cudaError_t prepare_tiles(int q) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, double, SQ>, attr, (int)strip_smem<SQ, T>(true));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, float, MA>, attr, (int)strip_smem<MA, T>(false));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, double, MA>, attr, (int)strip_smem<MA, T>(false));
+  if constexpr (std::is_same<T, float>::value) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, __half, BQ>, attr, (int)strip_smem<BQ, T>(true));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, __half, SQ>, attr, (int)strip_smem<SQ, T>(true));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, __half, MA>, attr, (int)strip_smem<MA, T>(false));
+  }
   return e;
 }
 
@@ -753,6 +758,10 @@ template void launch_tile_post<double, float>(const TileSmooth<double>&, const d
                                               const double*, double*, double*, float*, double, cudaStream_t);
 template void launch_tile_amass<float, double>(const TileMass<float>&, const double*, double*, float*, cudaStream_t);
 template void launch_tile_amass<double, float>(const TileMass<double>&, const double*, float*, double*,
+                                               cudaStream_t);
+template void launch_tile_post<float, __half>(const TileSmooth<float>&, const float*, const float*, const float*,
+                                              float*, float*, __half*, float, cudaStream_t);
+template void launch_tile_amass<float, __half>(const TileMass<float>&, const double*, __half*, float*,
                                                cudaStream_t);
 
 }  // namespace okg

@@ -136,7 +136,7 @@ def test_init_w_parity(dim, n):
         assert rel2(host(w0), ref) < 1e-12
 
 
-@pytest.mark.parametrize("precision,tol", [(ok.OK_FP64, 1e-10), (ok.OK_MIXED, 1e-8)])
+@pytest.mark.parametrize("precision,tol", [(ok.OK_FP64, 1e-10), (ok.OK_MIXED, 1e-8), (ok.OK_MIXED_HALF, 1e-8)])
 def test_timesteps_small_2d(precision, tol):
     """The 2D 32x32 workload (eps 0.04, sigma 100, m 0, theta 1, dt 1e-4): 5 steps."""
     wl = oi.SMALL_2D
@@ -157,7 +157,7 @@ def test_timesteps_small_2d(precision, tol):
             assert rel2(host(w), wr) < tol, step
 
 
-@pytest.mark.parametrize("precision,tol", [(ok.OK_FP64, 1e-10), (ok.OK_MIXED, 1e-8)])
+@pytest.mark.parametrize("precision,tol", [(ok.OK_FP64, 1e-10), (ok.OK_MIXED, 1e-8), (ok.OK_MIXED_HALF, 1e-8)])
 def test_timesteps_small_3d(precision, tol):
     """The 3D Kuhn workload's parameters (eps 0.03, sigma 100, m -0.2, theta 1) on 8^3."""
     wl = oi.scaled(oi.CUBE_128, 8, dt=5e-4)
