@@ -74,7 +74,8 @@ class Workload:
     theta: float
     dt: float
     steps: int          # timesteps of the full run
-    noise: str          # "uniform": m + a*U(-1,1); "normal": m + a*N(0,1)
+    noise: str          # "uniform": m + a*U(-1,1); "normal": m + a*N(0,1);
+                        # "cos": m + a*prod_k cos(2 pi x_k) (the paper's Sec. 4 start, a = 1/50)
     amp: float
     seed: int
     restart: int        # (F)GMRES restart length
@@ -110,6 +111,9 @@ def initial_u(w: Workload) -> np.ndarray:
         return w.m + w.amp * uniform(w.seed, nv, -1.0, 1.0)
     if w.noise == "normal":
         return w.m + w.amp * normal(w.seed, nv)
+    if w.noise == "cos":
+        x = nodal_coords(w.dim, w.n)
+        return w.m + w.amp * np.prod(np.cos(2.0 * np.pi * x), axis=1)
     raise ValueError(w.noise)
 
 
@@ -135,6 +139,13 @@ CUBE_512 = Workload("3d_n512", 3, 512, 0.01, 1000.0, 0.0, 0.5, 1e-5, 3,
                     "normal", 0.01, 3, 20, 1e-8, 1e-10)
 
 WORKLOADS = {w.name: w for w in (SMALL_2D, LARGE_2D, CUBE_128, CUBE_512)}
+
+# The paper's own experiment (Sec. 4): unit cube, m = 0.4, eps = 0.02,
+# sigma = 100, theta = 0.5, dt = eps^2, u0 = m + cos(2 pi x) cos(2 pi y) cos(2 pi z) / 50.
+# The paper's meshes have 50..800 cells per side; the geometric hierarchy here
+# wants n divisible by powers of two, so the stand-in sizes are 32..256.
+PAPER_3D = Workload("paper_3d", 3, 64, 0.02, 100.0, 0.4, 0.5, 4e-4, 300,
+                    "cos", 1.0 / 50.0, 0, 30, 1e-8, 1e-10)
 
 
 def scaled(w: Workload, n: int, **kw) -> Workload:

@@ -1,0 +1,112 @@
+"""Iteration counts of the paper's Sec. 4 experiments on this solver.
+
+Sec. 4 reports the average number of outer Krylov iterations per Newton step
+(Table 1: the mesh refined at fixed parameters; Table 2: eps -> 0 with
+dx = eps / 2 and dt = eps^2).  Flat counts are the preconditioner's claim.
+This module runs the same experiments through the library:
+
+    python -m paper_1603_04570_gb300.experiments table1 [--sizes 32 64 128 256] [--steps 3]
+    python -m paper_1603_04570_gb300.experiments table2 [--steps 3]
+    python -m paper_1603_04570_gb300.experiments refine2d [--sizes 128 256 512 1024] [--steps 2]
+
+Paper setting (Table 1): unit cube, m = 0.4, eps = 0.02, sigma = 100,
+theta = 0.5, dt = eps^2, u0 = m + cos(2 pi x) cos(2 pi y) cos(2 pi z) / 50,
+ten Chebyshev steps for A~^{-1}, two Richardson steps of S~^{-1} (k_R = 2),
+five V-cycles per S_hat^{-1}.  The paper does not state its Krylov and Newton
+tolerances; its solver (FEniCS over PETSc) defaults to a relative Krylov
+tolerance of 1e-5 and a relative Newton tolerance of 1e-8, which these runs
+use unless --gmres-rtol is given.  Meshes: n must be divisible by a power of
+two for the geometric hierarchy, so the sizes stand in for the paper's
+50..800 cells per side.  Each line printed is a JSON record; --markdown
+prints a table.
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+import time
+
+import ok_inputs as oi
+
+from . import OK_FP64, OK_MIXED, Grid
+
+
+def run(wl: oi.Workload, steps: int, k_R: int = 2, precision: int = OK_MIXED, gmres_rtol: float = 1e-5,
+        newton_rtol: float = 1e-8, **opts) -> dict:
+    """`steps` timesteps of workload `wl`; FGMRES and Newton counts."""
+    import torch
+    o = dict(restart=wl.restart, gmres_rtol=gmres_rtol, newton_atol=1e-300, newton_rtol=newton_rtol,
+             precision=precision, k_R=k_R, q_A=10, n_V=5)
+    o.update(opts)
+    with Grid(wl.dim, wl.n, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, **o) as g:
+        u = torch.from_numpy(oi.initial_u(wl)).cuda()
+        w = torch.empty_like(u)
+        g.init_w(u, w)
+        torch.cuda.synchronize()
+        its = newton = 0
+        per_step = []
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            info = g.timestep(u, w)
+            its += info.gmres_its
+            newton += info.newton_its
+            per_step.append(info.gmres_its / max(info.newton_its, 1))
+        torch.cuda.synchronize()
+        seconds = time.perf_counter() - t0
+    return dict(workload=wl.name, dim=wl.dim, n=wl.n, dofs=wl.dofs, eps=wl.eps, dt=wl.dt, steps=steps,
+                k_R=k_R, precision="fp64" if precision == OK_FP64 else "mixed", gmres_rtol=gmres_rtol,
+                newton_steps=newton, gmres_its=its, its_per_newton=its / max(newton, 1),
+                its_per_newton_by_step=per_step, seconds=seconds)
+
+
+def table1(sizes, steps, k_R, **kw):
+    for n in sizes:
+        yield run(oi.scaled(oi.PAPER_3D, n), steps, k_R, **kw)
+
+
+def table2(steps, k_R, ns=(64, 128, 256), **kw):
+    # dx = eps / 2: eps = 2 / n, dt = eps^2
+    for n in ns:
+        eps = 2.0 / n
+        yield run(oi.scaled(oi.PAPER_3D, n, eps=eps, dt=eps * eps), steps, k_R, **kw)
+
+
+def refine2d(sizes, steps, k_R, **kw):
+    for n in sizes:
+        wl = dataclasses.replace(oi.scaled(oi.LARGE_2D, n))
+        yield run(wl, steps, k_R, coarse_max=32 if n >= 128 else 4, **kw)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("experiment", choices=["table1", "table2", "refine2d"])
+    ap.add_argument("--sizes", type=int, nargs="*", default=None)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--k-r", type=int, default=None, help="1: S~^{-1}; 2: two Richardson steps (paper)")
+    ap.add_argument("--gmres-rtol", type=float, default=1e-5)
+    ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--markdown", action="store_true")
+    a = ap.parse_args(argv)
+    prec = OK_FP64 if a.fp64 else OK_MIXED
+    if a.experiment == "table1":
+        rows = table1(a.sizes or [32, 64, 128, 256], a.steps, a.k_r or 2, precision=prec, gmres_rtol=a.gmres_rtol)
+    elif a.experiment == "table2":
+        rows = table2(a.steps, a.k_r or 2, precision=prec, gmres_rtol=a.gmres_rtol)
+    else:
+        rows = refine2d(a.sizes or [128, 256, 512, 1024], a.steps, a.k_r or 1, precision=prec,
+                        gmres_rtol=a.gmres_rtol)
+    out = []
+    for r in rows:
+        out.append(r)
+        print(json.dumps(r), flush=True)
+    if a.markdown:
+        print("\n| n | DoF | eps | dt | k_R | rtol | Newton steps | FGMRES its | its / Newton |")
+        print("|---|---|---|---|---|---|---|---|---|")
+        for r in out:
+            print(f"| {r['n']} | {r['dofs']:,} | {r['eps']:.4g} | {r['dt']:.3g} | {r['k_R']} | {r['gmres_rtol']:g} | "
+                  f"{r['newton_steps']} | {r['gmres_its']} | {r['its_per_newton']:.2f} |")
+
+
+if __name__ == "__main__":
+    main()

@@ -383,3 +383,13 @@ def test_programmatic_dependent_launch_is_bitwise_identical(dim, n, graphs):
             g.timestep(u, w)
             out.append((host(u), host(w)))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_experiments_module_runs():
+    """The Sec. 4 experiment driver: two small refinements of the paper's 3D
+    setting (k_R = 2), one timestep each, converge with a bounded count."""
+    from paper_1603_04570_gb300 import experiments
+    rows = list(experiments.table1([8, 16], steps=1, k_R=2))
+    assert [r["n"] for r in rows] == [8, 16]
+    for r in rows:
+        assert r["newton_steps"] >= 1 and 1 <= r["its_per_newton"] <= 30
