@@ -208,6 +208,42 @@ typedef struct ok_batch_info {
  * independent; each gets its own stream, derived from `stream`'s device. */
 int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream stream);
 
+/* Serving (no counterpart in the paper): whole simulations admitted
+ * continuously.  Requests are taken in order of `arrival` (seconds after the
+ * call starts); one is admitted when it has arrived, fewer than
+ * `max_inflight` are in flight and its estimated device footprint (Krylov
+ * basis dominant) fits in `mem_budget` bytes beside those in flight.  Each
+ * admitted request runs on its own host thread and non-blocking stream:
+ * ok_grid_create, ok_init_w when init_w != 0, `steps` ok_timestep calls,
+ * ok_grid_destroy, so the work of requests in flight overlaps on the device.
+ * A request's arithmetic does not depend on what else runs: its results are
+ * bitwise those it gets alone.  Returns the status of the first failed
+ * request (all requests run regardless); OK_ERR_NOMEM marks a request whose
+ * footprint exceeds the whole budget. */
+typedef struct ok_serve_request {
+  int dim, n;               /* in: grid                                              */
+  ok_params params;         /* in                                                    */
+  const ok_opts* opts;      /* in: NULL for the defaults                             */
+  double* u;                /* in-out: N_v, host or device                           */
+  double* w;                /* in-out: N_v; computed from u first when init_w != 0   */
+  int init_w;               /* in                                                    */
+  int steps;                /* in: timesteps                                         */
+  double arrival;           /* in: seconds after the call starts                     */
+  int status;               /* out: OK_*                                             */
+  int newton_its, gmres_its;/* out: summed over the steps                            */
+  double t_admit, t_done;   /* out: seconds after the call starts                    */
+  long long device_bytes;   /* out: footprint charged at admission (estimate)        */
+} ok_serve_request;
+
+typedef struct ok_serve_info {
+  int completed, failed;
+  int peak_inflight;        /* most requests in flight at once                       */
+  long long peak_bytes;     /* most estimated bytes in flight at once                */
+  double seconds;           /* wall time of the call                                 */
+} ok_serve_info;
+
+int ok_serve(ok_serve_request* reqs, int count, int max_inflight, long long mem_budget, ok_serve_info* info);
+
 /* Sampled kernel timing (no counterpart in the paper: measurement support).
  * ok_profile(g, 1) clears the counters and, from the next Arnoldi step on,
  * records one CUDA-event pair per kernel class per step on the handle's

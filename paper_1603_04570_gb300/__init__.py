@@ -54,6 +54,18 @@ class BatchInfo(Structure):
     _fields_ = [("completed", c_int), ("failed", c_int), ("seconds", c_double)]
 
 
+class ServeRequest(Structure):
+    _fields_ = [("dim", c_int), ("n", c_int), ("params", Params), ("opts", POINTER(Opts)), ("u", c_void_p),
+                ("w", c_void_p), ("init_w", c_int), ("steps", c_int), ("arrival", c_double), ("status", c_int),
+                ("newton_its", c_int), ("gmres_its", c_int), ("t_admit", c_double), ("t_done", c_double),
+                ("device_bytes", c_longlong)]
+
+
+class ServeInfo(Structure):
+    _fields_ = [("completed", c_int), ("failed", c_int), ("peak_inflight", c_int), ("peak_bytes", c_longlong),
+                ("seconds", c_double)]
+
+
 class KernelStat(Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("samples", c_longlong), ("total_ms", c_double)]
 
@@ -96,6 +108,7 @@ def load(build: bool = True):
         "ok_newton_step": (c_int, [P, P, P, P, P, POINTER(StepInfo), P]),
         "ok_timestep": (c_int, [P, P, P, POINTER(StepInfo), P]),
         "ok_solve_batch": (c_int, [POINTER(Request), c_int, POINTER(BatchInfo), P]),
+        "ok_serve": (c_int, [POINTER(ServeRequest), c_int, c_int, c_longlong, POINTER(ServeInfo)]),
         "ok_profile": (c_int, [P, c_int]),
         "ok_profile_read": (c_int, [P, POINTER(KernelStat), c_int, POINTER(c_int)]),
         "ok_launch_count": (c_longlong, []),
@@ -259,6 +272,31 @@ def ok_solve_batch(requests, stream=None):
     out = BatchInfo()
     st = load().ok_solve_batch(arr, len(requests), byref(out), _stream(stream, *(r[1] for r in requests)))
     return st, [arr[i] for i in range(len(requests))], out
+
+
+def ok_serve(requests, max_inflight, mem_budget):
+    """requests: list of dicts with dim, n, eps, sigma, m, theta, dt, u, w, steps,
+    and optionally arrival (s), init_w (bool), opts (dict of ok_opts fields).
+    u and w are updated in place.  Returns (status, [ServeRequest], ServeInfo)."""
+    arr = (ServeRequest * len(requests))()
+    keep = []
+    for i, r in enumerate(requests):
+        nv = (r["n"] + 1) ** r["dim"]
+        q = arr[i]
+        q.dim, q.n = r["dim"], r["n"]
+        q.params = Params(r["eps"], r["sigma"], r["m"], r["theta"], r["dt"])
+        if r.get("opts"):
+            o = ok_default_opts(**r["opts"])
+            keep.append(o)
+            q.opts = ctypes.pointer(o)
+        q.u = _ptr(r["u"], nv, "u")
+        q.w = _ptr(r["w"], nv, "w")
+        q.init_w = 1 if r.get("init_w") else 0
+        q.steps = r["steps"]
+        q.arrival = float(r.get("arrival", 0.0))
+    info = ServeInfo()
+    st = load().ok_serve(arr, len(requests), max_inflight, int(mem_budget), byref(info))
+    return st, [arr[i] for i in range(len(requests))], info
 
 
 class Grid:

@@ -9,6 +9,9 @@
 #include <array>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -514,7 +517,7 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
                       cudaMemcpyDeviceToDevice));
       CK(prepare_coarse_gemv<T>(nc));
     }
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(0));      // setup work of this handle (legacy stream); other handles keep running
   }
   // fused coarse part: the longest suffix of levels whose five vectors fit in
   // shared memory (at most COARSE_MAXLEV levels); worth it from two levels on
@@ -1028,7 +1031,7 @@ int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid
     G->pd.prof = &G->prof;
     G->pf.prof = &G->prof;
     krylov_blocks();
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(0));      // setup work of this handle (legacy stream); other handles keep running
   });
   if (st != OK_SUCCESS) {
     if (G) ok_grid_destroy(G);
@@ -1334,6 +1337,122 @@ int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream st
     out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   if (failed == 0) return OK_SUCCESS;
+  for (int i = 0; i < count; ++i)
+    if (reqs[i].status != OK_SUCCESS) {
+      g_last_error = "request " + std::to_string(i) + " failed with status " + std::to_string(reqs[i].status);
+      return reqs[i].status;
+    }
+  return OK_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// serving: continuous admission of whole simulations
+// ---------------------------------------------------------------------------
+// Device bytes a handle of (dim, n, o) allocates, from the same sizes
+// ok_grid_create uses (an upper estimate for admission; the multigrid
+// vectors and the coarse inverse are bounded from above).
+static long long serve_estimate(int dim, int n, const ok_opts& o) {
+  const double nv = std::pow((double)(n + 1), dim);
+  const double N = 2.0 * nv;
+  const int nslot = dim == 2 ? 4 : 8;
+  const double zb = o.precision == OK_FP64 ? 8.0 : (o.precision == OK_MIXED ? 4.0 : 2.0);
+  const double tb = o.precision == OK_FP64 ? 8.0 : 4.0;
+  double b = 8.0 * N * (o.restart + 1) + zb * N * o.restart;   // V, Z
+  b += nslot * nv * 12.0;                                     // C store, float64 + float32
+  b += 12.0 * nv * 8.0;                                       // state and work vectors
+  b += 9.0 * nv * tb * (dim == 2 ? 4.0 / 3.0 : 8.0 / 7.0);  // multigrid vectors over the levels
+  const double nc = std::min(std::pow((double)(o.coarse_max + 2), dim), 4913.0);
+  b += nc * nc * (8.0 + 2.0 * tb) + (1 << 20);                // coarse inverse (+ padded copy), scalars
+  return (long long)b;
+}
+
+extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, long long mem_budget,
+                        ok_serve_info* info) {
+  if (count < 0 || (count > 0 && !reqs) || max_inflight < 1 || mem_budget <= 0) {
+    g_last_error = "invalid serving arguments";
+    return OK_ERR_INVALID_ARG;
+  }
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    g_last_error = "no CUDA device";
+    return OK_ERR_CUDA;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  auto now = [&] { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return reqs[a].arrival < reqs[b].arrival; });
+  std::mutex mu;
+  std::condition_variable cv;
+  int inflight = 0, peak_inflight = 0;
+  long long bytes = 0, peak_bytes = 0;
+  std::vector<std::thread> workers;
+  workers.reserve(count);
+  for (int i : order) {
+    ok_serve_request& r = reqs[i];
+    r.status = OK_SUCCESS;
+    r.newton_its = r.gmres_its = 0;
+    r.t_admit = r.t_done = 0.0;
+    ok_opts o;
+    ok_default_opts(&o);
+    if (r.opts) o = *r.opts;
+    r.device_bytes = serve_estimate(r.dim, r.n, o);
+    if (!r.u || !r.w || r.steps < 0 || r.dim < 2 || r.dim > 3 || r.n < 2) {
+      r.status = OK_ERR_INVALID_ARG;
+      continue;
+    }
+    if (r.device_bytes > mem_budget) {
+      r.status = OK_ERR_NOMEM;
+      continue;
+    }
+    const double wait = r.arrival - now();
+    if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(wait));
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv.wait(lk, [&] { return inflight < max_inflight && bytes + r.device_bytes <= mem_budget; });
+      ++inflight;
+      bytes += r.device_bytes;
+      peak_inflight = std::max(peak_inflight, inflight);
+      peak_bytes = std::max(peak_bytes, bytes);
+    }
+    r.t_admit = now();
+    workers.emplace_back([&, i, o] {
+      ok_serve_request& q = reqs[i];
+      cudaSetDevice(device);
+      cudaStream_t st = nullptr;
+      ok_grid* g = nullptr;
+      int status = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? OK_SUCCESS : OK_ERR_CUDA;
+      if (status == OK_SUCCESS) status = ok_grid_create(q.dim, q.n, &q.params, &o, &g);
+      if (status == OK_SUCCESS && q.init_w) status = ok_init_w(g, q.u, q.w, (ok_stream)st);
+      for (int k = 0; status == OK_SUCCESS && k < q.steps; ++k) {
+        ok_step_info si;
+        status = ok_timestep(g, q.u, q.w, &si, (ok_stream)st);
+        q.newton_its += si.newton_its;
+        q.gmres_its += si.gmres_its;
+      }
+      if (g) ok_grid_destroy(g);
+      if (st) cudaStreamDestroy(st);
+      q.status = status;
+      q.t_done = now();
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        --inflight;
+        bytes -= q.device_bytes;
+      }
+      cv.notify_all();
+    });
+  }
+  for (auto& t : workers) t.join();
+  int done = 0, failed = 0;
+  for (int i = 0; i < count; ++i) (reqs[i].status == OK_SUCCESS ? done : failed) += 1;
+  if (info) {
+    info->completed = done;
+    info->failed = failed;
+    info->peak_inflight = peak_inflight;
+    info->peak_bytes = peak_bytes;
+    info->seconds = now();
+  }
   for (int i = 0; i < count; ++i)
     if (reqs[i].status != OK_SUCCESS) {
       g_last_error = "request " + std::to_string(i) + " failed with status " + std::to_string(reqs[i].status);

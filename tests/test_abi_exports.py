@@ -75,3 +75,14 @@ def test_too_large_coarse_level_rejected():
     with pytest.raises(ok.OkError) as e:
         ok.ok_grid_create(3, 17, ok.Params(0.04, 100, 0, 1, 1e-4))    # 18^3 coarse unknowns
     assert e.value.status == ok.OK_ERR_INVALID_ARG and "coarsest" in str(e.value)
+
+
+def test_serving_structs_match_the_header():
+    assert ctypes.sizeof(ok.ServeRequest) == 128 and ok.ServeRequest.arrival.offset == 80
+    assert ok.ServeRequest.device_bytes.offset == 120
+    assert ctypes.sizeof(ok.ServeInfo) == 32 and ok.ServeInfo.seconds.offset == 24
+
+
+def test_serve_rejects_invalid_arguments_on_host():
+    st, _, _ = ok.ok_serve([], max_inflight=0, mem_budget=1 << 30)
+    assert st == ok.OK_ERR_INVALID_ARG

@@ -393,3 +393,57 @@ def test_experiments_module_runs():
     assert [r["n"] for r in rows] == [8, 16]
     for r in rows:
         assert r["newton_steps"] >= 1 and 1 <= r["its_per_newton"] <= 30
+
+
+
+def _serve_mix(seed=11):
+    """A small request mix: 2D and 3D grids, different parameters and lengths."""
+    specs = [(2, 24, 0.04, 100.0, 0.0, 1.0, 1e-4, 3), (3, 6, 0.05, 50.0, 0.1, 0.5, 2e-4, 2),
+             (2, 32, 0.03, 300.0, -0.1, 0.5, 5e-5, 2), (3, 8, 0.03, 100.0, -0.2, 1.0, 1e-4, 3),
+             (2, 48, 0.02, 200.0, 0.1, 0.5, 2e-5, 2), (3, 10, 0.04, 10.0, 0.2, 1.0, 3e-4, 2)]
+    rng = np.random.default_rng(seed)
+    out = []
+    for k, (dim, n, eps, sigma, m, theta, dt, steps) in enumerate(specs):
+        nv = (n + 1) ** dim
+        u0 = m + 0.01 * rng.uniform(-1.0, 1.0, nv)
+        out.append(dict(dim=dim, n=n, eps=eps, sigma=sigma, m=m, theta=theta, dt=dt, steps=steps, init_w=True,
+                        arrival=0.002 * k, u0=u0, opts=dict(precision=ok.OK_MIXED if k % 2 else ok.OK_FP64)))
+    return out
+
+
+def _serve(mix, max_inflight, budget):
+    reqs = []
+    for r in mix:
+        q = dict(r)
+        q["u"] = dev(r["u0"])
+        q["w"] = torch.zeros_like(q["u"])
+        reqs.append(q)
+    st, res, info = ok.ok_serve(reqs, max_inflight, budget)
+    assert st == ok.OK_SUCCESS, ok.load().ok_last_error()
+    return [(host(q["u"]), host(q["w"])) for q in reqs], res, info
+
+
+def test_serving_results_are_the_same_alone_and_in_the_mix():
+    """Continuous admission: every request's u and w are bitwise those it gets
+    alone, while several requests are in flight on the device at once."""
+    mix = _serve_mix()
+    alone = [_serve([r], 1, 1 << 34)[0][0] for r in mix]
+    mixed, res, info = _serve(mix, 4, 1 << 34)
+    assert info.completed == len(mix) and info.failed == 0 and info.peak_inflight >= 2
+    for k, ((ua, wa), (um, wm)) in enumerate(zip(alone, mixed)):
+        assert np.array_equal(ua, um) and np.array_equal(wa, wm), k
+    for r in res:
+        assert r.status == 0 and r.newton_its >= r.steps and r.t_done >= r.t_admit >= 0.0
+
+
+def test_serving_admits_by_memory_budget():
+    """Three requests of one footprint under a budget of one footprint run one
+    at a time; all finish; a request larger than the budget is refused."""
+    base = _serve_mix()[0]
+    mix = [dict(base, u0=base["u0"] + 0.001 * k, arrival=0.0) for k in range(3)]
+    footprint = _serve(mix[:1], 1, 1 << 34)[1][0].device_bytes
+    _, res, info = _serve(mix, 4, footprint + 1)
+    assert info.completed == 3 and info.peak_inflight == 1
+    reqs = [dict(mix[0], u=dev(mix[0]["u0"]), w=torch.zeros(len(mix[0]["u0"]), dtype=torch.float64, device="cuda"))]
+    st, res, info = ok.ok_serve(reqs, 1, footprint // 2)
+    assert st == ok.OK_ERR_NOMEM and res[0].status == ok.OK_ERR_NOMEM and info.failed == 1
