@@ -56,6 +56,12 @@ def parse():
     ap.add_argument("--profile-out", default=None, help="write per-kernel samples as JSON")
     ap.add_argument("--opt", action="append", default=[], metavar="KEY=INT",
                     help="override an integer ok_opts field of the timed runs (e.g. use_pdl=0)")
+    ap.add_argument("--serving", action="store_true",
+                    help="instead of the timed workload: the serving stream (Poisson arrivals) through ok_serve")
+    ap.add_argument("--requests", type=int, default=256, help="serving: requests of the stream")
+    ap.add_argument("--max-inflight", type=int, default=8, help="serving: requests in flight at once")
+    ap.add_argument("--budget-gb", type=float, default=200.0, help="serving: device memory budget")
+    ap.add_argument("--serving-fp64", action="store_true", help="serving: float64 instead of mixed precision")
     return ap.parse_args()
 
 
@@ -456,9 +462,54 @@ def main_reference(args):
     }))
 
 
+def main_serving(args):
+    """The serving stream: whole simulations with Poisson arrivals, admitted by
+    ok_serve; latency = completion - arrival per request."""
+    import torch
+    import paper_1603_04570_gb300 as ok
+    ok.load()
+    prec = ok.OK_FP64 if args.serving_fp64 else ok.OK_MIXED
+    stream = oi.serving_requests(args.requests)
+    reqs = []
+    for arrival, wl in stream:
+        atol, rtol = wl.newton_tols
+        u = torch.from_numpy(oi.initial_u(wl)).cuda()
+        reqs.append(dict(dim=wl.dim, n=wl.n, eps=wl.eps, sigma=wl.sigma, m=wl.m, theta=wl.theta, dt=wl.dt,
+                         u=u, w=torch.zeros_like(u), steps=wl.steps, init_w=True, arrival=arrival,
+                         opts=dict(precision=prec, restart=wl.restart, gmres_rtol=wl.gmres_rtol,
+                                   newton_atol=atol, newton_rtol=rtol,
+                                   coarse_max=32 if (wl.dim == 2 and wl.n >= 128) else 4)))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    st, res, info = ok.ok_serve(reqs, args.max_inflight, int(args.budget_gb * (1 << 30)))
+    clk = clocks.stop()
+    lat = [r.t_done - a for r, (a, _) in zip(res, stream)]
+    wait = [r.t_admit - a for r, (a, _) in zip(res, stream)]
+    units = sum(2 * wl.n_vertices * r.gmres_its for r, (_, wl) in zip(res, stream))
+    out = {
+        "metric": "serving latency p50/p99 (completion - arrival) of whole simulations", "impl": "ok",
+        "value": pct(lat, 0.99) * 1e3, "unit": "ms (p99)", "higher_is_better": False, "n_gpus": 1,
+        "p50_ms": pct(lat, 0.5) * 1e3, "p99_ms": pct(lat, 0.99) * 1e3,
+        "admission_wait_p50_ms": pct(wait, 0.5) * 1e3, "admission_wait_p99_ms": pct(wait, 0.99) * 1e3,
+        "requests": len(stream), "completed": info.completed, "failed": info.failed, "status": st,
+        "seconds": info.seconds, "throughput_req_s": info.completed / info.seconds,
+        "dof_iter_per_s": units / info.seconds, "peak_inflight": info.peak_inflight,
+        "errors": sorted({r.message.decode() for r in res if r.status != 0}),
+        "peak_estimated_gb": info.peak_bytes / 2 ** 30, "precision": "fp64" if args.serving_fp64 else "mixed",
+        "config": {"workload": "serving stream: Poisson arrivals at 40 req/s; 2D {64..512}^2 and 3D {32..96}^3, "
+                               "5-50 timesteps each", "max_inflight": args.max_inflight,
+                   "budget_gb": args.budget_gb},
+        "data": "synthetic", "clocks": clk,
+    }
+    print(json.dumps(out))
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.serving:
+        main_serving(a)
+    elif a.impl == "reference":
         main_reference(a)
     else:
         main_ok(a)

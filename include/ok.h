@@ -233,6 +233,7 @@ typedef struct ok_serve_request {
   int newton_its, gmres_its;/* out: summed over the steps                            */
   double t_admit, t_done;   /* out: seconds after the call starts                    */
   long long device_bytes;   /* out: footprint charged at admission (estimate)        */
+  char message[96];         /* out: ok_last_error() of a failed request, else ""     */
 } ok_serve_request;
 
 typedef struct ok_serve_info {

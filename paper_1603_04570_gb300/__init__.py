@@ -58,7 +58,7 @@ class ServeRequest(Structure):
     _fields_ = [("dim", c_int), ("n", c_int), ("params", Params), ("opts", POINTER(Opts)), ("u", c_void_p),
                 ("w", c_void_p), ("init_w", c_int), ("steps", c_int), ("arrival", c_double), ("status", c_int),
                 ("newton_its", c_int), ("gmres_its", c_int), ("t_admit", c_double), ("t_done", c_double),
-                ("device_bytes", c_longlong)]
+                ("device_bytes", c_longlong), ("message", ctypes.c_char * 96)]
 
 
 class ServeInfo(Structure):

@@ -522,7 +522,7 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
   // fused coarse part: the longest suffix of levels whose five vectors fit in
   // shared memory (at most COARSE_MAXLEV levels); worth it from two levels on
   const int nl = (int)P.lv.size();
-  const size_t budget = 200 * 1024;
+  const size_t budget = COARSE_SMEM_MAX;
   // 2D tile kernels need two smoothing steps, the S~^{-1} form and the
   // ten-step mass solve they are compiled for (the paper's ten Chebyshev steps)
   const bool tiles_ok =
@@ -801,22 +801,39 @@ void fgmres(ok_grid* G, TZ* Z, const double* f, double* x, int& its, double& rel
     int jused = 0;
     for (int j = 0; j < m; ++j) {
       TagSet tags;
-      if (graphs) {
-        if (!G->graphs[j]) {
-          cudaGraph_t gr;
-          G->prof.reset_step();
-          const long long c0 = g_launch_count.load();
-          CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      if (graphs && !G->graphs[j]) {
+        // A capture can be invalidated by another host thread's context-wide
+        // work (e.g. loading a module on first use); the step then runs
+        // uncaptured and the capture is tried again at the next cycle.
+        cudaGraph_t gr = nullptr;
+        G->prof.reset_step();
+        const long long c0 = g_launch_count.load();
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
           arnoldi<TZ>(G, Z, j, s);
-          cudaError_t e = cudaStreamEndCapture(s, &gr);
-          ck(e, "graph capture of an Arnoldi step");
-          const long long c1 = g_launch_count.load();
-          g_launch_count.fetch_sub(c1 - c0);          // counted when the graph runs
+          e = cudaStreamEndCapture(s, &gr);
+        }
+        const long long c1 = g_launch_count.load();
+        g_launch_count.fetch_sub(c1 - c0);            // counted when the graph runs
+        if (e == cudaSuccess && gr) e = cudaGraphInstantiate(&G->graphs[j], gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+        if (e == cudaSuccess && G->graphs[j]) {
           G->graph_kernels[j] = c1 - c0;
           G->graph_tags[j] = G->prof.ended;
-          CK(cudaGraphInstantiate(&G->graphs[j], gr, 0));
-          cudaGraphDestroy(gr);
+        } else {
+          cudaGetLastError();
+          cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+          if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t dead = nullptr;
+            cudaStreamEndCapture(s, &dead);
+            if (dead) cudaGraphDestroy(dead);
+          }
+          cudaGetLastError();
+          if (G->graphs[j]) cudaGraphExecDestroy(G->graphs[j]);
+          G->graphs[j] = nullptr;
         }
+      }
+      if (graphs && G->graphs[j]) {
         CK(cudaGraphLaunch(G->graphs[j], s));
         g_launch_count.fetch_add(G->graph_kernels[j]);
         tags = G->graph_tags[j];
@@ -1394,6 +1411,7 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
     r.status = OK_SUCCESS;
     r.newton_its = r.gmres_its = 0;
     r.t_admit = r.t_done = 0.0;
+    r.message[0] = 0;
     ok_opts o;
     ok_default_opts(&o);
     if (r.opts) o = *r.opts;
@@ -1430,6 +1448,10 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
         status = ok_timestep(g, q.u, q.w, &si, (ok_stream)st);
         q.newton_its += si.newton_its;
         q.gmres_its += si.gmres_its;
+      }
+      if (status != OK_SUCCESS) {
+        std::strncpy(q.message, ok_last_error(), sizeof(q.message) - 1);
+        q.message[sizeof(q.message) - 1] = 0;
       }
       if (g) ok_grid_destroy(g);
       if (st) cudaStreamDestroy(st);

@@ -87,6 +87,8 @@ void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const T
 // Fused coarse V-cycle: levels Lc..L of the hierarchy in one thread block with
 // every level vector in shared memory (x, b, r, d0, d1 at off[l]).
 constexpr int COARSE_MAXLEV = 8;
+constexpr size_t COARSE_SMEM_MAX = 200 * 1024;   // shared-memory budget of the fused coarse V-cycle
+constexpr long long COARSE_NC_MAX = 4913;         // largest coarsest level solved densely
 template <typename T> struct CoarseArgs {
   int nlev;                          // levels in the fused part (>= 2)
   Geom g[COARSE_MAXLEV];
@@ -105,7 +107,10 @@ template <typename T> struct CoarseArgs {
 template <typename T>
 void launch_coarse_vcycle(int dim, const CoarseArgs<T>& a, size_t smem, const T* b_in, const T* x_in, T* x_out,
                           cudaStream_t s);
-// allow `smem` bytes of dynamic shared memory for the fused kernel (call before capture)
+// allow the fused kernel its dynamic shared memory (call before capture).  The
+// limit is a property of the kernel shared by every handle in the process, so
+// it is always set to the largest any handle uses (COARSE_SMEM_MAX), never to
+// one handle's need.
 template <typename T>
 cudaError_t prepare_coarse_vcycle(int dim, size_t smem);
 

@@ -17,6 +17,8 @@
 //     (P x_c)(2i+b) = (x_c(i) + x_c(i+b)) / 2,     (P x_c)(2i) = x_c(i),
 //     (P^T r_f)(i)  = r_f(2i) + 1/2 sum_{b != 0} [r_f(2i+b) + r_f(2i-b)],
 // the second sum running over the same offsets +-b as the P1 stencil.
+#include <algorithm>
+
 #include "ok_internal.cuh"
 #include "ok_kernels.h"
 #include "ok_stencil.cuh"
@@ -428,8 +430,11 @@ void launch_coarse_gemv(long long nc, long long ld, const T* Ainv, const T* b, T
 }
 template <typename T>
 cudaError_t prepare_coarse_gemv(long long nc) {
+  // per-kernel limit shared by all handles: the largest coarsest level's need
+  (void)nc;
+  const size_t need = (size_t)gemv_staged<T>(gemv_ld(COARSE_NC_MAX, sizeof(T))) * sizeof(T);
   return cudaFuncSetAttribute(k_coarse_gemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(gemv_staged<T>(gemv_ld(nc, sizeof(T))) * sizeof(T)));
+                              (int)std::max(need, (size_t)48 * 1024));
 }
 template <typename T, typename TX, typename TY>
 void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha,
@@ -445,9 +450,10 @@ void launch_coarse_vcycle(int dim, const CoarseArgs<T>& a, size_t smem, const T*
 }
 template <typename T>
 cudaError_t prepare_coarse_vcycle(int dim, size_t smem) {
-  if (dim == 2)
-    return cudaFuncSetAttribute(k_coarse_vcycle<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaFuncSetAttribute(k_coarse_vcycle<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > COARSE_SMEM_MAX) return cudaErrorInvalidValue;
+  const int lim = (int)COARSE_SMEM_MAX;             // shared by all handles: never lowered
+  if (dim == 2) return cudaFuncSetAttribute(k_coarse_vcycle<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return cudaFuncSetAttribute(k_coarse_vcycle<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 template void launch_coarse_vcycle<double>(int, const CoarseArgs<double>&, size_t, const double*, const double*,
                                            double*, cudaStream_t);

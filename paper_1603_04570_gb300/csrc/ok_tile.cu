@@ -621,7 +621,8 @@ int prepare_low_vcycle(long long nc) {
   using GP = typename StripCfg<T>::template Low<4>;
   using GQ = typename StripCfg<T>::template Low<3>;
   auto kern = k_low_vcycle<T, GP, GQ>;
-  const size_t smem = low_smem<T>(nc);
+  (void)nc;
+  const size_t smem = low_smem<T>(COARSE_NC_MAX);  // per-kernel limit shared by all handles
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     cudaGetLastError();

@@ -78,7 +78,7 @@ def test_too_large_coarse_level_rejected():
 
 
 def test_serving_structs_match_the_header():
-    assert ctypes.sizeof(ok.ServeRequest) == 128 and ok.ServeRequest.arrival.offset == 80
+    assert ctypes.sizeof(ok.ServeRequest) == 224 and ok.ServeRequest.arrival.offset == 80
     assert ok.ServeRequest.device_bytes.offset == 120
     assert ctypes.sizeof(ok.ServeInfo) == 32 and ok.ServeInfo.seconds.offset == 24
 
