@@ -413,6 +413,9 @@ struct ok_grid {
   Prec<double> pd;
   Prec<float> pf;
   std::vector<cudaGraphExec_t> graphs;   // one Arnoldi step per j
+  std::vector<cudaGraphExec_t> cgraphs;  // the same behind a device-side IF (batched launches)
+  std::vector<long long> cgraph_kernels;
+  bool cond_ok = true;                   // conditional graphs build on this device
   std::vector<long long> graph_kernels;  // kernels captured in each graph
   std::vector<TagSet> graph_tags;        // profiled kernel classes in each graph
   Profiler prof;
@@ -772,6 +775,81 @@ void arnoldi(ok_grid* G, TZ* Z, int j, cudaStream_t s) {
   pr.end(PT_CGS2, s);
 }
 
+// Arnoldi steps launched per host check when conditional graphs are used
+static constexpr int COND_BATCH = 4;
+
+// Graph of Arnoldi step j behind a device-side condition: a one-thread kernel
+// sets the IF node's condition from the cycle's continue flag (the previous
+// step's stop test), and the captured step runs only while it is set.  The
+// host can then launch several steps and check once.  Returns false (and
+// leaves no error) when the device or the captured step cannot be built this
+// way; the caller keeps the per-step path.
+template <typename TZ>
+bool build_cond_graph(ok_grid* G, TZ* Z, int j) {
+  cudaStream_t s = G->s;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const bool pdl_saved = g_pdl;
+    if (attempt == 1) g_pdl = false;               // programmatic edges inside the body may be refused
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNode_t kn = nullptr, cn = nullptr;
+    bool ok = cudaGraphCreate(&gr, 0) == cudaSuccess;
+    ok = ok && cudaGraphConditionalHandleCreate(&h, gr, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+      KrylovState* ksp = G->ks;
+      void* args[] = {&h, &ksp};
+      cudaKernelNodeParams kp = {};
+      kp.func = cond_set_kernel();
+      kp.gridDim = dim3(1, 1, 1);
+      kp.blockDim = dim3(1, 1, 1);
+      kp.kernelParams = args;
+      ok = cudaGraphAddKernelNode(&kn, gr, nullptr, 0, &kp) == cudaSuccess;
+    }
+    cudaGraph_t body = nullptr;
+    if (ok) {
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeIf;
+      cp.conditional.size = 1;
+      ok = cudaGraphAddNode(&cn, gr, &kn, nullptr, 1, &cp) == cudaSuccess;
+      if (ok) body = cp.conditional.phGraph_out[0];
+    }
+    const long long c0 = g_launch_count.load();
+    if (ok) {
+      ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+           cudaSuccess;
+      if (ok) {
+        G->prof.reset_step();
+        arnoldi<TZ>(G, Z, j, s);
+        cudaGraph_t out = nullptr;
+        ok = cudaStreamEndCapture(s, &out) == cudaSuccess;
+      }
+    }
+    const long long c1 = g_launch_count.load();
+    g_launch_count.fetch_sub(c1 - c0);              // counted when a body runs
+    if (ok) ok = cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess;
+    if (gr) cudaGraphDestroy(gr);
+    g_pdl = pdl_saved;
+    if (ok) {
+      G->cgraphs[j] = ex;
+      G->cgraph_kernels[j] = c1 - c0;
+      return true;
+    }
+    cudaGetLastError();
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t dead = nullptr;
+      cudaStreamEndCapture(s, &dead);
+      if (dead) cudaGraphDestroy(dead);
+    }
+    cudaGetLastError();
+    if (ex) cudaGraphExecDestroy(ex);
+  }
+  return false;
+}
+
 // Right-preconditioned restarted FGMRES for J x = f (all device pointers).
 template <typename TZ>
 void fgmres(ok_grid* G, TZ* Z, const double* f, double* x, int& its, double& rel) {
@@ -794,12 +872,41 @@ void fgmres(ok_grid* G, TZ* Z, const double* f, double* x, int& its, double& rel
   CK(cudaMemcpyAsync(G->dsc + 1, G->dsc, sizeof(double), cudaMemcpyDeviceToDevice, s));
   const bool graphs = G->o.use_graphs != 0;
   while (beta > rtol * fnorm && its < G->o.max_gmres) {
-    launch_cycle_start(G->ks, G->dsc + 1, s);
+    launch_cycle_start(G->ks, G->dsc + 1, rtol * fnorm, s);
     launch_axpby<double, double>(N, 1.0, G->rv, 0.0, G->V, s);
     launch_scale_by(G->V, N, ks_beta_ptr(G->ks) + 1, s);    // inv_beta follows beta
     CKL();
     int jused = 0;
-    for (int j = 0; j < m; ++j) {
+    const int jmax = std::min(m, G->o.max_gmres - its);
+    bool stop = false;
+    while (!stop && jused < jmax) {
+      if (graphs && !G->prof.on && G->cond_ok) {
+        // up to COND_BATCH steps behind device-side conditions, one host check
+        const int nb = std::min(COND_BATCH, jmax - jused);
+        int launched = 0;
+        for (int b = 0; b < nb; ++b) {
+          const int jj = jused + b;
+          if (!G->cgraphs[jj] && !build_cond_graph<TZ>(G, Z, jj)) break;
+          CK(cudaGraphLaunch(G->cgraphs[jj], s));
+          ++launched;
+        }
+        if (launched > 0) {
+          CK(cudaMemcpyAsync(G->hpin, ks_eta_ptr(G->ks), 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          const double est = G->hpin[2], go = G->hpin[3];
+          const int taken = (int)G->hpin[4];
+          long long k = launched;                       // the condition kernels
+          for (int jj = jused; jj < taken; ++jj) k += G->cgraph_kernels[jj];
+          g_launch_count.fetch_add(k);
+          its += taken - jused;
+          jused = taken;
+          if (!std::isfinite(est)) fail(OK_ERR_NONFINITE, "non-finite value in FGMRES");
+          stop = go == 0.0;
+          continue;
+        }
+        G->cond_ok = false;                             // per-step graphs from here on
+      }
+      const int j = jused;
       TagSet tags;
       if (graphs && !G->graphs[j]) {
         // A capture can be invalidated by another host thread's context-wide
@@ -850,7 +957,7 @@ void fgmres(ok_grid* G, TZ* Z, const double* f, double* x, int& its, double& rel
       if (G->prof.on) G->prof.collect(tags);
       const double eta = G->hpin[0], est = G->hpin[2];
       if (!std::isfinite(est)) fail(OK_ERR_NONFINITE, "non-finite value in FGMRES");
-      if (est <= rtol * fnorm || its >= G->o.max_gmres || eta == 0.0) break;
+      stop = est <= rtol * fnorm || eta == 0.0;
     }
     launch_lsq(G->ks, jused, s);
     launch_multi_axpy<TZ>(Z, N, jused, G->ks, x, N, s);
@@ -1043,6 +1150,8 @@ int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid
       G->pd.tm.coef = G->coef;
     }
     G->graphs.assign(od.restart, nullptr);
+    G->cgraphs.assign(od.restart, nullptr);
+    G->cgraph_kernels.assign(od.restart, 0);
     G->graph_kernels.assign(od.restart, 0);
     G->graph_tags.assign(od.restart, TagSet{});
     G->pd.prof = &G->prof;
@@ -1062,6 +1171,8 @@ int ok_grid_destroy(ok_grid* G) {
   if (!G) return OK_SUCCESS;
   if (G->s) cudaStreamSynchronize(G->s);
   for (auto& ge : G->graphs)
+    if (ge) cudaGraphExecDestroy(ge);
+  for (auto& ge : G->cgraphs)
     if (ge) cudaGraphExecDestroy(ge);
   G->prof.destroy();
   G->arena.release();

@@ -205,7 +205,10 @@ void launch_scale_by(double* w, long long N, const double* factor, cudaStream_t 
 // out = ||x||_2 (device scalar)
 void launch_norm(const double* x, long long N, RedScratch rs, double* out, cudaStream_t s);
 // cycle start: v0 = r / beta with beta = ||r|| on device; ks reset
-void launch_cycle_start(KrylovState* ks, const double* beta, cudaStream_t s);
+void launch_cycle_start(KrylovState* ks, const double* beta, double thresh, cudaStream_t s);
+// k_cond_set(cudaGraphConditionalHandle, const KrylovState*): sets a graph's IF
+// condition from the cycle's continue flag
+void* cond_set_kernel();
 // y = H^{-1} g (upper triangular, size k)
 void launch_lsq(KrylovState* ks, int k, cudaStream_t s);
 // x += sum_k y_k Z_k

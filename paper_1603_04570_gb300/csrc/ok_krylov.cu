@@ -31,6 +31,9 @@ struct KrylovState {
   double beta, inv_beta;
   double eta, inv_eta;
   double resid;
+  double go;          // 1 while the cycle continues: set by each step (read with eta..nsteps)
+  double nsteps;      // Arnoldi steps taken in this cycle
+  double thresh;      // the steps' stop test: resid <= thresh (rtol ||f||)
   double nw0;         // ||w||^2 before the first Gram--Schmidt pass
   int skip2;          // 1: the second pass is not needed this step
   int passes2;        // second passes taken since the handle was created
@@ -204,7 +207,11 @@ __device__ void arnoldi_column(KrylovState* ks, int j, double s, bool two) {
   Hj[j + 1] = 0.0;
   ks->g[j + 1] = -sn * ks->g[j];
   ks->g[j] = c * ks->g[j];
-  ks->resid = fabs(ks->g[j + 1]);
+  const double res = fabs(ks->g[j + 1]);
+  ks->resid = res;
+  ks->nsteps += 1.0;
+  // continue while the estimate is above the tolerance, finite, and the basis grew
+  ks->go = (res > ks->thresh && eta > 0.0 && isfinite(res)) ? 1.0 : 0.0;
 }
 
 // w -= V h2 (h2 = ks->h2[K0..K0+K)), ||w||^2; last block: column j of H
@@ -326,7 +333,7 @@ __global__ void __launch_bounds__(RT) k_scale_by(double* __restrict__ w, long lo
   for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) w[e] *= f;
 }
 
-__global__ void k_cycle_start(KrylovState* ks, const double* __restrict__ beta) {
+__global__ void k_cycle_start(KrylovState* ks, const double* __restrict__ beta, double thresh) {
   pdl_entry();
   if (threadIdx.x == 0) {
     const double b = *beta;
@@ -335,8 +342,18 @@ __global__ void k_cycle_start(KrylovState* ks, const double* __restrict__ beta) 
     for (int i = 0; i <= KRYLOV_MAX; ++i) ks->g[i] = 0.0;
     ks->g[0] = b;
     ks->resid = b;
+    ks->go = 1.0;
+    ks->nsteps = 0.0;
+    ks->thresh = thresh;
   }
 }
+
+// First node of a conditional Arnoldi-step graph: the step's body runs only
+// while the cycle goes on (the previous step's stop test, on the device).
+__global__ void k_cond_set(cudaGraphConditionalHandle h, const KrylovState* __restrict__ ks) {
+  cudaGraphSetConditional(h, ks->go != 0.0 ? 1u : 0u);
+}
+void* cond_set_kernel() { return (void*)k_cond_set; }
 
 // back substitution R y = g, R = rotated H (k x k upper triangular)
 __global__ void k_lsq(KrylovState* ks, int k) {
@@ -470,8 +487,8 @@ void launch_norm(const double* x, long long N, RedScratch rs, double* out, cudaS
   launch_k(k_sumsq, krylov_blocks(), RT, 0, s, x, N, rs.partials, rs.counter, out);
 }
 
-void launch_cycle_start(KrylovState* ks, const double* beta, cudaStream_t s) {
-  launch_k(k_cycle_start, 1, 32, 0, s, ks, beta);
+void launch_cycle_start(KrylovState* ks, const double* beta, double thresh, cudaStream_t s) {
+  launch_k(k_cycle_start, 1, 32, 0, s, ks, beta, thresh);
 }
 
 void launch_lsq(KrylovState* ks, int k, cudaStream_t s) { launch_k(k_lsq, 1, 32, 0, s, ks, k); }
