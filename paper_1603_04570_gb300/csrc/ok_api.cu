@@ -1100,6 +1100,9 @@ int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid
     const int NSLOT = dim == 2 ? Topo<2>::NSLOT : Topo<3>::NSLOT;
     std::vector<double> refM(NCLASS * NOFF), refK(NCLASS * NOFF);
     reference_tables(dim, refM.data(), refK.data());
+    rc.msum4 = 0.0;
+    if (dim == 2)
+      for (int o = 0; o < NOFF; ++o) rc.msum4 += refM[4 * NOFF + o];
     Arena& A = G->arena;
     G->refWM = A.alloc<double>(refM.size());
     G->refWK = A.alloc<double>(refK.size());

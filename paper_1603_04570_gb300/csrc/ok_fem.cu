@@ -142,6 +142,50 @@ __device__ __forceinline__ double nonlinear_at(const Vtx<D>& v, const double (&u
   return a4 * t3 - a2 * lin;
 }
 
+// ---- 2D interior vertices: all six triangles, each neighbour in two ----------
+// The triangles at a vertex pair its neighbours (offsets 1 +x, 2 -x, 3 +y,
+// 4 -y, 5 +xy, 6 -xy) as (1,5) (3,5) (3,2) (2,6) (6,4) (4,1).  With the
+// neighbour sums S_k = sum u_o^k, E = sum_T b c and F = sum_T b c (b + c), the
+// simplex sums above are n = 6, A = 2 S1, B = 4 S2 + 2 E and, since per
+// triangle s1^3 + 3 s1 s2 + 2 s3 = 6 s1 s2 for two other vertices,
+// C = 6 (2 S3 + F).
+__host__ __device__ constexpr int pair_b(int t) { return t == 0 ? 1 : t == 1 ? 3 : t == 2 ? 3 : t == 3 ? 2 : t == 4 ? 6 : 4; }
+__host__ __device__ constexpr int pair_c(int t) { return t == 0 ? 5 : t == 1 ? 5 : t == 2 ? 2 : t == 3 ? 6 : t == 4 ? 4 : 1; }
+__device__ __forceinline__ double nonlinear_interior2(const double (&us)[Topo<2>::NOFF], double a4, double a2) {
+  const double a = us[0];
+  double S1 = 0.0, S2 = 0.0, S3 = 0.0, E = 0.0, F = 0.0;
+#pragma unroll
+  for (int o = 1; o < Topo<2>::NOFF; ++o) {
+    const double sq = us[o] * us[o];
+    S1 += us[o];
+    S2 += sq;
+    S3 = fma(sq, us[o], S3);
+  }
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const double bb = us[pair_b(t)], cc = us[pair_c(t)];
+    const double p = bb * cc;
+    E += p;
+    F = fma(p, bb + cc, F);
+  }
+  const double t3 = fma(fma(fma(144.0, a, 36.0 * S1), a, fma(24.0, S2, 12.0 * E)), a, fma(12.0, S3, 6.0 * F));
+  const double lin = fma(12.0, a, 2.0 * S1);
+  return a4 * t3 - a2 * lin;
+}
+
+// path-Laplacian sums of K at an interior vertex (compile time): the diagonal
+// (q = -1) and the positive offset 2q+1
+__host__ __device__ constexpr int klap_interior(int D, int q) {
+  int s = 0;
+  for (int i = 0; i < (D == 2 ? Topo<2>::NINC : Topo<3>::NINC); ++i)
+    for (int t = 0; t <= D; ++t) {
+      const int o = inc_off(D, i, t);
+      if ((q < 0 && t == inc_pos(D, i)) || (q >= 0 && t != inc_pos(D, i) && o == 2 * q + 1))
+        s += path_lap(D, inc_pos(D, i), t);
+    }
+  return s;
+}
+
 // ---------------------------------------------------------------------------
 // residual  f = -F(u, w)
 // ---------------------------------------------------------------------------
@@ -162,18 +206,37 @@ __global__ void __launch_bounds__(128) k_residual(Geom g, const double* __restri
   pdl_wait();
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
-  double us[Tp::NOFF], g1[Tp::NOFF], g2[Tp::NAX], ws[Tp::NOFF];
+  double us[Tp::NOFF], ws[Tp::NOFF], uns[Tp::NOFF], wns[Tp::NAX];
   static_for<0, Tp::NOFF>([&](auto O) {
     constexpr int o = decltype(O)::value;
-    bool ok = nb_valid<D, o>(v.c);
-    long long j = v.idx + (ok ? nb_delta<D, o>(g) : 0);
-    double uu = u[j], ww = w[j];
+    const bool ok = nb_valid<D, o>(v.c);
+    const long long j = v.idx + (ok ? nb_delta<D, o>(g) : 0);
+    const double uu = u[j], ww = w[j], uun = un[j];
     us[o] = ok ? uu : 0.0;
     ws[o] = ok ? ww : 0.0;
-    g1[o] = ok ? (rc.a11 * uu - rc.bn * un[j] - rc.dsm) : 0.0;
-    if constexpr (o < Tp::NAX) g2[o] = ok ? (rc.dth * ww + rc.dth1 * wn[j]) : 0.0;
+    uns[o] = ok ? uun : 0.0;
+    if constexpr (o < Tp::NAX) wns[o] = ok ? wn[j] : 0.0;
   });
   const double hd = rc.hd, hk = rc.hk;
+  if constexpr (D == 2) {
+    if (v.cls == 4) {            // interior: M (a11 u - bn un - dsm) = a11 M u - bn M un - dsm M 1
+      const double F1 = hd * (rc.a11 * dot_w<D, Tp::NOFF>(sWM, 4, us) - rc.bn * dot_w<D, Tp::NOFF>(sWM, 4, uns) -
+                              rc.dsm * rc.msum4) +
+                        hk * (rc.dth * dot_w<D, Tp::NAX>(sWK, 4, ws) + rc.dth1 * dot_w<D, Tp::NAX>(sWK, 4, wns));
+      double F2 = hd * dot_w<D, Tp::NOFF>(sWM, 4, ws) - rc.eps2 * hk * dot_w<D, Tp::NAX>(sWK, 4, us);
+      F2 -= rc.vol * nonlinear_interior2(us, rc.a4, rc.a2);
+      f[v.idx] = -F1;
+      f[v.idx + g.nv] = -F2;
+      return;
+    }
+  }
+  double g1[Tp::NOFF], g2[Tp::NAX];
+  static_for<0, Tp::NOFF>([&](auto O) {
+    constexpr int o = decltype(O)::value;
+    const bool ok = nb_valid<D, o>(v.c);
+    g1[o] = ok ? (rc.a11 * us[o] - rc.bn * uns[o] - rc.dsm) : 0.0;
+    if constexpr (o < Tp::NAX) g2[o] = ok ? (rc.dth * ws[o] + rc.dth1 * wns[o]) : 0.0;
+  });
   double F1 = hd * dot_w<D, Tp::NOFF>(sWM, v.cls, g1) + hk * dot_w<D, Tp::NAX>(sWK, v.cls, g2);
   double F2 = hd * dot_w<D, Tp::NOFF>(sWM, v.cls, ws) - rc.eps2 * hk * dot_w<D, Tp::NAX>(sWK, v.cls, us);
   // N(u)_v: sums over the incident simplices
@@ -215,6 +278,38 @@ __global__ void __launch_bounds__(128) k_assemble_c(Geom g, ResidualCoefs rc, co
   for (int o = 0; o < Tp::NOFF; ++o) sq[o] = us[o] * us[o];
   const double kscale = rc.eps2 * rc.hk * (1.0 / Tp::FACT);   // eps^2 h^(d-2) / d!
   const double a = us[0];
+  if constexpr (D == 2) {
+    if (v.cls == 4) {            // interior: six triangles, each edge in two
+      double S1 = 0.0, S2 = 0.0, E = 0.0;
+#pragma unroll
+      for (int o = 1; o < Tp::NOFF; ++o) {
+        S1 += us[o];
+        S2 += sq[o];
+      }
+#pragma unroll
+      for (int t = 0; t < 6; ++t) E = fma(us[pair_b(t)], us[pair_c(t)], E);
+      // sum over the triangles of p1^2 + p2 + 4 p1 a + 6 a^2 = 12 n a^2 + 6 a A + B
+      const double Paa = fma(fma(72.0, a, 12.0 * S1), a, fma(4.0, S2, 2.0 * E));
+      constexpr int KL0 = klap_interior(2, -1);
+      const double diag = -kscale * KL0 - rc.vol * 2.0 * (3.0 * rc.a4 * Paa - rc.a2 * 6.0);
+      coef[v.idx] = diag;
+      coef32[v.idx] = (float)diag;
+      // edge (v, v + pos_q) lies in two triangles whose third vertices are c1, c2
+      static_for<0, Tp::NPOS>([&](auto Q) {
+        constexpr int q = decltype(Q)::value;
+        constexpr int t1 = q == 0 ? 5 : (q == 1 ? 5 : 1), t2 = q == 0 ? 4 : (q == 1 ? 2 : 3);
+        const double b = us[2 * q + 1], c1 = us[t1], c2 = us[t2];
+        const double m = a + b;
+        const double R1 = c1 + c2, R2 = 2.0 * (sq[t1] + sq[t2]);
+        const double P = fma(2.0, fma(6.0 * m, m, -4.0 * a * b), fma(4.0 * m, R1, R2));
+        constexpr int KLQ = klap_interior(2, q);
+        const double c = -kscale * KLQ - rc.vol * (3.0 * rc.a4 * P - rc.a2 * 2.0);
+        coef[(1 + q) * g.nv + v.idx] = c;
+        coef32[(1 + q) * g.nv + v.idx] = (float)c;
+      });
+      return;
+    }
+  }
   // per positive offset p: simplices holding the edge, sum r1, sum (r1^2 + r2),
   // and the summed path-Laplacian entries of K
   double R1[Tp::NPOS], R2[Tp::NPOS];

@@ -19,6 +19,7 @@ struct ResidualCoefs {
   double vol;    // |T| = h^d / d!
   double a4;     // d! / (d+4)!
   double a2;     // d! / (d+2)!
+  double msum4;  // 2D: row sum of the reference mass table of an interior vertex
 };
 
 // y = alpha J z + beta y0 (y0 may be null: y = J z)
