@@ -619,6 +619,9 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
     m.WM = P.WM;
     m.dinvM = P.dinvM;
     m.coef = nullptr;         // set when the coefficient store is bound
+    m.sx = P.cx;              // the Chebyshev-on-M buffers of the untiled path
+    m.sr = P.cr;
+    m.sd = P.cd0;
     m.q = P.q_A;
     m.inv_th = (T)(1.0 / P.thM);
     m.inv_a11 = (T)P.inv_a11;

@@ -132,6 +132,7 @@ template <typename T> struct TileMass {
   int q;                  // Chebyshev steps (halo width), 1..16
   T inv_th, inv_a11;
   T c1[16], c2[16];
+  T *sx, *sr, *sd;        // x, r, d handed from the first launch to the second (N_v each)
 };
 // pre-smoothing (2 steps from x_in, or zero when x_in is null), restriction into bc
 template <typename T>

@@ -26,8 +26,8 @@
 //                 optionally M x (the middle factor of
 //                 S~^{-1} = S_hat^{-1} M S_hat^{-1}) and a cast of x (H = 3);
 //   k_strip_amass QTILE Chebyshev steps on M (A~^{-1} r1, Sec. 3) and the
-//                 preconditioner's C-step t = r2 - C A~^{-1} r1 (eqn prec)
-//                 (H = QTILE).
+//                 preconditioner's C-step t = r2 - C A~^{-1} r1 (eqn prec),
+//                 in two launches of halo QSPLIT.
 // x is read from one buffer and written to another (ping-pong), because other
 // blocks read the old x in their halos while this block writes.
 #include "ok_internal.cuh"
@@ -36,7 +36,8 @@
 
 namespace okg {
 
-constexpr int QTILE = 10;   // mass Chebyshev steps handled by the strip kernel
+constexpr int QTILE = 10;   // mass Chebyshev steps handled by the strip kernels
+constexpr int QSPLIT = 5;   // steps of the first of the two mass launches
 constexpr int NTAB = Topo<2>::NCLASS * Topo<2>::NOFF;
 
 // Window geometry: CW columns, CH = RY * NCH rows, halo H.
@@ -68,7 +69,7 @@ template <typename T> struct StripCfg;
 template <> struct StripCfg<float> {
   template <int H> using Big = SG<OK_STRIP_F_BIG, H>;
   template <int H> using Small = SG<OK_STRIP_F_SMALL, H>;
-  using Mass = SG<OK_STRIP_F_MASS, QTILE>;
+  using Mass = SG<OK_STRIP_F_MASS, QSPLIT>;
   template <int H> using Low = SG<64, 4, 16, H>;       // one window per block of the cluster kernel
 };
 #ifndef OK_STRIP_D_BIG
@@ -78,12 +79,12 @@ template <> struct StripCfg<float> {
 #define OK_STRIP_D_SMALL 32, 2, 8
 #endif
 #ifndef OK_STRIP_D_MASS
-#define OK_STRIP_D_MASS 64, 4, 16
+#define OK_STRIP_D_MASS 64, 2, 16
 #endif
 template <> struct StripCfg<double> {
   template <int H> using Big = SG<OK_STRIP_D_BIG, H>;
   template <int H> using Small = SG<OK_STRIP_D_SMALL, H>;
-  using Mass = SG<OK_STRIP_D_MASS, QTILE>;
+  using Mass = SG<OK_STRIP_D_MASS, QSPLIT>;
   template <int H> using Low = SG<64, 2, 16, H>;
 };
 
@@ -437,11 +438,15 @@ __global__ void __launch_bounds__(G::NT) k_strip_post(TileSmooth<T> a, const T* 
 }
 
 // ---------------------------------------------------------------------------
-// QTILE Chebyshev steps on M + C-step:  z1 = A~^{-1} r1,  t = r2 - C z1
+// QTILE Chebyshev steps on M + C-step:  z1 = A~^{-1} r1,  t = r2 - C z1, in
+// two launches of QSPLIT and QTILE - 1 - QSPLIT steps (halo 5 each instead of
+// 10 in one: a third less redundant work); the first stores x, r, d of its
+// owned vertices for the second, whose windows reload them with their halo.
 // ---------------------------------------------------------------------------
-template <typename T, typename TZ, class G, bool INT>
+template <typename T, typename TZ, class G, bool INT, int K0, int K1, bool FIRST, bool LAST>
 __device__ __forceinline__ void strip_amass_body(const TileMass<T>& a, const Pos& p, T* buf0, T* buf1,
                                                  const T* sW, const T* sD, const double* v, TZ* z1, T* t_out) {
+  static_assert(G::H >= (K1 - K0) + (LAST ? 1 : 0), "halo too narrow for the steps of this launch");
   constexpr int RY = G::RY, Q = QTILE;
   const int n = a.g.n;
   const long long sy = a.g.sy, nv = a.g.nv;
@@ -449,25 +454,34 @@ __device__ __forceinline__ void strip_amass_body(const TileMass<T>& a, const Pos
 #pragma unroll
   for (int i = 0; i < RY; ++i) {
     const bool in = INT || row_in(p, i, n);
-    x[i] = (T)0;
-    r[i] = in ? (T)v[p.gx + sy * (p.gy0 + i)] : (T)0;    // b, held until the tables arrive
+    const long long gi = p.gx + sy * (p.gy0 + i);
+    if constexpr (FIRST) {
+      x[i] = (T)0;
+      r[i] = in ? (T)v[gi] : (T)0;                  // b, held until the tables arrive
+    } else {
+      x[i] = in ? a.sx[gi] : (T)0;
+      r[i] = in ? a.sr[gi] : (T)0;
+      d[i] = in ? a.sd[gi] : (T)0;
+    }
   }
   __syncthreads();                                  // tables visible
   RegW<2, T> rw{};
   if constexpr (INT) rw = reg_weights<2, T>(sW, sD, 4);
+  if constexpr (FIRST) {
 #pragma unroll
-  for (int i = 0; i < RY; ++i) {                    // cheb_init (b scaled by 1)
-    int cy;
-    const int cls = row_class<INT>(p, i, n, cy);
-    const T dv = INT ? rw.dinv : sD[cls];
-    T rr = r[i] * (T)1;
-    r[i] = rr;
-    d[i] = dv * rr * a.inv_th;
+    for (int i = 0; i < RY; ++i) {                  // cheb_init (b scaled by 1)
+      int cy;
+      const int cls = row_class<INT>(p, i, n, cy);
+      const T dv = INT ? rw.dinv : sD[cls];
+      T rr = r[i] * (T)1;
+      r[i] = rr;
+      d[i] = dv * rr * a.inv_th;
+    }
   }
   Nb<G, T> nb;
-  static_for<0, Q - 1>([&](auto Kc) {               // cheb_step k (first at k = 0)
+  static_for<K0, K1>([&](auto Kc) {                 // cheb_step k (first at k = 0)
     constexpr int k = decltype(Kc)::value;
-    T* buf = (k & 1) ? buf1 : buf0;
+    T* buf = ((k - K0) & 1) ? buf1 : buf0;
     xput<G>(buf, p, d);
     __syncthreads();
     xget<G>(buf, p, nb);
@@ -487,40 +501,52 @@ __device__ __forceinline__ void strip_amass_body(const TileMass<T>& a, const Pos
 #pragma unroll
     for (int i = 0; i < RY; ++i) d[i] = dn[i];
   });
+  if constexpr (!LAST) {                            // hand x, r, d of the owned vertices on
 #pragma unroll
-  for (int i = 0; i < RY; ++i) {                    // cheb_last without the residual
-    T xx = (Q == 1 ? (T)0 : x[i]) + d[i];
-    x[i] = xx;
-  }
-  // C-step at the owned vertices (capply_at on y = x, scaled by 1 / a11)
-  T* buf = ((Q - 1) & 1) ? buf1 : buf0;
-  xput<G>(buf, p, x);
-  __syncthreads();
-  xget<G>(buf, p, nb);
+    for (int i = 0; i < RY; ++i) {
+      if (!owned<G>(p, i) || !(INT || row_in(p, i, n))) continue;
+      const long long gi = p.gx + sy * (p.gy0 + i);
+      a.sx[gi] = x[i];
+      a.sr[gi] = r[i];
+      a.sd[gi] = d[i];
+    }
+    return;
+  } else {
 #pragma unroll
-  for (int i = 0; i < RY; ++i) {
-    if (!owned<G>(p, i) || !(INT || row_in(p, i, n))) continue;
-    const long long gi = p.gx + sy * (p.gy0 + i);
-    int cy;
-    row_class<INT>(p, i, n, cy);
-    const int c[3] = {p.cx, cy, 1};
-    z1[gi] = (TZ)(x[i] * a.inv_a11);
-    T xs[Topo<2>::NOFF];
-    nb_row<G, T, INT>(x, nb, i, p.cx, cy, xs);
-    T acc = a.coef[gi] * xs[0] * a.inv_a11;
-    static_for<0, Topo<2>::NPOS>([&](auto P) {
-      constexpr int q = decltype(P)::value;
-      constexpr int op = 2 * q + 1, om = 2 * q + 2;
-      constexpr long long dxm = off_comp(2, om, 0), dym = off_comp(2, om, 1);
-      if (INT || nb_valid<2, op>(c)) acc = fma(a.coef[(1 + q) * nv + gi], xs[op] * a.inv_a11, acc);
-      if (INT || nb_valid<2, om>(c))
-        acc = fma(a.coef[(1 + q) * nv + gi + dxm + sy * dym], xs[om] * a.inv_a11, acc);
-    });
-    t_out[gi] = (T)v[gi + nv] * (T)1 - acc;
+    for (int i = 0; i < RY; ++i) {                  // cheb_last without the residual
+      T xx = (Q == 1 ? (T)0 : x[i]) + d[i];
+      x[i] = xx;
+    }
+    // C-step at the owned vertices (capply_at on y = x, scaled by 1 / a11)
+    T* buf = ((K1 - K0) & 1) ? buf1 : buf0;
+    xput<G>(buf, p, x);
+    __syncthreads();
+    xget<G>(buf, p, nb);
+#pragma unroll
+    for (int i = 0; i < RY; ++i) {
+      if (!owned<G>(p, i) || !(INT || row_in(p, i, n))) continue;
+      const long long gi = p.gx + sy * (p.gy0 + i);
+      int cy;
+      row_class<INT>(p, i, n, cy);
+      const int c[3] = {p.cx, cy, 1};
+      z1[gi] = (TZ)(x[i] * a.inv_a11);
+      T xs[Topo<2>::NOFF];
+      nb_row<G, T, INT>(x, nb, i, p.cx, cy, xs);
+      T acc = a.coef[gi] * xs[0] * a.inv_a11;
+      static_for<0, Topo<2>::NPOS>([&](auto P) {
+        constexpr int q = decltype(P)::value;
+        constexpr int op = 2 * q + 1, om = 2 * q + 2;
+        constexpr long long dxm = off_comp(2, om, 0), dym = off_comp(2, om, 1);
+        if (INT || nb_valid<2, op>(c)) acc = fma(a.coef[(1 + q) * nv + gi], xs[op] * a.inv_a11, acc);
+        if (INT || nb_valid<2, om>(c))
+          acc = fma(a.coef[(1 + q) * nv + gi + dxm + sy * dym], xs[om] * a.inv_a11, acc);
+      });
+      t_out[gi] = (T)v[gi + nv] * (T)1 - acc;
+    }
   }
 }
 
-template <typename T, typename TZ, class G>
+template <typename T, typename TZ, class G, int K0, int K1, bool FIRST, bool LAST>
 __global__ void __launch_bounds__(G::NT) k_strip_amass(TileMass<T> a, const double* __restrict__ v,
                                                         TZ* __restrict__ z1, T* __restrict__ t_out) {
   pdl_launch_dependents();
@@ -534,8 +560,9 @@ __global__ void __launch_bounds__(G::NT) k_strip_amass(TileMass<T> a, const doub
   pdl_wait();                                      // tables are fixed at setup; the rest is not
   const Pos p = strip_pos<G>(a.g.n, blockIdx.x, blockIdx.y);
   if (strip_interior<G>(a.g.n, blockIdx.x, blockIdx.y))
-    strip_amass_body<T, TZ, G, true>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
-  else strip_amass_body<T, TZ, G, false>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
+    strip_amass_body<T, TZ, G, true, K0, K1, FIRST, LAST>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
+  else
+    strip_amass_body<T, TZ, G, false, K0, K1, FIRST, LAST>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -704,8 +731,10 @@ void launch_tile_post(const TileSmooth<T>& a, const T* x_in, const T* xc, const 
 template <typename T, typename TZ>
 void launch_tile_amass(const TileMass<T>& a, const double* v, TZ* z1, T* t_out, cudaStream_t s) {
   using Mass = typename StripCfg<T>::Mass;
-  launch_k(k_strip_amass<T, TZ, Mass>, strip_grid<Mass>(a.g), Mass::NT, strip_smem<Mass, T>(false), s, a, v, z1,
-           t_out);
+  launch_k(k_strip_amass<T, TZ, Mass, 0, QSPLIT, true, false>, strip_grid<Mass>(a.g), Mass::NT,
+           strip_smem<Mass, T>(false), s, a, v, z1, t_out);
+  launch_k(k_strip_amass<T, TZ, Mass, QSPLIT, QTILE - 1, false, true>, strip_grid<Mass>(a.g), Mass::NT,
+           strip_smem<Mass, T>(false), s, a, v, z1, t_out);
 }
 
 template <typename T>
@@ -724,12 +753,17 @@ cudaError_t prepare_tiles(int q) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, double, BQ>, attr, (int)strip_smem<BQ, T>(true));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, float, SQ>, attr, (int)strip_smem<SQ, T>(true));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, double, SQ>, attr, (int)strip_smem<SQ, T>(true));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, float, MA>, attr, (int)strip_smem<MA, T>(false));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, double, MA>, attr, (int)strip_smem<MA, T>(false));
+  const int ms = (int)strip_smem<MA, T>(false);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, float, MA, 0, QSPLIT, true, false>, attr, ms);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, float, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, double, MA, 0, QSPLIT, true, false>, attr, ms);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, double, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
   if constexpr (std::is_same<T, float>::value) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, __half, BQ>, attr, (int)strip_smem<BQ, T>(true));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, __half, SQ>, attr, (int)strip_smem<SQ, T>(true));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, __half, MA>, attr, (int)strip_smem<MA, T>(false));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, __half, MA, 0, QSPLIT, true, false>, attr, ms);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_strip_amass<T, __half, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
   }
   return e;
 }
