@@ -779,7 +779,10 @@ void arnoldi(ok_grid* G, TZ* Z, int j, cudaStream_t s) {
 }
 
 // Arnoldi steps launched per host check when conditional graphs are used
-static constexpr int COND_BATCH = 4;
+#ifndef OK_COND_BATCH
+#define OK_COND_BATCH 4
+#endif
+static constexpr int COND_BATCH = OK_COND_BATCH;
 
 // Graph of Arnoldi step j behind a device-side condition: a one-thread kernel
 // sets the IF node's condition from the cycle's continue flag (the previous
