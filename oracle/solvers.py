@@ -12,7 +12,7 @@ Follows Farrell & Pearson, Sec. 2-4:
     here Jacobi-preconditioned on the interval [1/2, (d+2)/2] that holds the
     spectrum of diag(M)^{-1} M for P1 simplices;
   * S_hat^{-1}: n_V multigrid V-cycles (Sec. 2 and 4 use algebraic multigrid;
-    this build reads it as geometric multigrid on the nested uniform meshes,
+    here read as geometric multigrid on the nested uniform meshes,
     Chebyshev--Jacobi smoothing, linear interpolation, exact coarsest solve);
   * optional k_R = 2: two Richardson steps on S with S~^{-1} (Sec. 4).
 Each routine is written in the order of its textbook definition, with no
