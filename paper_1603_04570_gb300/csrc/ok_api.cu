@@ -1455,7 +1455,7 @@ int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream st
       continue;
     }
     for (int k = 0; k < r.steps; ++k) {
-      ok_step_info info;
+      ok_step_info info = {};
       int st = ok_timestep(r.grid, r.u, r.w, &info, stream);
       r.newton_its += info.newton_its;
       r.gmres_its += info.gmres_its;
@@ -1500,7 +1500,7 @@ static long long serve_estimate(int dim, int n, const ok_opts& o) {
   b += 9.0 * nv * tb * (dim == 2 ? 4.0 / 3.0 : 8.0 / 7.0);  // multigrid vectors over the levels
   const double nc = std::min(std::pow((double)(o.coarse_max + 2), dim), 4913.0);
   b += nc * nc * (8.0 + 2.0 * tb) + (1 << 20);                // coarse inverse (+ padded copy), scalars
-  return (long long)b;
+  return b < 9.0e18 ? (long long)b : 9000000000000000000LL;
 }
 
 extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, long long mem_budget,
@@ -1526,6 +1526,15 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
   long long bytes = 0, peak_bytes = 0;
   std::vector<std::thread> workers;
   workers.reserve(count);
+  // returns a request's slot and bytes (outlives every worker: they are joined below)
+  auto release = [&](ok_serve_request& q) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      --inflight;
+      bytes -= q.device_bytes;
+    }
+    cv.notify_all();
+  };
   for (int i : order) {
     ok_serve_request& r = reqs[i];
     r.status = OK_SUCCESS;
@@ -1535,11 +1544,13 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
     ok_opts o;
     ok_default_opts(&o);
     if (r.opts) o = *r.opts;
-    r.device_bytes = serve_estimate(r.dim, r.n, o);
-    if (!r.u || !r.w || r.steps < 0 || r.dim < 2 || r.dim > 3 || r.n < 2) {
+    r.device_bytes = 0;
+    if (!r.u || !r.w || r.steps < 0 || r.dim < 2 || r.dim > 3 || r.n < 2 || o.restart < 1 ||
+        o.restart >= KRYLOV_MAX || o.coarse_max < 1) {
       r.status = OK_ERR_INVALID_ARG;
       continue;
     }
+    r.device_bytes = serve_estimate(r.dim, r.n, o);
     if (r.device_bytes > mem_budget) {
       r.status = OK_ERR_NOMEM;
       continue;
@@ -1555,35 +1566,37 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
       peak_bytes = std::max(peak_bytes, bytes);
     }
     r.t_admit = now();
-    workers.emplace_back([&, i, o] {
-      ok_serve_request& q = reqs[i];
-      cudaSetDevice(device);
-      cudaStream_t st = nullptr;
-      ok_grid* g = nullptr;
-      int status = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? OK_SUCCESS : OK_ERR_CUDA;
-      if (status == OK_SUCCESS) status = ok_grid_create(q.dim, q.n, &q.params, &o, &g);
-      if (status == OK_SUCCESS && q.init_w) status = ok_init_w(g, q.u, q.w, (ok_stream)st);
-      for (int k = 0; status == OK_SUCCESS && k < q.steps; ++k) {
-        ok_step_info si;
-        status = ok_timestep(g, q.u, q.w, &si, (ok_stream)st);
-        q.newton_its += si.newton_its;
-        q.gmres_its += si.gmres_its;
-      }
-      if (status != OK_SUCCESS) {
-        std::strncpy(q.message, ok_last_error(), sizeof(q.message) - 1);
-        q.message[sizeof(q.message) - 1] = 0;
-      }
-      if (g) ok_grid_destroy(g);
-      if (st) cudaStreamDestroy(st);
-      q.status = status;
-      q.t_done = now();
-      {
-        std::lock_guard<std::mutex> lk(mu);
-        --inflight;
-        bytes -= q.device_bytes;
-      }
-      cv.notify_all();
-    });
+    try {
+      workers.emplace_back([&, i, o] {
+        ok_serve_request& q = reqs[i];
+        cudaSetDevice(device);
+        cudaStream_t st = nullptr;
+        ok_grid* g = nullptr;
+        int status = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? OK_SUCCESS : OK_ERR_CUDA;
+        if (status == OK_SUCCESS) status = ok_grid_create(q.dim, q.n, &q.params, &o, &g);
+        if (status == OK_SUCCESS && q.init_w) status = ok_init_w(g, q.u, q.w, (ok_stream)st);
+        for (int k = 0; status == OK_SUCCESS && k < q.steps; ++k) {
+          ok_step_info si = {};
+          status = ok_timestep(g, q.u, q.w, &si, (ok_stream)st);
+          q.newton_its += si.newton_its;
+          q.gmres_its += si.gmres_its;
+        }
+        if (status != OK_SUCCESS) {
+          std::strncpy(q.message, ok_last_error(), sizeof(q.message) - 1);
+          q.message[sizeof(q.message) - 1] = 0;
+        }
+        if (g) ok_grid_destroy(g);
+        if (st) cudaStreamDestroy(st);
+        q.status = status;
+        q.t_done = now();
+        release(q);
+      });
+    } catch (const std::exception&) {                // no thread: the request fails, nothing leaks
+      r.status = OK_ERR_NOMEM;
+      std::strncpy(r.message, "could not start a worker thread", sizeof(r.message) - 1);
+      r.t_done = now();
+      release(r);
+    }
   }
   for (auto& t : workers) t.join();
   int done = 0, failed = 0;
