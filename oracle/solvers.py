@@ -205,13 +205,18 @@ class Preconditioner:
 # --------------------------------------------------------------------------
 # right-preconditioned restarted flexible GMRES (Saad 1993)
 # --------------------------------------------------------------------------
-def fgmres(J_apply, P_apply, f, restart=30, rtol=1e-10, max_its=1000):
+def fgmres(J_apply, P_apply, f, restart=30, rtol=1e-10, max_its=1000, cycles=None):
     """Solve J x = f from x_0 = 0.  Returns (x, iterations, true rel. residual).
 
     Arnoldi with modified Gram--Schmidt on w = J z_j, z_j = P^{-1} v_j; the
     iterate is x_0 + Z_m y with y = argmin || beta e_1 - H_m y ||.  Stops when
     that least-squares residual is <= rtol ||f||; at every restart and at exit
     the true residual f - J x is recomputed.
+
+    `cycles`: if a list, every restart cycle of m steps appends a dict with
+    its Arnoldi relation J Z_m = V_{m+1} Hbar_m: "H" = Hbar_m ((m+1) x m),
+    "V" = [v_0 .. v_m] (v_m absent after a breakdown), "Z" = [z_0 .. z_{m-1}].
+    Recording changes no arithmetic.
     """
     fnorm = np.linalg.norm(f)
     x = np.zeros_like(f)
@@ -243,6 +248,9 @@ def fgmres(J_apply, P_apply, f, restart=30, rtol=1e-10, max_its=1000):
                 V.append(w / H[j + 1, j])
             if est <= rtol * fnorm or its >= max_its or breakdown:
                 break
+        if cycles is not None:
+            m = len(Z)
+            cycles.append({"H": H[:m + 1, :m].copy(), "V": np.column_stack(V), "Z": np.column_stack(Z)})
         x = x + np.column_stack(Z) @ y
         r = f - J_apply(x)
         beta = np.linalg.norm(r)

@@ -176,6 +176,52 @@ def test_block_preconditioned_spectrum():
     assert np.abs(lam - expect).max() < 1e-8
 
 
+@pytest.mark.parametrize("mode,k_R", [("inexact", 1), ("inexact", 2), ("exact", 1)])
+def test_fgmres_records_its_arnoldi_decomposition(mode, k_R):
+    """The recorded cycle is the (unique) Arnoldi decomposition of J P^{-1}
+    from v_0 = f / ||f||: Z = P^{-1} V, V orthonormal, Hbar upper Hessenberg
+    with positive subdiagonal and J Z = V Hbar; these conditions determine
+    Hbar (implicit Q theorem).  Restart 4 gives several cycles."""
+    sysm, u, rng = small_system(2, 6, seed=11, dt=2e-3)
+    J = sysm.jacobian(u)
+    P = Preconditioner(sysm, u, mode=mode, k_R=k_R)
+    f = rng.standard_normal(2 * sysm.mesh.nv)
+    for restart in (4, 30):
+        cycles = []
+        x, its, rel = fgmres(lambda z: J @ z, P.apply, f, restart=restart, rtol=1e-8, cycles=cycles)
+        assert sum(c["H"].shape[1] for c in cycles) == its
+        assert len(cycles) == (1 if restart == 30 else -(-its // restart))
+        c = cycles[0]
+        H, V, Z = c["H"], c["V"], c["Z"]
+        m = H.shape[1]
+        assert H.shape == (m + 1, m) and V.shape[1] == m + 1 and Z.shape[1] == m
+        assert np.abs(V[:, 0] - f / np.linalg.norm(f)).max() < 1e-15
+        assert np.abs(V.T @ V - np.eye(m + 1)).max() < 1e-6         # MGS: O(eps cond) loss
+        for j in range(m):
+            assert np.array_equal(Z[:, j], P.apply(V[:, j]))
+        assert np.all(np.tril(H, -2) == 0) and np.all(np.diag(H, -1) > 0)
+        assert np.abs(J @ Z - V @ H).max() < 1e-12 * np.abs(J @ Z).max()
+
+
+def test_ritz_values_recover_the_schur_spectrum():
+    """Sec. 3: eig(J P^{-1}) = {1} and eig(S~^{-1} S) for exact A^{-1} and
+    S~^{-1}.  Once the Krylov space is invariant the Ritz values of the cycle
+    contain every eigenvalue of S~^{-1} S (real: Lemma 1)."""
+    sysm, u, rng = small_system(2, 3, seed=3, amp=1.0, dt=2e-3)
+    J = sysm.jacobian(u)
+    P = Preconditioner(sysm, u, mode="exact")
+    f = rng.standard_normal(2 * sysm.mesh.nv)
+    cycles = []
+    fgmres(lambda z: J @ z, P.apply, f, restart=63, rtol=1e-15, max_its=63, cycles=cycles)
+    H = cycles[0]["H"]
+    m = H.shape[1]
+    ritz = np.linalg.eigvals(H[:m, :m])
+    _, _, _, S, St = dense_schur(sysm, u)
+    lam = np.linalg.eigvals(np.linalg.solve(St, S))
+    assert np.abs(lam.imag).max() < 1e-8
+    assert max(np.abs(ritz - l).min() for l in lam.real) < 1e-9
+
+
 @pytest.mark.parametrize("k_R", [1, 2])
 def test_exact_mode_preconditioner_inverts_block_triangle(k_R):
     sysm, u, rng = small_system(2, 5, seed=6, dt=2e-3)
