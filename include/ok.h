@@ -265,6 +265,46 @@ typedef struct ok_kernel_stat {
 int ok_profile(ok_grid* g, int enable);
 int ok_profile_read(const ok_grid* g, ok_kernel_stat* out, int max, int* count);
 
+/* Spectral diagnostics of the preconditioned Jacobian (Sec. 3, Lemmas 1-2).
+ * With A inverted exactly the right-preconditioned Jacobian J P^{-1} has the
+ * eigenvalue 1 and the eigenvalues of S~^{-1} S, which Lemma 1 makes real and
+ * Lemma 2 (K perturbed to be SPD) places in
+ *   [1/2 + sqrt(c) l_- / (2 eps), 1 + sqrt(c) l_+ / (2 eps)),
+ * l_- = min(lambda_min(M^{-1} M_E), 0), l_+ = max(lambda_max(M^{-1} M_E), 0),
+ * c = dt theta / (1 + dt theta sigma).  Each FGMRES restart cycle is an
+ * Arnoldi process on J P^{-1}: J Z_k = V_{k+1} Hbar_k, Z_k = P^{-1} V_k
+ * (exactly so while the preconditioner is a fixed linear map, as it is here:
+ * fixed Chebyshev steps and V-cycles).  These calls read the Arnoldi matrix
+ * of the LAST restart cycle run on `g` (by ok_solve_linear, ok_newton_step,
+ * ok_timestep); a call whose right-hand side was zero runs no cycle and
+ * leaves the previous one.  A handle that has run no cycle reports k = 0.
+ *
+ * ok_arnoldi_hessenberg: writes Hbar_k ((k+1) x k, column-major, leading
+ *   dimension ldh >= max_k + 1) into the HOST array H, k = min(steps of the
+ *   cycle, max_k) into *k; the first k columns of a longer cycle are the
+ *   Arnoldi matrix of its first k steps.  The device holds Hbar reduced by
+ *   its Givens rotations; it is restored on the host.  Synchronises with
+ *   `stream` (the stream of the solve).
+ * ok_ritz_values: the eigenvalues (Ritz values) of the square part H_k,
+ *   k <= max, into the HOST arrays re[0..k) and im[0..k) (complex pairs
+ *   adjacent), k into *count.  OK_ERR_NOT_CONVERGED if the QR iteration does
+ *   not converge, OK_ERR_NONFINITE for a non-finite Arnoldi matrix.
+ * ok_givens_unrotate: host only, no GPU needed.  H (column-major, ldh >=
+ *   k + 1) holds in columns 0..k-1 the triangular factor R left by applying,
+ *   to column j of an upper Hessenberg matrix, the rotations i = 0..j that
+ *   map rows (i, i+1) as (a, b) -> (cs[i] a + sn[i] b, -sn[i] a + cs[i] b);
+ *   overwrites it with that Hessenberg matrix (rows j+2..k of column j zeroed).
+ * ok_hessenberg_eigenvalues: host only, no GPU needed.  Eigenvalues of the
+ *   k x k upper Hessenberg matrix H (column-major, ldh >= k; entries below
+ *   the first subdiagonal are ignored) by the implicit double-shift QR
+ *   iteration (Francis 1961; Golub and Van Loan, Sec. 7.5), into re/im
+ *   (length k, in deflation order, complex pairs adjacent).
+ * All four return OK_ERR_INVALID_ARG for NULL arrays or bad sizes. */
+int ok_arnoldi_hessenberg(ok_grid* g, double* H, int ldh, int max_k, int* k, ok_stream stream);
+int ok_ritz_values(ok_grid* g, double* re, double* im, int max, int* count, ok_stream stream);
+int ok_givens_unrotate(int k, double* H, int ldh, const double* cs, const double* sn);
+int ok_hessenberg_eigenvalues(int k, const double* H, int ldh, double* re, double* im);
+
 /* y = J(u_k) z like ok_apply_jacobian, for callers that cannot allocate
  * device memory: applications that own all GPU memory through their own
  * allocator or run under a fixed memory budget, and latency-critical loops

@@ -113,6 +113,10 @@ def load(build: bool = True):
         "ok_profile_read": (c_int, [P, POINTER(KernelStat), c_int, POINTER(c_int)]),
         "ok_launch_count": (c_longlong, []),
         "ok_apply_jacobian_noalloc": (c_int, [c_int, c_int, POINTER(Params), P, P, P, P]),
+        "ok_arnoldi_hessenberg": (c_int, [P, P, c_int, c_int, POINTER(c_int), P]),
+        "ok_ritz_values": (c_int, [P, P, P, c_int, POINTER(c_int), P]),
+        "ok_givens_unrotate": (c_int, [c_int, P, c_int, P, P]),
+        "ok_hessenberg_eigenvalues": (c_int, [c_int, P, c_int, P, P]),
         "ok_last_error": (c_char_p, []),
         "ok_version": (c_char_p, []),
     }
@@ -257,6 +261,58 @@ def ok_apply_jacobian_noalloc(dim, n, params: Params, u_k, z, y, stream=None):
                                             _ptr(y, 2 * nv, "y"), _stream(stream, y, z)))
 
 
+def ok_arnoldi_hessenberg(h, max_k=63, stream=None):
+    """Hbar ((k+1) x k numpy array) of the handle's last FGMRES restart cycle."""
+    import numpy as np
+    H = np.zeros((max_k + 1, max(max_k, 1)), order="F")
+    k = c_int()
+    _check(load().ok_arnoldi_hessenberg(h, H.ctypes.data, max_k + 1, max_k, byref(k), _stream(stream)))
+    return np.ascontiguousarray(H[:k.value + 1, :k.value])
+
+
+def ok_ritz_values(h, limit=63, stream=None):
+    """Eigenvalues of the square Arnoldi matrix of the last cycle, at most `limit` steps
+    (complex numpy array)."""
+    import numpy as np
+    re, im = np.zeros(max(limit, 1)), np.zeros(max(limit, 1))
+    k = c_int()
+    _check(load().ok_ritz_values(h, re.ctypes.data, im.ctypes.data, limit, byref(k), _stream(stream)))
+    return re[:k.value] + 1j * im[:k.value]
+
+
+def _host_status(st, what):
+    if st != OK_SUCCESS:
+        raise OkError(st, what)
+
+
+def ok_givens_unrotate(R, cs, sn):
+    """The Hessenberg matrix whose Givens reduction (rotations cs, sn) is R ((k+1) x k)."""
+    import numpy as np
+    k = R.shape[1]
+    H = np.array(R, dtype=np.float64, order="F")
+    cs, sn = np.ascontiguousarray(cs, dtype=np.float64), np.ascontiguousarray(sn, dtype=np.float64)
+    if H.shape != (k + 1, k) or cs.size < k or sn.size < k:
+        raise ValueError("R must be (k+1) x k with k rotations")
+    _host_status(load().ok_givens_unrotate(k, H.ctypes.data, k + 1, cs.ctypes.data, sn.ctypes.data),
+                 "ok_givens_unrotate rejected its arguments")
+    return np.ascontiguousarray(H)
+
+
+def ok_hessenberg_eigenvalues(H):
+    """Eigenvalues of a square upper Hessenberg matrix (complex numpy array)."""
+    import numpy as np
+    A = np.array(H, dtype=np.float64, order="F")
+    k = A.shape[0]
+    if A.ndim != 2 or A.shape[1] != k:
+        raise ValueError("H must be square")
+    re, im = np.zeros(max(k, 1)), np.zeros(max(k, 1))
+    st = load().ok_hessenberg_eigenvalues(k, A.ctypes.data if k else None, max(k, 1), re.ctypes.data,
+                                           im.ctypes.data)
+    _host_status(st, {OK_ERR_NONFINITE: "non-finite entry", OK_ERR_NOT_CONVERGED: "QR iteration did not converge"}
+                 .get(st, "invalid argument"))
+    return re[:k] + 1j * im[:k]
+
+
 def ok_launch_count() -> int:
     return load().ok_launch_count()
 
@@ -346,6 +402,12 @@ class Grid:
 
     def timestep(self, u, w, stream=None, check=True):
         return ok_timestep(self.handle, self.nv, u, w, stream, check)
+
+    def arnoldi_hessenberg(self, max_k=63, stream=None):
+        return ok_arnoldi_hessenberg(self.handle, max_k, stream)
+
+    def ritz_values(self, limit=63, stream=None):
+        return ok_ritz_values(self.handle, limit, stream)
 
 
 def version() -> str:

@@ -1436,6 +1436,54 @@ int ok_profile_read(const ok_grid* G, ok_kernel_stat* out, int max, int* count) 
   return OK_SUCCESS;
 }
 
+int ok_arnoldi_hessenberg(ok_grid* G, double* H, int ldh, int max_k, int* k, ok_stream stream) {
+  if (!G || !k || max_k < 0 || (max_k > 0 && !H) || ldh < max_k + 1) {
+    g_last_error = "NULL argument, max_k < 0 or ldh < max_k + 1";
+    return OK_ERR_INVALID_ARG;
+  }
+  return guarded([&] {
+    StreamScope sc(G, (cudaStream_t)stream);
+    double steps = 0.0;
+    CK(cudaMemcpyAsync(&steps, ks_nsteps_ptr(G->ks), sizeof(double), cudaMemcpyDeviceToHost, G->s));
+    CK(cudaStreamSynchronize(G->s));
+    // the leading columns of Hbar are themselves the Arnoldi matrix of fewer steps
+    const int kk = std::max(0, std::min({(int)steps, max_k, KRYLOV_MAX - 1}));
+    const int ld = KRYLOV_MAX + 1;
+    std::vector<double> R((size_t)ld * kk), cs(kk), sn(kk);
+    if (kk > 0) {
+      CK(cudaMemcpyAsync(R.data(), ks_H_ptr(G->ks), R.size() * sizeof(double), cudaMemcpyDeviceToHost, G->s));
+      CK(cudaMemcpyAsync(cs.data(), ks_cs_ptr(G->ks), kk * sizeof(double), cudaMemcpyDeviceToHost, G->s));
+      CK(cudaMemcpyAsync(sn.data(), ks_sn_ptr(G->ks), kk * sizeof(double), cudaMemcpyDeviceToHost, G->s));
+      CK(cudaStreamSynchronize(G->s));
+    }
+    for (int j = 0; j < kk; ++j)
+      for (int i = 0; i <= kk; ++i) H[(size_t)ldh * j + i] = i <= j ? R[(size_t)ld * j + i] : 0.0;
+    if (ok_givens_unrotate(kk, H, ldh, cs.data(), sn.data()) != OK_SUCCESS)
+      fail(OK_ERR_INVALID_ARG, "Givens restoration rejected its arguments");
+    *k = kk;
+  });
+}
+
+int ok_ritz_values(ok_grid* G, double* re, double* im, int max, int* count, ok_stream stream) {
+  if (!G || !count || max < 0 || (max > 0 && (!re || !im))) {
+    g_last_error = "NULL argument or max < 0";
+    return OK_ERR_INVALID_ARG;
+  }
+  const int cap = std::min(max, KRYLOV_MAX - 1);
+  std::vector<double> H((size_t)(cap + 1) * std::max(cap, 1));
+  int k = 0;
+  int st = ok_arnoldi_hessenberg(G, H.data(), cap + 1, cap, &k, stream);
+  if (st != OK_SUCCESS) return st;
+  st = ok_hessenberg_eigenvalues(k, H.data(), cap + 1, re, im);
+  if (st != OK_SUCCESS) {
+    g_last_error = st == OK_ERR_NONFINITE ? "non-finite Arnoldi matrix" : "QR iteration did not converge";
+    return st;
+  }
+  *count = k;
+  g_last_error.clear();
+  return OK_SUCCESS;
+}
+
 long long ok_launch_count(void) { return g_launch_count.load(); }
 
 int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream stream) {

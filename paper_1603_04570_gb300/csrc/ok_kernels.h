@@ -233,5 +233,11 @@ double* ks_h2_ptr(KrylovState* ks);
 double* ks_nw0_ptr(KrylovState* ks);
 int* ks_skip2_ptr(KrylovState* ks);
 int* ks_passes2_ptr(KrylovState* ks);
+// the Arnoldi matrix of the current cycle, reduced by its Givens rotations
+// (column j at H + (KRYLOV_MAX + 1) j), the rotations and the steps taken
+const double* ks_H_ptr(const KrylovState* ks);
+const double* ks_cs_ptr(const KrylovState* ks);
+const double* ks_sn_ptr(const KrylovState* ks);
+const double* ks_nsteps_ptr(const KrylovState* ks);
 
 }  // namespace okg

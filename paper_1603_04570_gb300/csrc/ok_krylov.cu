@@ -48,6 +48,10 @@ double* ks_h2_ptr(KrylovState* ks) { return ks->h2; }
 int* ks_skip2_ptr(KrylovState* ks) { return &ks->skip2; }
 double* ks_nw0_ptr(KrylovState* ks) { return &ks->nw0; }
 int* ks_passes2_ptr(KrylovState* ks) { return &ks->passes2; }
+const double* ks_H_ptr(const KrylovState* ks) { return ks->H; }
+const double* ks_cs_ptr(const KrylovState* ks) { return ks->cs; }
+const double* ks_sn_ptr(const KrylovState* ks) { return ks->sn; }
+const double* ks_nsteps_ptr(const KrylovState* ks) { return &ks->nsteps; }
 
 static constexpr int RT = 256;    // threads per reduction block
 static constexpr int KC = 16;     // vectors per multi-dot launch (register budget)

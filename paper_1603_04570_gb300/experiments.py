@@ -8,6 +8,15 @@ This module runs the same experiments through the library:
     python -m paper_1603_04570_gb300.experiments table1 [--sizes 32 64 128 256] [--steps 3]
     python -m paper_1603_04570_gb300.experiments table2 [--steps 3]
     python -m paper_1603_04570_gb300.experiments refine2d [--sizes 128 256 512 1024] [--steps 2]
+    python -m paper_1603_04570_gb300.experiments spectrum [--workloads 2d_n1024 3d_n128] [--steps 2]
+
+`spectrum` estimates eig(J P^{-1}) (Sec. 3: 1 and eig(S~^{-1} S)) at full
+size from the Arnoldi matrix of FGMRES cycles: after each timestep, the Ritz
+values of the step's last Newton solve, and of one solve of a seeded random
+right-hand side at the new state, against Lemma 2's interval enclosed with
+l_- >= -1 and l_+ <= 3 max u^2 - 1 (the range of 3 u_h^2 - 1, which bounds
+eig(M^{-1} M_E)).  k_R = 1, so the Schur approximation is the one the lemmas
+are about.
 
 Paper setting (Table 1): unit cube, m = 0.4, eps = 0.02, sigma = 100,
 theta = 0.5, dt = eps^2, u0 = m + cos(2 pi x) cos(2 pi y) cos(2 pi z) / 50,
@@ -78,9 +87,50 @@ def refine2d(sizes, steps, k_R, **kw):
         yield run(wl, steps, k_R, coarse_max=32 if n >= 128 else 4, **kw)
 
 
+def _ritz_record(g, wl, u, label, its):
+    import numpy as np
+    ritz = g.ritz_values()
+    c = wl.dt * wl.theta / (1 + wl.dt * wl.theta * wl.sigma)
+    lp = max(3.0 * float((u * u).max()) - 1.0, 0.0)
+    lo, hi = 0.5 - c ** 0.5 / (2 * wl.eps), 1.0 + c ** 0.5 * lp / (2 * wl.eps)
+    re = np.sort(ritz.real)
+    return dict(solve=label, gmres_its=its, ritz_count=len(ritz), ritz_re_min=float(re[0]), ritz_re_max=float(re[-1]),
+                ritz_im_max=float(np.abs(ritz.imag).max()), dist_to_1=float(np.abs(ritz - 1.0).min()),
+                lemma2_lo=lo, lemma2_hi=hi, outside=int(np.sum((ritz.real < lo) | (ritz.real >= hi))),
+                smallest=[round(float(x), 5) for x in re[:4]], largest=[round(float(x), 5) for x in re[-3:]])
+
+
+def spectrum(names, steps, precision=OK_MIXED, restart=60):
+    """Ritz values of eig(J P^{-1}) after each of `steps` timesteps."""
+    import numpy as np
+    import torch
+    for name in names:
+        wl = oi.PAPER_3D if name == "paper_3d" else oi.WORKLOADS[name]
+        if name == "paper_3d":
+            wl = oi.scaled(wl, 128)
+        o = dict(restart=restart, gmres_rtol=wl.gmres_rtol, k_R=1, precision=precision,
+                 newton_atol=wl.newton_tols[0], newton_rtol=wl.newton_tols[1])
+        if wl.dim == 2 and wl.n >= 128:
+            o["coarse_max"] = 32
+        with Grid(wl.dim, wl.n, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, **o) as g:
+            u = torch.from_numpy(oi.initial_u(wl)).cuda()
+            w = torch.empty_like(u)
+            g.init_w(u, w)
+            f = torch.from_numpy(np.random.default_rng(7).standard_normal(wl.dofs)).cuda()
+            x = torch.empty_like(f)
+            for step in range(1, steps + 1):
+                info = g.timestep(u, w)
+                rec = dict(workload=wl.name, dofs=wl.dofs, step=step, newton_steps=info.newton_its,
+                           precision="fp64" if precision == OK_FP64 else "mixed")
+                yield {**rec, **_ritz_record(g, wl, u, "newton", info.last_gmres_its)}
+                si = g.solve_linear(u, f, x, check=False)
+                yield {**rec, **_ritz_record(g, wl, u, "random_rhs", si.gmres_its)}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("experiment", choices=["table1", "table2", "refine2d"])
+    ap.add_argument("experiment", choices=["table1", "table2", "refine2d", "spectrum"])
+    ap.add_argument("--workloads", nargs="*", default=None, help="spectrum: 2d_n1024, 3d_n128, paper_3d, ...")
     ap.add_argument("--sizes", type=int, nargs="*", default=None)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--k-r", type=int, default=None, help="1: S~^{-1}; 2: two Richardson steps (paper)")
@@ -93,6 +143,8 @@ def main(argv=None):
         rows = table1(a.sizes or [32, 64, 128, 256], a.steps, a.k_r or 2, precision=prec, gmres_rtol=a.gmres_rtol)
     elif a.experiment == "table2":
         rows = table2(a.steps, a.k_r or 2, precision=prec, gmres_rtol=a.gmres_rtol)
+    elif a.experiment == "spectrum":
+        rows = spectrum(a.workloads or ["2d_n1024", "paper_3d"], a.steps, precision=prec)
     else:
         rows = refine2d(a.sizes or [128, 256, 512, 1024], a.steps, a.k_r or 1, precision=prec,
                         gmres_rtol=a.gmres_rtol)
@@ -100,7 +152,15 @@ def main(argv=None):
     for r in rows:
         out.append(r)
         print(json.dumps(r), flush=True)
-    if a.markdown:
+    if a.markdown and a.experiment == "spectrum":
+        print("\n| workload | step | solve | FGMRES its | Ritz Re min | Ritz Re max | max |Im| | dist to 1 | "
+              "Lemma 2 enclosure | outside |")
+        print("|---|---|---|---|---|---|---|---|---|---|")
+        for r in out:
+            print(f"| {r['workload']} | {r['step']} | {r['solve']} | {r['gmres_its']} | {r['ritz_re_min']:.4f} | "
+                  f"{r['ritz_re_max']:.4f} | {r['ritz_im_max']:.2e} | {r['dist_to_1']:.1e} | "
+                  f"[{r['lemma2_lo']:.4f}, {r['lemma2_hi']:.4f}) | {r['outside']} |")
+    elif a.markdown:
         print("\n| n | DoF | eps | dt | k_R | rtol | Newton steps | FGMRES its | its / Newton |")
         print("|---|---|---|---|---|---|---|---|---|")
         for r in out:

@@ -158,3 +158,42 @@ def test_cube_512_timestep_properties():
     per512 = info.gmres_its / info.newton_its
     per128 = i128.gmres_its / i128.newton_its
     assert per512 <= 1.5 * per128 + 2, (per512, per128)
+
+
+def test_ritz_values_at_1024_within_the_lemma_2_enclosure():
+    """Spectral diagnostics at 2.1M DoF (2D 1024^2, the benchmark's
+    parameters and u0, float32 preconditioner): one FGMRES cycle of a seeded
+    right-hand side; the Arnoldi matrix's least-squares residual is the
+    solve's true residual.  The smallest Ritz value estimates the bottom of
+    eig(S~^{-1} S) and must respect Lemma 2's lower end, enclosed with
+    l_- >= -1 (eig(M^{-1} M_E) lies between the extremes of 3 u_h^2 - 1);
+    0.02 allows for the inexact A~^{-1} and S_hat^{-1}.  Near the eigenvalue 1
+    of Sec. 3 the Ritz values spread into the field of values: J P^{-1} is
+    far from normal through its A^{-1} B = c M^{-1} K block, of M-norm
+    28.1 c h^{-2} (294 here, 4.6 at 128^2), so they come in complex pairs within a few
+    1e-2 of 1 (measured: up to 1.022, |Im| 0.046, nearest 0.0105 away; the
+    oracle gives 1.0015 at 128^2), bounded here by 0.1 and 0.05."""
+    wl = oi.LARGE_2D
+    nv = wl.n_vertices
+    u = oi.initial_u(wl)
+    f = np.random.default_rng(7).standard_normal(2 * nv)
+    with ok.Grid(wl.dim, wl.n, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, restart=60, gmres_rtol=1e-8,
+                 precision=ok.OK_MIXED, coarse_max=32) as g:
+        x = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        info = g.solve_linear(torch.from_numpy(u).cuda(), torch.from_numpy(f).cuda(), x)
+        H = g.arnoldi_hessenberg()
+        ritz = g.ritz_values()
+    m = H.shape[1]
+    assert m == info.gmres_its and 4 <= m < 60
+    e1 = np.zeros(m + 1)
+    e1[0] = np.linalg.norm(f)
+    y = np.linalg.lstsq(H, e1, rcond=None)[0]
+    est = np.linalg.norm(e1 - H @ y) / np.linalg.norm(f)
+    assert abs(est - info.rel_resid) <= 1e-2 * info.rel_resid + 1e-14
+    c = wl.dt * wl.theta / (1 + wl.dt * wl.theta * wl.sigma)
+    lo = 0.5 - np.sqrt(c) / (2 * wl.eps)
+    hi = 1.0 + np.sqrt(c) * max(3 * np.max(u ** 2) - 1, 0.0) / (2 * wl.eps)
+    assert np.abs(ritz.imag).max() <= 0.1
+    assert lo - 0.02 <= ritz.real.min() and ritz.real.max() <= hi + 0.1
+    assert np.abs(ritz - 1.0).min() <= 0.05
+

@@ -20,7 +20,7 @@ torch = pytest.importorskip("torch")
 import ok_inputs as oi
 import paper_1603_04570_gb300 as ok
 from oracle.fem import Mesh, Params, System
-from oracle.solvers import Options, Preconditioner, timestep
+from oracle.solvers import Options, Preconditioner, fgmres, timestep
 
 pytestmark = pytest.mark.gpu
 
@@ -393,6 +393,15 @@ def test_experiments_module_runs():
     assert [r["n"] for r in rows] == [8, 16]
     for r in rows:
         assert r["newton_steps"] >= 1 and 1 <= r["its_per_newton"] <= 30
+    # spectral diagnostics on the 32^2 workload: Ritz values of the Newton solve
+    # and of a random right-hand side inside Lemma 2's enclosure (widened for
+    # the inexact preconditioner), the eigenvalue 1 found
+    rows = list(experiments.spectrum(["2d_n32"], steps=1))
+    assert [r["solve"] for r in rows] == ["newton", "random_rhs"]
+    for r in rows:
+        assert r["ritz_count"] >= 1 and r["ritz_im_max"] <= 0.1
+        assert r["lemma2_lo"] - 0.05 <= r["ritz_re_min"] and r["ritz_re_max"] <= r["lemma2_hi"] + 0.05
+    assert rows[1]["ritz_count"] >= 4 and rows[1]["dist_to_1"] <= 0.01
 
 
 
@@ -447,3 +456,75 @@ def test_serving_admits_by_memory_budget():
     reqs = [dict(mix[0], u=dev(mix[0]["u0"]), w=torch.zeros(len(mix[0]["u0"]), dtype=torch.float64, device="cuda"))]
     st, res, info = ok.ok_serve(reqs, 1, footprint // 2)
     assert st == ok.OK_ERR_NOMEM and res[0].status == ok.OK_ERR_NOMEM and info.failed == 1
+
+
+def _match(a, b):
+    """Largest distance of an optimal one-to-one pairing of two eigenvalue sets."""
+    from scipy.optimize import linear_sum_assignment
+    C = np.abs(np.asarray(a)[:, None] - np.asarray(b)[None, :])
+    r, c = linear_sum_assignment(C)
+    return C[r, c].max()
+
+
+def _lsq_resid(H, beta):
+    """min_y || beta e_1 - Hbar y || (the FGMRES residual of a cycle from x_0 = 0)."""
+    e1 = np.zeros(H.shape[0])
+    e1[0] = beta
+    y = np.linalg.lstsq(H, e1, rcond=None)[0]
+    return np.linalg.norm(e1 - H @ y)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 12), (2, 17), (3, 6)])
+@pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
+def test_arnoldi_matrix_and_ritz_values_parity(dim, n, precision):
+    """Spectral diagnostics (Sec. 3): the Arnoldi matrix of the solve's FGMRES
+    cycle, restored on the host from the device's Givens-reduced form, against
+    the oracle's recorded cycle for the same J, P and f (the oracle runs
+    modified, the GPU here two-pass classical Gram--Schmidt: equal up to the
+    basis' loss of orthogonality); its Ritz values from the library's QR
+    iteration against LAPACK on the same matrix; its least-squares residual
+    against the solve's true residual."""
+    sysm, p, rng = make(dim, n, seed=21, dt=1e-4)
+    nv = sysm.mesh.nv
+    u = rng.uniform(-1.0, 1.0, nv)
+    f = rng.standard_normal(2 * nv)
+    J = sysm.jacobian(u)
+    P = Preconditioner(sysm, u, mode="inexact", q_A=10, n_V=3, k_R=1, nu_pre=2, nu_post=2)
+    cycles = []
+    fgmres(lambda z: J @ z, P.apply, f, restart=40, rtol=1e-8, cycles=cycles)
+    assert len(cycles) == 1
+    Href = cycles[0]["H"]
+    with ok.Grid(dim, n, **p, n_V=3, precision=precision, restart=40, gmres_rtol=1e-8, reorth=1) as g:
+        assert g.arnoldi_hessenberg().shape == (1, 0) and g.ritz_values().size == 0   # no cycle yet
+        x = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        info = g.solve_linear(dev(u), dev(f), x)
+        H = g.arnoldi_hessenberg()
+        ritz = g.ritz_values()
+        H5 = g.arnoldi_hessenberg(max_k=5)
+        ritz5 = g.ritz_values(limit=5)
+    m = H.shape[1]
+    assert H.shape == (m + 1, m) and m == info.gmres_its == info.last_gmres_its   # one cycle
+    assert abs(m - Href.shape[1]) <= 1
+    k = min(m, Href.shape[1])
+    scale = np.abs(Href).max()
+    if precision == ok.OK_FP64:
+        k0 = min(k, 6)
+        assert np.abs(H[:k0 + 1, :k0] - Href[:k0 + 1, :k0]).max() <= 1e-9 * scale
+        assert np.abs(H[:k + 1, :k] - Href[:k + 1, :k]).max() <= 1e-6 * scale
+    else:
+        assert np.abs(H[:k + 1, :k] - Href[:k + 1, :k]).max() <= 1e-3 * scale
+    assert np.all(np.tril(H, -2) == 0) and np.all(np.diag(H, -1) > 0)
+    assert np.array_equal(H5, H[:6, :5])
+    # Ritz values: each an exact eigenvalue of a matrix within 1e-12 |H| of H_m
+    # (backward error; the forward error of clustered, non-normal H can be
+    # far larger), summing to the trace, and close to LAPACK's
+    for r, k_ in ((ritz, m), (ritz5, 5)):
+        Hk = H[:k_, :k_]
+        assert len(r) == k_
+        for lam in r:
+            assert np.linalg.svd(Hk - lam * np.eye(k_), compute_uv=False)[-1] <= 1e-12 * np.abs(H).max() * k_
+        assert abs(r.sum() - np.trace(Hk)) <= 1e-12 * np.abs(H).max() * k_
+        assert _match(r, np.linalg.eigvals(Hk)) <= 1e-6 * np.abs(H).max()
+    est = _lsq_resid(H, np.linalg.norm(f)) / np.linalg.norm(f)
+    assert abs(est - info.rel_resid) <= 1e-2 * info.rel_resid + 1e-14
+
