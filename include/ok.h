@@ -60,7 +60,9 @@ enum ok_status {
   OK_ERR_CUDA = 3,            /* a CUDA runtime call failed                  */
   OK_ERR_NOT_CONVERGED = 4,   /* Newton or GMRES hit its iteration cap       */
   OK_ERR_NONFINITE = 5,       /* NaN/Inf in an input or during the solve     */
-  OK_ERR_TIMEOUT = 6          /* a bounded device-side wait gave up          */
+  OK_ERR_TIMEOUT = 6,         /* a bounded device-side wait gave up          */
+  OK_ERR_INTERNAL = 7         /* an unexpected host-side failure (message in
+                                 ok_last_error); no exception leaves the ABI  */
 };
 
 enum ok_precision {
@@ -295,7 +297,7 @@ int ok_profile_read(const ok_grid* g, ok_kernel_stat* out, int max, int* count);
  *   map rows (i, i+1) as (a, b) -> (cs[i] a + sn[i] b, -sn[i] a + cs[i] b);
  *   overwrites it with that Hessenberg matrix (rows j+2..k of column j zeroed).
  * ok_hessenberg_eigenvalues: host only, no GPU needed.  Eigenvalues of the
- *   k x k upper Hessenberg matrix H (column-major, ldh >= k; entries below
+ *   k x k upper Hessenberg matrix H (0 <= k <= 4096; column-major, ldh >= k; entries below
  *   the first subdiagonal are ignored) by the implicit double-shift QR
  *   iteration (Francis 1961; Golub and Van Loan, Sec. 7.5), into re/im
  *   (length k, in deflation order, complex pairs adjacent).

@@ -17,10 +17,10 @@ from ctypes import POINTER, Structure, byref, c_char_p, c_double, c_int, c_longl
 from . import _build
 
 OK_SUCCESS, OK_ERR_INVALID_ARG, OK_ERR_NOMEM, OK_ERR_CUDA = 0, 1, 2, 3
-OK_ERR_NOT_CONVERGED, OK_ERR_NONFINITE, OK_ERR_TIMEOUT = 4, 5, 6
+OK_ERR_NOT_CONVERGED, OK_ERR_NONFINITE, OK_ERR_TIMEOUT, OK_ERR_INTERNAL = 4, 5, 6, 7
 OK_FP64, OK_MIXED, OK_MIXED_HALF = 0, 1, 2
 STATUS_NAMES = {0: "OK_SUCCESS", 1: "OK_ERR_INVALID_ARG", 2: "OK_ERR_NOMEM", 3: "OK_ERR_CUDA",
-                4: "OK_ERR_NOT_CONVERGED", 5: "OK_ERR_NONFINITE", 6: "OK_ERR_TIMEOUT"}
+                4: "OK_ERR_NOT_CONVERGED", 5: "OK_ERR_NONFINITE", 6: "OK_ERR_TIMEOUT", 7: "OK_ERR_INTERNAL"}
 
 
 class Params(Structure):

@@ -60,6 +60,12 @@ int guarded(F&& f) {
   } catch (const std::bad_alloc&) {
     g_last_error = "host allocation failed";
     return OK_ERR_NOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = std::string("internal error: ") + e.what();
+    return OK_ERR_INTERNAL;
+  } catch (...) {
+    g_last_error = "internal error";
+    return OK_ERR_INTERNAL;
   }
 }
 
@@ -1476,7 +1482,9 @@ int ok_ritz_values(ok_grid* G, double* re, double* im, int max, int* count, ok_s
   if (st != OK_SUCCESS) return st;
   st = ok_hessenberg_eigenvalues(k, H.data(), cap + 1, re, im);
   if (st != OK_SUCCESS) {
-    g_last_error = st == OK_ERR_NONFINITE ? "non-finite Arnoldi matrix" : "QR iteration did not converge";
+    g_last_error = st == OK_ERR_NONFINITE ? "non-finite Arnoldi matrix"
+                   : st == OK_ERR_NOMEM    ? "host allocation failed"
+                                           : "QR iteration did not converge";
     return st;
   }
   *count = k;

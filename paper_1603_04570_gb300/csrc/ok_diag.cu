@@ -63,6 +63,8 @@ bool house3(double x, double y, double z, double& v1, double& v2, double& tau) {
   return true;
 }
 
+int hessenberg_qr(int k, const double* H, int ldh, double* re, double* im);
+
 }  // namespace
 
 extern "C" {
@@ -83,7 +85,19 @@ int ok_givens_unrotate(int k, double* H, int ldh, const double* cs, const double
 }
 
 int ok_hessenberg_eigenvalues(int k, const double* H, int ldh, double* re, double* im) {
-  if (k < 0 || (k > 0 && (!H || !re || !im)) || ldh < k) return OK_ERR_INVALID_ARG;
+  if (k < 0 || k > 4096 || (k > 0 && (!H || !re || !im)) || ldh < k) return OK_ERR_INVALID_ARG;
+  try {
+    return hessenberg_qr(k, H, ldh, re, im);      // a dense k x k working copy
+  } catch (...) {
+    return OK_ERR_NOMEM;
+  }
+}
+
+}  // extern "C"
+
+namespace {
+
+int hessenberg_qr(int k, const double* H, int ldh, double* re, double* im) {
   Dense A(k);
   double amax = 0.0;
   for (int j = 0; j < k; ++j)
@@ -196,4 +210,4 @@ int ok_hessenberg_eigenvalues(int k, const double* H, int ldh, double* re, doubl
   return OK_SUCCESS;
 }
 
-}  // extern "C"
+}  // namespace

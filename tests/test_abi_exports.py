@@ -77,6 +77,13 @@ def test_too_large_coarse_level_rejected():
     assert e.value.status == ok.OK_ERR_INVALID_ARG and "coarsest" in str(e.value)
 
 
+def test_status_codes_match_the_header():
+    text = open(os.path.join(ROOT, "include", "ok.h")).read()
+    codes = dict((name, int(v)) for name, v in re.findall(r"^\s*(OK_(?:SUCCESS|ERR_\w+))\s*=\s*(\d+)", text, re.M))
+    assert codes == {name: code for code, name in ok.STATUS_NAMES.items()}
+    assert ok.OK_ERR_INTERNAL == 7
+
+
 def test_serving_structs_match_the_header():
     assert ctypes.sizeof(ok.ServeRequest) == 224 and ok.ServeRequest.arrival.offset == 80
     assert ok.ServeRequest.device_bytes.offset == 120

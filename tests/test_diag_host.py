@@ -124,6 +124,8 @@ def test_invalid_sizes_are_rejected():
     assert lib.ok_hessenberg_eigenvalues(-1, p, 4, p, p) == ok.OK_ERR_INVALID_ARG
     assert lib.ok_hessenberg_eigenvalues(3, p, 2, p, p) == ok.OK_ERR_INVALID_ARG       # ldh < k
     assert lib.ok_hessenberg_eigenvalues(2, None, 2, p, p) == ok.OK_ERR_INVALID_ARG
+    assert lib.ok_hessenberg_eigenvalues(4097, p, 4097, p, p) == ok.OK_ERR_INVALID_ARG    # k cap
+    assert lib.ok_hessenberg_eigenvalues(1_500_000_000, p, 1_500_000_000, p, p) == ok.OK_ERR_INVALID_ARG
     assert lib.ok_givens_unrotate(3, p, 3, p, p) == ok.OK_ERR_INVALID_ARG              # ldh < k + 1
     assert lib.ok_givens_unrotate(-1, p, 4, p, p) == ok.OK_ERR_INVALID_ARG
     assert lib.ok_givens_unrotate(0, None, 1, None, None) == ok.OK_SUCCESS
