@@ -24,6 +24,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -321,6 +322,25 @@ def e2e_run(ok, torch, res, wl, steps, flush):
             "api": "ok_timestep with pinned host arrays"}
 
 
+def host_cpu():
+    """The host's CPU model (x86 "model name"; on Arm the implementer/part codes) and core count."""
+    model, part = None, None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                key = key.strip().lower()
+                if key == "model name" and not model:
+                    model = val.strip()
+                elif key == "cpu part" and not part:
+                    part = val.strip()
+    except OSError:
+        pass
+    if not model:
+        model = platform.machine() + (f" (CPU part {part})" if part else "")
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
 def cpu_baseline(wl, iters=3):
     """The oracle's preconditioned FGMRES on the same workload: first `iters`
     iterations of the first Newton linear solve (plain numpy/scipy, 1 thread)."""
@@ -338,7 +358,7 @@ def cpu_baseline(wl, iters=3):
     return {"value": 2 * sysm.mesh.nv * its / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {its} FGMRES iterations of the first Newton solve of {wl.name} "
                       f"({2 * sysm.mesh.nv} DoF), scipy CSR operators, {dt:.1f} s",
-            "seconds": dt}
+            "seconds": dt, **host_cpu()}
 
 
 def main_ok(args):
@@ -466,7 +486,8 @@ def main_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "dim": wl.dim, "n": wl.n, "dofs": dof, "restart": wl.restart,
                    "gmres_rtol": wl.gmres_rtol},
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample,
+                         **host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
