@@ -10,7 +10,12 @@ block (ragged tails).  Tolerances:
     contraction, so rounding does not grow);
   * mixed preconditioner: 2e-4 relative (float32 arithmetic);
   * timesteps: 1e-10 (FP64) and 1e-8 (mixed) relative in the 2-norm after
-    every step, the targets of the method.
+    every step, the targets of the method;
+  * Arnoldi matrix of an FGMRES cycle: FP64 1e-9 on the first six columns and
+    1e-6 on all (the oracle orthogonalises with modified, the GPU with
+    two-pass classical Gram--Schmidt: they differ by the basis' loss of
+    orthogonality), mixed 1e-3, relative to the largest entry; Ritz values by
+    backward error 1e-12 |H| k.
 """
 import numpy as np
 import pytest
