@@ -93,3 +93,35 @@ def test_serving_structs_match_the_header():
 def test_serve_rejects_invalid_arguments_on_host():
     st, _, _ = ok.ok_serve([], max_inflight=0, mem_budget=1 << 30)
     assert st == ok.OK_ERR_INVALID_ARG
+
+
+def test_binding_rejects_badly_typed_arrays():
+    """Argument marshalling: float64, contiguous, of the stated size."""
+    import numpy as np
+    assert ok._ptr(None) is None
+    a = np.zeros(8)
+    assert ok._ptr(a, 8) == a.ctypes.data
+    with pytest.raises(TypeError):
+        ok._ptr(np.zeros(8, dtype=np.float32), 8, "u")
+    with pytest.raises(TypeError):
+        ok._ptr(np.zeros(16)[::2], 8, "u")                      # not contiguous
+    with pytest.raises(ValueError):
+        ok._ptr(np.zeros(7), 8, "u")
+    with pytest.raises(TypeError):
+        ok._ptr([0.0] * 8, 8, "u")
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(8, dtype=torch.float64)
+    assert ok._ptr(t, 8) == t.data_ptr()
+    with pytest.raises(TypeError):
+        ok._ptr(torch.zeros(8, dtype=torch.float32), 8, "u")
+    with pytest.raises(ValueError):
+        ok._ptr(torch.zeros(9, dtype=torch.float64), 8, "u")
+
+
+def test_host_diagnostic_wrappers_validate_shapes():
+    import numpy as np
+    with pytest.raises(ValueError):
+        ok.ok_hessenberg_eigenvalues(np.zeros((3, 4)))
+    with pytest.raises(ValueError):
+        ok.ok_givens_unrotate(np.zeros((3, 3)), np.zeros(3), np.zeros(3))   # R must be (k+1) x k
+    assert ok.ok_givens_unrotate(np.zeros((1, 0)), np.zeros(0), np.zeros(0)).shape == (1, 0)
