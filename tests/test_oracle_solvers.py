@@ -14,7 +14,11 @@ Checks against closed forms and the paper's statements:
   * [A 0; C S~] applied to the exact-mode preconditioner output returns v;
   * FGMRES agrees with dense LU of J (Sec. 2, eqn newton);
   * a timestep keeps the mean law (u_bar - m)(1 + dt th sig) = (u_bar_n - m)(1 - dt (1-th) sig)
-    and maps a constant state to its closed form.
+    and maps a constant state to its closed form;
+  * a small discrete eigenmode K v = lam M v is multiplied per timestep by the
+    theta-method's amplification factor (1 - (1-th) dt mu)/(1 + th dt mu),
+    mu = lam (eps^2 lam - 1) + sig, which pins the explicit (1 - theta) part of
+    the residual (invisible to the mean law and the constant state, since K 1 = 0).
 """
 import numpy as np
 import pytest
@@ -311,3 +315,64 @@ def test_timestep_matches_direct_newton():
     b = timestep(sysm, u0, w0, Options(linear="direct", newton_atol=1e-10, newton_extra=1))
     for x, y in zip(a[:2], b[:2]):
         assert np.linalg.norm(x - y) <= 1e-12 * np.linalg.norm(y)
+
+
+# --------------------------------------------------------------------------
+# the theta-method's explicit part (Sec. 2: theta-method in time for eqn oka)
+# --------------------------------------------------------------------------
+def _generalised_mode(sysm, target):
+    """A discrete eigenpair K v = lam M v (dense, tiny grids) with lam near `target`."""
+    lam, Q = sla.eigh(sysm.K.toarray(), sysm.M.toarray())
+    k = int(np.argmin(np.abs(lam - target)))
+    v = Q[:, k]
+    return lam[k], v / np.abs(v).max()
+
+
+@pytest.mark.parametrize("dim,n,theta", [(2, 6, 0.5), (2, 6, 1.0), (2, 6, 0.3), (3, 3, 0.5)])
+def test_timestep_amplifies_an_eigenmode_by_the_theta_method_factor(dim, n, theta):
+    """Small-amplitude eigenmode through two whole timesteps.
+
+    For m = 0 and |u| << 1, N(u) = -M u + O(|u|^3), so with K v = lam M v the
+    semi-discrete system reduces on span{v} to the scalar ODE a' = -mu a with
+    w = (eps^2 lam - 1) a and mu = lam (eps^2 lam - 1) + sigma.  The
+    theta-method maps a_n to R a_n with the textbook amplification factor
+        R = (1 - (1 - theta) dt mu) / (1 + theta dt mu).
+    Both the implicit and the explicit (weight 1 - theta) parts of eqn oka
+    enter R; a dropped or sign-flipped K w_n or sigma M (u_n - m) term in the
+    residual changes it by O(dt lam b) or O(dt sigma), far above the O(a^2)
+    linearisation error checked here.
+    """
+    eps, sigma, dt = 0.2, 10.0, 1e-3
+    sysm = System(Mesh(dim, n), Params(eps, sigma, 0.0, theta, dt))
+    lam, v = _generalised_mode(sysm, 120.0)
+    mu = lam * (eps ** 2 * lam - 1.0) + sigma
+    R = (1.0 - (1.0 - theta) * dt * mu) / (1.0 + theta * dt * mu)
+    assert abs(R) > 0.05 and abs(R - 1.0) > 0.05          # the step visibly changes the mode
+    a0 = 1e-5
+    u, w = a0 * v, (eps ** 2 * lam - 1.0) * a0 * v
+    opts = Options(linear="direct", newton_atol=0.0, newton_rtol=1e-11, newton_extra=1)
+    a = a0
+    for _ in range(2):
+        u, w, info = timestep(sysm, u, w, opts)
+        assert info["converged"]
+        a = R * a
+        assert np.linalg.norm(u - a * v) <= 1e-7 * abs(a) * np.linalg.norm(v)
+        assert np.linalg.norm(w - (eps ** 2 * lam - 1.0) * a * v) <= 1e-7 * abs(a) * np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("theta", [0.25, 0.5, 1.0])
+def test_residual_at_the_previous_state_is_the_full_explicit_step(theta):
+    """At (u, w) = (u_n, w_n) the theta weights add up to one, so for every
+    theta  F1 = dt [K w_n + sigma M (u_n - m)]  and  F2 = M w_n - eps^2 K u_n - N(u_n)."""
+    rng = np.random.default_rng(21)
+    p = Params(0.07, 40.0, 0.15, theta, 3e-3)
+    sysm = System(Mesh(2, 5), p)
+    nv = sysm.mesh.nv
+    un, wn = rng.uniform(-1, 1, nv), rng.uniform(-1, 1, nv)
+    F = sysm.residual(un, wn, un, wn)
+    ref_theta1 = System(Mesh(2, 5), Params(p.eps, p.sigma, p.m, 1.0, p.dt)).residual(un, wn, un, wn)
+    assert np.abs(F - ref_theta1).max() <= 1e-14 * np.abs(F).max()
+    # and the theta = 1 value is independent of (u_n, w_n) beyond the M (u - u_n) term:
+    ua, wa = rng.uniform(-1, 1, nv), rng.uniform(-1, 1, nv)
+    F1 = System(Mesh(2, 5), Params(p.eps, p.sigma, p.m, 1.0, p.dt)).residual(ua, wa, un, wn)[:nv]
+    assert np.abs(F1 - (F[:nv] + sysm.M @ (un - ua))).max() <= 1e-14 * np.abs(F1).max()
