@@ -9,8 +9,14 @@ p50/p99 latency of the timesteps and of the Newton linear solves.
 Workload (default): the unit square cut into 1024 x 1024 squares, each split
 into two P1 triangles (1,050,625 vertices, 2,101,250 DoF); eps 0.02,
 sigma 200, m 0.1, theta 0.5, dt 2e-5; u0 = m + 0.05 N(0,1) (seeded); FGMRES(30)
-to 1e-8; 9 multigrid levels.  A "step" is one theta-method timestep (Newton
-to its stop test, every Newton step one preconditioned FGMRES solve).
+to 1e-8; classical Gram--Schmidt with reorthogonalisation (CGS2); six
+multigrid levels (1024^2 down to a dense 33^2 coarsest solve).  A "step" is
+one theta-method timestep (Newton to its stop test, every Newton step one
+preconditioned FGMRES solve).  Beside the headline the JSON line carries the
+float64 path, one-pass Gram--Schmidt, the nine-level hierarchy (down to 5^2),
+the 3D 128^3 workload (mixed and float64) and the 3D 512^3 workload's
+finest-level kernels (working set far above L2), and the oracle timed per
+Newton step on the host.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ok|reference]
 Under torchrun each rank runs an independent replica (the method has no
@@ -54,6 +60,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer run (short profiling runs)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the one-pass Gram--Schmidt, nine-level and 3D runs beside the headline")
     ap.add_argument("--profile-out", default=None, help="write per-kernel samples as JSON")
     ap.add_argument("--opt", action="append", default=[], metavar="KEY=INT",
                     help="override an integer ok_opts field of the timed runs (e.g. use_pdl=0)")
@@ -171,16 +179,27 @@ def kernel_model(tag, wl, precision):
     if tag in ("mg_smooth_l0", "cheb_mass_step"):
         return nv * 6 * bp, nv * 2 * (noff + 4), "hbm"
     nc = (wl.n // 2 + 1) ** d
-    if tag == "mg_tile_pre_l0":
-        # first pre-smoothing launch of a solve starts from x = 0: reads b, writes x and P^T r
-        return nv * 2 * bp + nc * bp, nv * 2 * (3 * noff + 12) + nc * 2 * noff, "hbm"
-    if tag == "mg_tile_post_l0":
-        # reads x, b and the coarse x; writes x
-        return nv * 3 * bp + nc * bp, nv * 2 * (2 * noff + 12), "hbm"
+    if tag in ("mg_tile_pre_l0", "mg_tile_post_l0"):
+        # the multigrid's per-unit figure: 5 vectors per smoothing step (nu = 2
+        # per launch) plus half of the level's 5 transfer/residual vectors
+        # (restriction in the pre launch, prolongation in the post launch)
+        return nv * 12.5 * bp, nv * 2 * (3 * noff + 12) + nc * 2 * noff, "hbm"
     if tag == "tile_mass_cstep":
         # reads v (2 float64 fields) and the C store (1 + NPOS values), writes z1 and t
         return nv * (16 + bp * (npos + 1) + bz + bp), nv * 2 * (9 * (noff + 4) + 2 * npos + 2), "hbm"
     return None, None, None
+
+
+def min_bytes(tag, wl, precision):
+    """Bytes a fused launch cannot avoid (its inputs and outputs once), for comparison."""
+    nv, d = wl.n_vertices, wl.dim
+    bp = 4 if precision == "mixed" else 8
+    nc = (wl.n // 2 + 1) ** d
+    if tag == "mg_tile_pre_l0":
+        return nv * 2 * bp + nc * bp          # b in, x out, P^T r out
+    if tag == "mg_tile_post_l0":
+        return nv * 3 * bp + nc * bp          # x, b, coarse x in, x out
+    return None
 
 
 def launches_per_iteration(tag, opts):
@@ -341,24 +360,124 @@ def host_cpu():
     return {"cpu_model": model, "nproc": os.cpu_count()}
 
 
-def cpu_baseline(wl, iters=3):
-    """The oracle's preconditioned FGMRES on the same workload: first `iters`
-    iterations of the first Newton linear solve (plain numpy/scipy, 1 thread)."""
+def cpu_baseline(wl):
+    """The oracle timed per Newton step on the host (plain numpy/scipy, one
+    thread: scipy's CSR products are single-threaded, the only dense work is
+    the coarsest level): the 32^2 workload's five whole timesteps (FGMRES(30)
+    to 1e-10) and the first Newton step of the timed workload (its FGMRES
+    solve to the workload's tolerance, with the same multigrid hierarchy;
+    the oracle assembles J and builds its preconditioner inside the step)."""
     from oracle.fem import Mesh, Params, System
-    from oracle.solvers import Preconditioner, fgmres
+    from oracle.solvers import Options, linear_solve, timestep
+    sm = oi.SMALL_2D
+    sysm = System(Mesh(sm.dim, sm.n), Params(sm.eps, sm.sigma, sm.m, sm.theta, sm.dt))
+    u = oi.initial_u(sm)
+    w = sysm.initial_w(u)
+    atol, rtol = sm.newton_tols
+    opts = Options(restart=sm.restart, gmres_rtol=sm.gmres_rtol, newton_atol=atol, newton_rtol=rtol)
+    t0 = time.perf_counter()
+    newton_s, its_s = 0, 0
+    for _ in range(sm.steps):
+        u, w, info = timestep(sysm, u, w, opts)
+        newton_s += info["newton"]
+        its_s += sum(info["gmres"])
+    t_small = time.perf_counter() - t0
     sysm = System(Mesh(wl.dim, wl.n), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
     u0 = oi.initial_u(wl)
-    w0 = sysm.initial_w(u0)
+    w0 = sysm.initial_w(u0, solver="chebyshev")
     F = sysm.residual(u0, w0, u0, w0)
-    J = sysm.jacobian(u0)
-    P = Preconditioner(sysm, u0, mode="inexact", q_A=10, n_V=5, k_R=1)
     t0 = time.perf_counter()
-    _, its, _ = fgmres(lambda z: J @ z, P.apply, -F, restart=wl.restart, rtol=wl.gmres_rtol, max_its=iters)
+    _, its, rel = linear_solve(sysm, u0, -F, Options(restart=wl.restart, gmres_rtol=wl.gmres_rtol,
+                                                     coarse_max=32 if wl.dim == 2 else 4))
     dt = time.perf_counter() - t0
-    return {"value": 2 * sysm.mesh.nv * its / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {its} FGMRES iterations of the first Newton solve of {wl.name} "
-                      f"({2 * sysm.mesh.nv} DoF), scipy CSR operators, {dt:.1f} s",
-            "seconds": dt, **host_cpu()}
+    dof = 2 * sysm.mesh.nv
+    return {"value": dof * its / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the first Newton step of {wl.name} ({dof} DoF): Jacobian assembly, preconditioner "
+                      f"setup and FGMRES to {wl.gmres_rtol:g} ({its} iterations), {dt:.1f} s; "
+                      f"value = DoF x iterations / that time",
+            "newton_step_s": dt, "gmres_its": its, "rel_resid": rel,
+            "small_2d_n32": {"timesteps": sm.steps, "newton_its": newton_s, "gmres_its": its_s,
+                             "seconds": t_small, "s_per_newton_step": t_small / max(newton_s, 1)},
+            **host_cpu()}
+
+
+def roofline_of(res, wl, precision, total_ms):
+    """Roofline of the sampled kernel class with the largest estimated share."""
+    peaks, peak_kind = measured_peaks()
+    best = None
+    for tag, (n, tot) in res["prof"].items():
+        lpi = launches_per_iteration(tag, res["opts"])
+        if n == 0 or lpi is None or kernel_model(tag, wl, precision)[0] is None:
+            continue
+        share = tot / n * lpi * res["its"]
+        if best is None or share > best[1]:
+            best = (tag, share, tot / n, n)
+    if not best:
+        return None
+    tag, share, avg_ms, n = best
+    by, fl, bound = kernel_model(tag, wl, precision)
+    if bound == "hbm":
+        ach = by / (avg_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        unit = "GB/s"
+    else:
+        ach = fl / (avg_ms * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS
+        unit = "TFLOP/s"
+    mb = min_bytes(tag, wl, precision)
+    vec_mb = wl.n_vertices * (4 if precision == "mixed" else 8) / 1e6
+    return {"kernel": tag, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+            "traffic": recorded_traffic(tag, wl.name, precision), "algorithmic_bytes_per_launch": by,
+            "flops_per_launch": fl, "avg_launch_ms": avg_ms, "samples": n,
+            "share_of_timed_region": share / total_ms,
+            "fused_min_bytes_per_launch": mb,
+            "frac_of_fused_min": (mb / (avg_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]) if mb else None,
+            "vector_mb": vec_mb, "l2_resident": vec_mb * 4 < 129,
+            "peak_source": (f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})" if bound == "hbm" else
+                            "FP64 nominal: 152 SMs x 2 FMA/clk x 2.07 GHz")}
+
+
+def variant(ok, torch, wl, precision_name, overrides, steps, warmup, rank, flush, ref=None, profile=False):
+    """A secondary timed run (same protocol as the headline): value, iterations,
+    and the relative 2-norm difference of u and w from `ref` (same steps)."""
+    res = run_precision(ok, torch, wl, precision_name, steps, warmup, rank, profile, flush, overrides)
+    ms = sum(res["step_ms"])
+    out = {"value": wl.dofs * res["its"] / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
+           "gmres_its": res["its"], "newton_its": res["newton"], "mg_levels": res["g"].levels,
+           "step_p50_ms": pct(res["step_ms"], 0.5), "step_p99_ms": pct(res["step_ms"], 0.99)}
+    if ref is not None:
+        out["rel_diff_u"] = float(torch.linalg.norm(res["u"] - ref["u"]) / torch.linalg.norm(ref["u"]))
+        out["rel_diff_w"] = float(torch.linalg.norm(res["w"] - ref["w"]) / torch.linalg.norm(ref["w"]))
+    return out, res
+
+
+def workloads_3d(ok, torch, args, rank, flush):
+    """The 3D Kuhn workloads beside the 2D headline: 128^3 (mixed and float64,
+    a few timesteps) and the 512^3 workload's sampled finest-level kernels
+    (one timestep; its float32 vectors of 540 MB are far above the 129 MB L2,
+    so these kernels stream from HBM)."""
+    out = {}
+    wl = oi.CUBE_128
+    k = min(args.steps, 5)
+    m, rm = variant(ok, torch, wl, "mixed", args.opt, k, 2, rank, flush)
+    f, rf = variant(ok, torch, wl, "fp64", args.opt, k, 2, rank, flush, ref=rm)
+    rm["g"].close()
+    rf["g"].close()
+    out[wl.name] = {"mixed": m, "fp64": f, "speedup": m["value"] / f["value"]}
+    del rm, rf
+    torch.cuda.empty_cache()
+    wl = oi.CUBE_512
+    r = run_precision(ok, torch, wl, "mixed", 1, 1, rank, True, flush, args.opt)
+    ms = sum(r["step_ms"])
+    out[wl.name] = {"mixed": {"value": wl.dofs * r["its"] / (ms / 1e3), "ms_per_step": ms, "steps": 1,
+                              "gmres_its": r["its"], "newton_its": r["newton"], "mg_levels": r["g"].levels},
+                    "roofline": roofline_of(r, wl, "mixed", ms),
+                    "kernel_samples": {kk: {"samples": n, "avg_ms": (t / n if n else None)}
+                                       for kk, (n, t) in r["prof"].items()}}
+    r["g"].close()
+    del r
+    torch.cuda.empty_cache()
+    return out
 
 
 def main_ok(args):
@@ -384,34 +503,7 @@ def main_ok(args):
     agg = reduce_across({"ms": total_ms}, "max")
     units = reduce_across({"u": dof * mixed["its"]}, "sum")["u"]
     value = units / (agg["ms"] / 1e3)
-    # dominant sampled kernel: largest estimated share of the step
-    peaks, peak_kind = measured_peaks()
-    best = None
-    for tag, (n, tot) in mixed["prof"].items():
-        lpi = launches_per_iteration(tag, mixed["opts"])
-        if n == 0 or lpi is None:
-            continue
-        share = tot / n * lpi * mixed["its"]
-        if best is None or share > best[1]:
-            best = (tag, share, tot / n, n)
-    roof = None
-    if best:
-        tag, share, avg_ms, n = best
-        by, fl, bound = kernel_model(tag, wl, "mixed")
-        if bound == "hbm":
-            ach = by / (avg_ms * 1e-3) / 1e9
-            peak = peaks["hbm_gbs"]
-            unit = "GB/s"
-        else:
-            ach = fl / (avg_ms * 1e-3) / 1e12
-            peak = FP64_PEAK_TFLOPS
-            unit = "TFLOP/s"
-        tr = recorded_traffic(tag, wl.name, "mixed")
-        roof = {"kernel": tag, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                "traffic": tr, "algorithmic_bytes_per_launch": by, "flops_per_launch": fl,
-                "avg_launch_ms": avg_ms, "samples": n, "share_of_timed_region": share / total_ms,
-                "peak_source": (f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})" if bound == "hbm" else
-                                "FP64 nominal: 152 SMs x 2 FMA/clk x 2.07 GHz")}
+    roof = roofline_of(mixed, wl, "mixed", total_ms)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": agg["ms"] / args.steps, "higher_is_better": True,
@@ -419,6 +511,8 @@ def main_ok(args):
         "config": {"workload": wl.name, "dim": wl.dim, "n": wl.n, "vertices": wl.n_vertices, "dofs": dof,
                    "eps": wl.eps, "sigma": wl.sigma, "m": wl.m, "theta": wl.theta, "dt": wl.dt,
                    "restart": wl.restart, "gmres_rtol": wl.gmres_rtol, "mg_levels": mixed["g"].levels,
+                   "gram_schmidt": {0: "DGKS-conditional second pass", 1: "CGS2 (classical, reorthogonalised)",
+                                    2: "one classical pass"}[mixed["g"].opts.reorth],
                    "precision": "mixed (float32 preconditioner, float64 FGMRES/J/residual)",
                    "l2": "flushed by a 512 MB write before every timed step", "parallelism": f"replicas x{world}",
                    **({"overrides": args.opt} if args.opt else {})},
@@ -441,6 +535,22 @@ def main_ok(args):
                                           for k, (n, t) in fp64["prof"].items()}}
         out["mixed_vs_fp64"] = {"speedup": out["value"] / out["fp64"]["value"], "rel_diff_u": du,
                                 "rel_diff_w": dw}
+    if not args.no_variants:
+        ref = fp64 if fp64 is not None else None
+        v1, r1 = variant(ok, torch, wl, "mixed", list(args.opt) + ["reorth=2"], args.steps, args.warmup, rank,
+                         flush, ref=ref)
+        r1["g"].close()
+        v1["what"] = "one classical Gram-Schmidt pass per Arnoldi step (no reorthogonalisation)"
+        out["one_pass_gram_schmidt"] = v1
+        if wl.dim == 2:
+            v2, r2 = variant(ok, torch, wl, "mixed", list(args.opt) + ["coarse_max=4"], args.steps, args.warmup,
+                             rank, flush, ref=ref)
+            r2["g"].close()
+            v2["what"] = "nine multigrid levels (1024^2 down to a dense 5^2 coarsest solve)"
+            out["mg_9_levels"] = v2
+            del r1, r2
+        if wl.name == "2d_n1024":
+            out["workloads"] = workloads_3d(ok, torch, args, rank, flush)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if args.profile_out and rank == 0:
@@ -462,10 +572,10 @@ def main_reference(args):
     wl = oi.WORKLOADS[args.workload]
     sysm = System(Mesh(wl.dim, wl.n), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
     u0 = oi.initial_u(wl)
-    w0 = sysm.initial_w(u0)
+    w0 = sysm.initial_w(u0, solver="chebyshev")
     F = sysm.residual(u0, w0, u0, w0)
     J = sysm.jacobian(u0)
-    P = Preconditioner(sysm, u0, mode="inexact", q_A=10, n_V=5, k_R=1)
+    P = Preconditioner(sysm, u0, mode="inexact", q_A=10, n_V=5, k_R=1, coarse_max=32 if wl.dim == 2 else 4)
     per_step = 2
     run = lambda: fgmres(lambda z: J @ z, P.apply, -F, restart=wl.restart, rtol=wl.gmres_rtol, max_its=per_step)[1]
     for _ in range(args.warmup):

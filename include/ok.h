@@ -108,7 +108,8 @@ typedef struct ok_opts {
   int use_pdl;        /* programmatic dependent launch between kernels [1]      */
   int reorth;         /* Gram--Schmidt: 0 second pass only when the first one
                          cancels more than half of ||w||^2, 1 always two
-                         passes (CGS2), 2 one classical pass [2]                */
+                         passes (classical Gram--Schmidt with
+                         reorthogonalisation, CGS2), 2 one classical pass [1]   */
   double gmres_rtol;  /* stop when ||f - J x|| <= gmres_rtol ||f|| [1e-10]      */
   double newton_atol; /* Newton stops when ||F||_2 <= max(atol, rtol ||F_0||)   */
   double newton_rtol; /*   [atol 1e-10, rtol 0]                                 */
@@ -175,12 +176,19 @@ int ok_apply_preconditioner(ok_grid* g, const double* u_k, const double* v, doub
 int ok_solve_linear(ok_grid* g, const double* u_k, const double* f, double* x,
                     ok_step_info* info, ok_stream stream);
 
-/* One Newton step for the timestep from (u_n, w_n): f = -F(u_k, w_k),
- * solve J(u_k) d = f, then (u_k, w_k) += d.  u_k, w_k are in-out. */
+/* One Newton step for the timestep from (u_n, w_n) (Sec. 2, first paragraph:
+ * a Newton iteration per timestep, each solving eqn newton): f = -F(u_k, w_k)
+ * as in ok_assemble_rhs, J(u_k) d = f solved as ok_solve_linear does, then
+ * (u_k, w_k) += d.  u_k, w_k are in-out; u_n, w_n are read only.  info (may
+ * be NULL) receives the FGMRES iterations, the linear solve's relative
+ * residual and ||F||_2 before and after the step; converged = 1 when the
+ * latter meets the Newton stop test of ok_timestep. */
 int ok_newton_step(ok_grid* g, const double* u_n, const double* w_n,
                    double* u_k, double* w_k, ok_step_info* info, ok_stream stream);
 
-/* One theta-method timestep: Newton from (u, w) at t_n to the stop test,
+/* One theta-method timestep of eqns oka/okb (Sec. 2, first paragraph; Sec. 4
+ * runs these with theta = 1/2): Newton from (u, w) at t_n, each step as
+ * ok_newton_step, until ||F||_2 <= max(newton_atol, newton_rtol ||F_0||_2),
  * then newton_extra more steps; (u, w) are overwritten with t_{n+1}.
  * Returns OK_ERR_NOT_CONVERGED (state left at the last iterate) when the
  * Newton cap is hit. */
@@ -206,8 +214,10 @@ typedef struct ok_batch_info {
   double seconds;      /* wall time of the whole batch                     */
 } ok_batch_info;
 
-/* Run every request to completion.  Requests on distinct handles are
- * independent; each gets its own stream, derived from `stream`'s device. */
+/* Run every request to completion, one after another, on `stream` (no
+ * counterpart in the paper).  Requests on distinct handles are independent;
+ * a failing request does not stop the others.  Returns the status of the
+ * first failed request. */
 int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream stream);
 
 /* Serving (no counterpart in the paper): whole simulations admitted

@@ -240,8 +240,18 @@ class System:
         """S_hat = M + eps sqrt(c) K (the factor of eqn outer_approx)."""
         return (self.M + self.p.gamma * self.K).tocsr()
 
-    def initial_w(self, u0) -> np.ndarray:
-        """w0 from eqn okb: the L2 projection M w0 = eps^2 K u0 + N(u0)."""
-        import scipy.sparse.linalg as spla
+    def initial_w(self, u0, solver: str = "lu") -> np.ndarray:
+        """w0 from eqn okb: the L2 projection M w0 = eps^2 K u0 + N(u0).
+
+        solver "lu": sparse LU of M; "chebyshev": 80 Jacobi-preconditioned
+        Chebyshev steps on the interval [1/2, (d+2)/2] that holds the spectrum
+        of diag(M)^{-1} M (error factor below 1e-30, i.e. round-off), for
+        grids where the LU's fill makes it slow.
+        """
         rhs = self.p.eps ** 2 * (self.K @ u0) + nonlinear_term(self.mesh, u0)
+        if solver == "chebyshev":
+            from .solvers import chebyshev, mass_interval
+            lo, hi = mass_interval(self.mesh.dim)
+            return chebyshev(self.M, 1.0 / self.M.diagonal(), rhs, np.zeros_like(rhs), 80, lo, hi)
+        import scipy.sparse.linalg as spla
         return spla.spsolve(self.M.tocsc(), rhs)

@@ -766,11 +766,11 @@ void arnoldi(ok_grid* G, TZ* Z, int j, cudaStream_t s) {
   launch_apply_j<TZ>(G->dim, G->g0, G->refWM, G->refWK, G->jc, G->coef, zj, w, nullptr, s);
   pr.end(PT_APPLYJ, s);
   pr.begin(PT_CGS2, s);
-  if (G->o.reorth == 1) {           // CGS2: always two passes
+  if (G->o.reorth == 1) {           // CGS2: always two passes (the default)
     launch_multidot(G->V, N, j + 1, w, N, G->rs, ks_h1_ptr(G->ks), s);
     launch_update_multidot(G->V, N, j + 1, ks_h1_ptr(G->ks), w, N, G->rs, ks_h2_ptr(G->ks), s);
     launch_update_norm_givens(G->V, N, j + 1, w, N, G->rs, G->ks, j, s);
-  } else if (G->o.reorth == 2) {    // one classical pass (the default)
+  } else if (G->o.reorth == 2) {    // one classical pass
     launch_multidot(G->V, N, j + 1, w, N, G->rs, ks_h1_ptr(G->ks), s);
     launch_update_norm_check(G->V, N, j + 1, w, N, G->rs, G->ks, j, s, true);
   } else {                          // second pass only when the first cancelled too much
@@ -1048,7 +1048,7 @@ void ok_default_opts(ok_opts* o) {
   o->fuse_coarse = 1;
   o->tile_fine = 1;
   o->use_pdl = 1;
-  o->reorth = 2;
+  o->reorth = 1;
   o->gmres_rtol = 1e-10;
   o->newton_atol = 1e-10;
   o->newton_rtol = 0.0;

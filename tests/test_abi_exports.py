@@ -40,7 +40,7 @@ def test_default_opts_match_header_documentation():
     assert (o.restart, o.q_A, o.n_V, o.k_R, o.smooth_pre, o.smooth_post) == (30, 10, 5, 1, 2, 2)
     assert o.precision == ok.OK_FP64 and o.gmres_rtol == 1e-10 and o.smooth_lo_frac == 0.25
     assert o.use_graphs == 1 and o.fuse_coarse == 1
-    assert o.tile_fine == 1 and o.use_pdl == 1 and o.reorth == 2
+    assert o.tile_fine == 1 and o.use_pdl == 1 and o.reorth == 1
     assert ok.Opts.gmres_rtol.offset == 64 and ctypes.sizeof(ok.Opts) == 96   # 16 ints, 4 doubles
 
 

@@ -10,7 +10,10 @@ use what it can compute at any size:
   * 3D 512^3 Kuhn (135M vertices): one timestep with the float32 preconditioner
     against float64: convergence, the mean law, agreement, and FGMRES
     iterations per Newton step against the 128^3 case (mesh independence);
-  * all: mixed precision within 1e-8 of float64 (the method's target).
+  * all: mixed precision within 1e-8 of float64 (the method's target);
+  * element-wise oracle parity at full size where the oracle takes seconds:
+    P^{-1} v and every row of J z at 1024^2 with the benchmark's own
+    hierarchy and launch configuration, and both at 3D 64^3.
 """
 import numpy as np
 import pytest
@@ -197,3 +200,85 @@ def test_ritz_values_at_1024_within_the_lemma_2_enclosure():
     assert lo - 0.02 <= ritz.real.min() and ritz.real.max() <= hi + 0.1
     assert np.abs(ritz - 1.0).min() <= 0.05
 
+
+
+# ---------------------------------------------------------------------------
+# element-wise oracle parity at the benchmark's own sizes and hierarchies
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def oracle_1024():
+    """The oracle's J and inexact preconditioner at the 1024^2 workload's u0,
+    with the hierarchy the benchmark times: 1024, 512, ..., 32 (coarse_max 32,
+    dense 33^2 coarsest solve), q_A = 10, n_V = 5, k_R = 1, 2 + 2 smoothing."""
+    from oracle.fem import Mesh, Params, System
+    from oracle.solvers import Preconditioner
+    wl = oi.LARGE_2D
+    sysm = System(Mesh(wl.dim, wl.n), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
+    u = oi.initial_u(wl)
+    P = Preconditioner(sysm, u, mode="inexact", q_A=10, n_V=5, k_R=1, nu_pre=2, nu_post=2, coarse_max=32)
+    assert P.mg.sizes == [1024, 512, 256, 128, 64, 32]
+    v = np.random.default_rng(31).standard_normal(2 * sysm.mesh.nv)
+    return wl, sysm, u, v, P.apply(v)
+
+
+@pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
+def test_preconditioner_parity_at_the_1024_benchmark_hierarchy(oracle_1024, precision):
+    """z = P^{-1} v element by element against the oracle on the exact launch
+    configuration of the benchmark: the 64-column RY = 8 strip kernels on the
+    1025^2 level, the 32-column ones from 513^2 down, the two halo-5 mass
+    launches and the dense 33^2 coarse GEMV (eqns prec, schurinv; Sec. 3).
+    Tolerances as in the small-grid parity tests: 1e-10 (float64), 2e-4
+    (float32 preconditioner), relative to the largest entry of each block."""
+    wl, sysm, u, v, ref = oracle_1024
+    nv = sysm.mesh.nv
+    with ok.Grid(wl.dim, wl.n, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, precision=precision, coarse_max=32) as g:
+        assert g.levels == 6
+        z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        g.apply_preconditioner(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), z)
+        zh = z.cpu().numpy()
+    tol = 1e-10 if precision == ok.OK_FP64 else 2e-4
+    for blk in (slice(0, nv), slice(nv, 2 * nv)):
+        err = np.abs(zh[blk] - ref[blk]).max() / np.abs(ref[blk]).max()
+        assert err < tol, (precision, err)
+
+
+def test_jacobian_parity_every_row_at_1024(oracle_1024):
+    """y = J(u0) z at all 2.1M rows (eqn newton), 1e-13 of each row's |J||z| scale."""
+    wl, sysm, u, v, _ = oracle_1024
+    nv = sysm.mesh.nv
+    J = sysm.jacobian(u)
+    with ok.Grid(wl.dim, wl.n, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, coarse_max=32) as g:
+        y = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        g.apply_jacobian(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), y)
+        yh = y.cpu().numpy()
+    scale = abs(J) @ np.abs(v)
+    assert (np.abs(yh - J @ v) <= 1e-13 * scale).all()
+
+
+@pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
+def test_preconditioner_and_jacobian_parity_at_3d_64(precision):
+    """3D 64^3 Kuhn grid (274,625 vertices), hierarchy 64, 32, 16, 8, 4 with the
+    dense 5^3 coarsest solve and the one-block fused coarse V-cycle below 17^3:
+    P^{-1} v and J z element by element against the oracle."""
+    from oracle.fem import Mesh, Params, System
+    from oracle.solvers import Preconditioner
+    wl = oi.CUBE_128
+    sysm = System(Mesh(3, 64), Params(wl.eps, wl.sigma, wl.m, wl.theta, wl.dt))
+    nv = sysm.mesh.nv
+    rng = np.random.default_rng(64)
+    u = wl.m + 0.3 * rng.uniform(-1, 1, nv)
+    v = rng.standard_normal(2 * nv)
+    P = Preconditioner(sysm, u, mode="inexact", q_A=10, n_V=5, k_R=1, coarse_max=4)
+    assert P.mg.sizes == [64, 32, 16, 8, 4]
+    ref = P.apply(v)
+    with ok.Grid(3, 64, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, precision=precision) as g:
+        z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        g.apply_preconditioner(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), z)
+        y = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        g.apply_jacobian(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), y)
+        zh, yh = z.cpu().numpy(), y.cpu().numpy()
+    tol = 1e-10 if precision == ok.OK_FP64 else 2e-4
+    for blk in (slice(0, nv), slice(nv, 2 * nv)):
+        assert np.abs(zh[blk] - ref[blk]).max() < tol * np.abs(ref[blk]).max()
+    J = sysm.jacobian(u)
+    assert (np.abs(yh - J @ v) <= 1e-13 * (abs(J) @ np.abs(v))).all()

@@ -197,3 +197,12 @@ def test_initial_w_solves_okb():
     a = 0.25                                   # constant state: w0 = a^3 - a
     w_c = sysm.initial_w(np.full(sysm.mesh.nv, a))
     assert np.abs(w_c - (a ** 3 - a)).max() < 1e-14
+
+
+@pytest.mark.parametrize("dim,n", [(2, 9), (3, 4)])
+def test_initial_w_chebyshev_equals_lu(dim, n):
+    """Both solvers of the okb projection reach the same w0 (to round-off)."""
+    sysm = System(Mesh(dim, n), Params(0.05, 50.0, 0.1, 0.5, 1e-3))
+    u0 = 0.1 + 0.5 * np.random.default_rng(4).uniform(-1, 1, sysm.mesh.nv)
+    a, b = sysm.initial_w(u0), sysm.initial_w(u0, solver="chebyshev")
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
