@@ -104,7 +104,9 @@ typedef struct ok_opts {
                          it), otherwise as 1 [1]                                 */
   int tile_fine;      /* 2D: register-strip tile kernels on the fine levels:
                          0 off, 1 automatic window width, 2 / 3 force 32 / 64
-                         columns [1]                                            */
+                         columns; 3D: any nonzero value runs the multigrid's
+                         stencil steps by z-marching blocks (0: one thread per
+                         vertex; both give the same bits) [1]                   */
   int use_pdl;        /* programmatic dependent launch between kernels [1]      */
   int reorth;         /* Gram--Schmidt: 0 second pass only when the first one
                          cancels more than half of ||w||^2, 1 always two
@@ -338,6 +340,22 @@ int ok_hessenberg_eigenvalues(int k, const double* H, int ldh, double* re, doubl
  * Errors are reported through ok_last_error(). */
 int ok_apply_jacobian_noalloc(int dim, int n, const ok_params* p, const double* u_k, const double* z,
                               double* y, ok_stream stream);
+
+/* The Ohta--Kawasaki free energy (Sec. 1, the functional E[u] whose H^{-1}
+ * gradient flow eqns oka/okb are) of the P1 function with nodal values u
+ * (N_v, host or device):
+ *   terms[0] = eps^2/2 u^T K u                       (interfacial term),
+ *   terms[1] = 1/4 int (1 - u_h^2)^2 dx              (double well, exact quadrature),
+ *   terms[2] = sigma/2 (f, phi)_{L2}                 (nonlocal term),
+ * with f = u minus its mean and phi the solution of the Neumann problem
+ * K phi = M f (the inverse Neumann Laplacian of Sec. 1), solved by conjugate
+ * gradients preconditioned with two multigrid V-cycles for M + K (float64)
+ * to a relative residual of 1e-12; *E = terms[0] + terms[1] + terms[2].
+ * terms (3 doubles) and E are HOST pointers; either may be NULL, not both.
+ * The first call on a handle builds that multigrid (device memory about the
+ * size of the float64 preconditioner's hierarchy) and keeps it.  Synchronises
+ * `stream`.  OK_ERR_NONFINITE for a non-finite u. */
+int ok_energy(ok_grid* g, const double* u, double* terms, double* E, ok_stream stream);
 
 /* Number of this library's kernels launched by the process so far (graph
  * replays count every kernel node). */

@@ -141,10 +141,9 @@ CUBE_512 = Workload("3d_n512", 3, 512, 0.01, 1000.0, 0.0, 0.5, 1e-5, 3,
 WORKLOADS = {w.name: w for w in (SMALL_2D, LARGE_2D, CUBE_128, CUBE_512)}
 
 # The paper's own experiment (Sec. 4): unit cube, m = 0.4, eps = 0.02,
-# sigma = 100, theta = 0.5, dt = eps^2, u0 = m + cos(2 pi x) cos(2 pi y) cos(2 pi z) / 50.
-# The paper's meshes have 50..800 cells per side; the geometric hierarchy here
-# wants n divisible by powers of two, so the stand-in sizes are 32..256.
-PAPER_3D = Workload("paper_3d", 3, 64, 0.02, 100.0, 0.4, 0.5, 4e-4, 300,
+# sigma = 100, theta = 0.5, dt = eps^2, u0 = m + cos(2 pi x) cos(2 pi y) cos(2 pi z) / 50,
+# on meshes of 50 2^k cells per side (scaled() picks the size).
+PAPER_3D = Workload("paper_3d", 3, 50, 0.02, 100.0, 0.4, 0.5, 4e-4, 300,
                     "cos", 1.0 / 50.0, 0, 30, 1e-8, 1e-10)
 
 

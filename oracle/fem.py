@@ -173,6 +173,26 @@ def nonlinear_term(mesh: Mesh, u: np.ndarray) -> np.ndarray:
     return _assemble_vector(mesh, loc)
 
 
+def double_well_integral(mesh: Mesh, u: np.ndarray) -> float:
+    """int (1 - u_h^2)^2 dx for the P1 function u_h, exact: on each simplex
+    1 - 2 u_h^2 + u_h^4 with u_h = sum_a u_a lambda_a expanded term by term."""
+    d = mesh.dim
+    us = u[mesh.simplices]
+    vol = mesh.volume
+    r = range(d + 1)
+    sq = np.zeros(len(vol))
+    for a in r:
+        for b in r:
+            sq += us[:, a] * us[:, b] * monomial_factor(d, (a, b))
+    qu = np.zeros(len(vol))
+    for a in r:
+        for b in r:
+            for c in r:
+                for e in r:
+                    qu += us[:, a] * us[:, b] * us[:, c] * us[:, e] * monomial_factor(d, (a, b, c, e))
+    return float(np.sum(vol * (1.0 - 2.0 * sq + qu)))
+
+
 # --------------------------------------------------------------------------
 # the discrete Ohta--Kawasaki system
 # --------------------------------------------------------------------------
@@ -239,6 +259,31 @@ class System:
     def s_hat(self) -> sp.csr_matrix:
         """S_hat = M + eps sqrt(c) K (the factor of eqn outer_approx)."""
         return (self.M + self.p.gamma * self.K).tocsr()
+
+    def energy(self, u) -> dict:
+        """The Ohta--Kawasaki free energy (Sec. 1) of the P1 function u_h:
+
+            E = 1/2 int ( eps^2 |grad u|^2 + 1/2 (1 - u^2)^2
+                          + sigma |(-Delta_N)^{-1/2} (u - m)|^2 ) dx.
+
+        gradient = eps^2/2 u^T K u;  double_well = 1/4 int (1 - u_h^2)^2 (exact);
+        nonlocal = sigma/2 (f, phi)_{L2} with f = u - m less its mean (the
+        inverse Neumann Laplacian acts on mean-free data) and phi the
+        mean-free solution of K phi = M f, solved exactly (sparse LU of K
+        bordered by the mean constraint 1^T M phi = 0).
+        """
+        import scipy.sparse.linalg as spla
+        p, M, K = self.p, self.M, self.K
+        lm = M @ self.one                                   # 1^T M (lumped masses)
+        f = u - p.m
+        f = f - (lm @ f) / (lm @ self.one)
+        nv = self.mesh.nv
+        A = sp.bmat([[K, sp.csr_matrix(lm[:, None])], [sp.csr_matrix(lm[None, :]), None]], format="csc")
+        phi = spla.spsolve(A, np.concatenate([M @ f, [0.0]]))[:nv]
+        grad = 0.5 * p.eps ** 2 * float(u @ (K @ u))
+        well = 0.25 * double_well_integral(self.mesh, u)
+        nonl = 0.5 * p.sigma * float(f @ (M @ phi))
+        return {"gradient": grad, "double_well": well, "nonlocal": nonl, "total": grad + well + nonl}
 
     def initial_w(self, u0, solver: str = "lu") -> np.ndarray:
         """w0 from eqn okb: the L2 projection M w0 = eps^2 K u0 + N(u0).

@@ -117,12 +117,22 @@ class Multigrid:
             self.dinv.append(1.0 / A.diagonal())
         for nl in self.sizes[1:]:
             self.P.append(prolongation(dim, nl))
-        self.coarse = self.A[-1].toarray()
+        # the coarsest level is solved exactly: dense LU when small, sparse LU
+        # for the large odd coarse levels of n = c 2^k with c odd and large
+        if self.A[-1].shape[0] <= 5000:
+            self.coarse, self.coarse_lu = self.A[-1].toarray(), None
+        else:
+            self.coarse, self.coarse_lu = None, spla.splu(self.A[-1].tocsc())
+
+    def coarse_solve(self, b):
+        if self.coarse_lu is not None:
+            return self.coarse_lu.solve(b)
+        return np.linalg.solve(self.coarse, b)
 
     def vcycle(self, level, b, x):
         A = self.A[level]
         if level == len(self.sizes) - 1:
-            return np.linalg.solve(self.coarse, b)
+            return self.coarse_solve(b)
         x = chebyshev(A, self.dinv[level], b, x, self.nu_pre, self.lo, self.hi)
         r = b - A @ x
         P = self.P[level]

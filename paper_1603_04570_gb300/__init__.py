@@ -112,6 +112,7 @@ def load(build: bool = True):
         "ok_profile": (c_int, [P, c_int]),
         "ok_profile_read": (c_int, [P, POINTER(KernelStat), c_int, POINTER(c_int)]),
         "ok_launch_count": (c_longlong, []),
+        "ok_energy": (c_int, [P, P, P, P, P]),
         "ok_apply_jacobian_noalloc": (c_int, [c_int, c_int, POINTER(Params), P, P, P, P]),
         "ok_arnoldi_hessenberg": (c_int, [P, P, c_int, c_int, POINTER(c_int), P]),
         "ok_ritz_values": (c_int, [P, P, P, c_int, POINTER(c_int), P]),
@@ -313,6 +314,14 @@ def ok_hessenberg_eigenvalues(H):
     return re[:k] + 1j * im[:k]
 
 
+def ok_energy(h, nv, u, stream=None):
+    """The Ohta--Kawasaki energy of u: (terms [interfacial, double well, nonlocal], total)."""
+    terms = (c_double * 3)()
+    total = c_double()
+    _check(load().ok_energy(h, _ptr(u, nv, "u"), terms, byref(total), _stream(stream, u)))
+    return [terms[0], terms[1], terms[2]], total.value
+
+
 def ok_launch_count() -> int:
     return load().ok_launch_count()
 
@@ -402,6 +411,9 @@ class Grid:
 
     def timestep(self, u, w, stream=None, check=True):
         return ok_timestep(self.handle, self.nv, u, w, stream, check)
+
+    def energy(self, u, stream=None):
+        return ok_energy(self.handle, self.nv, u, stream)
 
     def arnoldi_hessenberg(self, max_k=63, stream=None):
         return ok_arnoldi_hessenberg(self.handle, max_k, stream)

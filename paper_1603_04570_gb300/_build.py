@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libok_gb300.so")
-SOURCES = ["ok_fem.cu", "ok_mg.cu", "ok_tile.cu", "ok_krylov.cu", "ok_api.cu", "ok_noalloc.cu", "ok_diag.cu"]
+SOURCES = ["ok_fem.cu", "ok_mg.cu", "ok_tile.cu", "ok_plane3.cu", "ok_krylov.cu", "ok_api.cu", "ok_noalloc.cu",
+           "ok_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wall", "-Xcompiler", "-Wno-unused-function"]

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -218,9 +219,23 @@ template <typename T> struct Prec {
 #endif
   static constexpr int LOW_N1 = OK_LOW_N1;      // cluster kernel: levels of at most this many vertices per side
 
+  // coarsest level above COARSE_NC_MAX unknowns (odd coarse sides such as the
+  // 26^3 of n = 50 2^k): Chebyshev--Jacobi iteration from zero instead of the
+  // dense inverse, qC steps on [lo, (d+2)/2] with lo = (1/2) / (1 + gamma rho),
+  // rho = max over classes of diag(K)/diag(M) on that level (see build_prec)
+  bool cheb_coarse = false;
+  int qC = 0;
+  double thC = 1;
+  std::vector<double> cC1, cC2;
   void coarse_solve(const T* rhs, T* x, cudaStream_t s) {
-    if (gemv_inv) launch_coarse_gemv<T>(nc, gemv_ldA, gemv_inv, rhs, x, s);
-    else launch_coarse_solve<T>(nc, coarse_inv, rhs, x, s);
+    if (cheb_coarse) {
+      Level<T>& C = lv.back();
+      cheb<T, T>(C.g, C.WS, C.dinvS, rhs, true, x, C.r, C.d0, C.d1, qC, thC, cC1, cC2, (T*)nullptr, (T)1, false, s);
+    } else if (gemv_inv) {
+      launch_coarse_gemv<T>(nc, gemv_ldA, gemv_inv, rhs, x, s);
+    } else {
+      launch_coarse_solve<T>(nc, coarse_inv, rhs, x, s);
+    }
   }
   T *cx = nullptr, *cr = nullptr, *cd0 = nullptr, *cd1 = nullptr;   // Chebyshev on M
   T *tt = nullptr, *yy = nullptr;                                    // k_R = 2
@@ -297,21 +312,43 @@ template <typename T> struct Prec {
     mg_solve_t<TZ>(b2, z + nv, (T*)nullptr, s);                  // z2 = S_hat^{-1} b2
   }
 
+  bool plane3 = false;         // 3D: stencil steps by z-marching blocks (ok_plane3.cu)
+
+  // out = n_V V-cycles from zero on the level-0 system with right-hand side rhs
+  void solve_mg(const T* rhs, T* out, cudaStream_t s) {
+    if (tiled) {
+      mg_solve_t<T>(rhs, out, (T*)nullptr, s);
+    } else {
+      launch_axpby<T, T>(lv[0].g.nv, 1.0, rhs, 0.0, lv[0].b, s);
+      mg_solve<T>(out, s);
+    }
+  }
+
   template <typename TB, typename TO>
   void cheb(const Geom& g, const T* W, const T* dinv, const TB* b, bool x_zero, T* x, T* r, T* d0, T* d1,
             int steps, double th, const std::vector<double>& c1, const std::vector<double>& c2, TO* out,
             T oscale, bool want_r, cudaStream_t s, int tag = -1) {
     if (x_zero) launch_cheb_init<T, TB>(dim, g, dinv, b, (T)1, r, d0, (T)(1.0 / th), s);
+    else if (plane3) launch_resid_init3<T>(g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s);
     else launch_resid_init<T>(dim, g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s);
     T* d[2] = {d0, d1};
     int cur = 0;
     for (int k = 0; k + 1 < steps; ++k) {
       if (k == 0 && prof) prof->begin(tag, s);
-      launch_cheb_step<T>(dim, g, W, dinv, x, r, d[cur], d[1 - cur], (T)c1[k], (T)c2[k], x_zero && k == 0, s);
+      if (plane3)
+        launch_cheb_step3<T>(g, W, dinv, x, r, d[cur], d[1 - cur], (T)c1[k], (T)c2[k], x_zero && k == 0, s);
+      else
+        launch_cheb_step<T>(dim, g, W, dinv, x, r, d[cur], d[1 - cur], (T)c1[k], (T)c2[k], x_zero && k == 0, s);
       if (k == 0 && prof) prof->end(tag, s);
       cur ^= 1;
     }
-    launch_cheb_last<T, TO>(dim, g, W, x, want_r ? r : nullptr, d[cur], x_zero && steps == 1, out, oscale, s);
+    if (plane3 && want_r) launch_cheb_last3<T, TO>(g, W, x, r, d[cur], x_zero && steps == 1, out, oscale, s);
+    else launch_cheb_last<T, TO>(dim, g, W, x, want_r ? r : nullptr, d[cur], x_zero && steps == 1, out, oscale, s);
+  }
+  // y = alpha W x on level g (M x, or dt theta K y for k_R = 2)
+  void op(const Geom& g, const T* W, bool axis_only, const T* x, T* y, T alpha, cudaStream_t s) {
+    if (plane3) launch_op_apply3<T, T, T>(g, W, axis_only, x, y, alpha, (const T*)nullptr, (T)0, s);
+    else launch_op_apply<T, T, T>(dim, g, W, axis_only, x, y, alpha, (const T*)nullptr, (T)0, s);
   }
 
   template <typename TO>
@@ -364,21 +401,21 @@ template <typename T> struct Prec {
     launch_cstep<T, double>(dim, g, coef, v + nv, (T)1, cx, (T)inv_a11, L0.b, s);   // t = r2 - C z1
     if (k_R == 1) {
       mg_solve<T>((T*)nullptr, s);                                         // S_hat^{-1} t
-      launch_op_apply<T, T, T>(dim, g, WM, false, L0.x, L0.b, (T)1, (const T*)nullptr, (T)0, s);   // M .
+      op(g, WM, false, L0.x, L0.b, (T)1, s);                               // M .
       mg_solve<TZ>(z + nv, s);                                             // S_hat^{-1} .
       return;
     }
     // k_R = 2: y = S~^{-1} t;  z2 = y + S~^{-1} (t - S y),  S y = M y - C A~^{-1} (dt theta K y)
     launch_axpby<T, T>(nv, 1.0, L0.b, 0.0, tt, s);
     mg_solve<T>((T*)nullptr, s);
-    launch_op_apply<T, T, T>(dim, g, WM, false, L0.x, L0.b, (T)1, (const T*)nullptr, (T)0, s);
+    op(g, WM, false, L0.x, L0.b, (T)1, s);
     mg_solve<T>(yy, s);
-    launch_op_apply<T, T, T>(dim, g, WK, true, yy, cr, (T)dth, (const T*)nullptr, (T)0, s);   // q = dt th K y
+    op(g, WK, true, yy, cr, (T)dth, s);                                                     // q = dt th K y
     launch_axpby<T, T>(nv, 1.0, cr, 0.0, L0.r, s);                                          // keep q
     a_inv<T, T>(L0.r, (T*)nullptr, s);                                                     // cx = Cheb(q)
     launch_schur_resid<T>(dim, g, WM, (T)1, coef, tt, yy, cx, (T)inv_a11, L0.b, s);         // t - S y
     mg_solve<T>((T*)nullptr, s);
-    launch_op_apply<T, T, T>(dim, g, WM, false, L0.x, L0.b, (T)1, (const T*)nullptr, (T)0, s);
+    op(g, WM, false, L0.x, L0.b, (T)1, s);
     mg_solve<T>((T*)nullptr, s);
     launch_axpby<T, T>(nv, 1.0, yy, 1.0, L0.x, s);
     launch_axpby<T, TZ>(nv, 1.0, L0.x, 0.0, z + nv, s);
@@ -427,17 +464,31 @@ struct ok_grid {
   Profiler prof;
   double cheb_init_th = 1;
   std::vector<double> cI1, cI2;          // 60-step mass Chebyshev for w0
+  struct EnergyWork* ew = nullptr;       // ok_energy's multigrid and vectors (first call)
+};
+
+// ok_energy: multigrid of M + K (float64) as the preconditioner of conjugate
+// gradients for the Neumann problem K phi = M f, and the vectors of that solve.
+struct EnergyWork {
+  Prec<double> mg;
+  double *ones = nullptr, *lm = nullptr, *f = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr,
+         *p = nullptr, *q = nullptr, *e = nullptr;
+  int last_its = 0;
 };
 
 namespace {
 
+// The multigrid hierarchy of M + gamma K (gamma < 0: S_hat's eps sqrt(c)) and
+// the rest of the block preconditioner's workspace.
 template <typename T>
 void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std::vector<double>& refM,
-                const std::vector<double>& refK) {
+                const std::vector<double>& refK, double gamma_in = -1.0) {
   const int dim = G->dim;
   const int NOFF = dim == 2 ? Topo<2>::NOFF : Topo<3>::NOFF;
   const int NCLASS = dim == 2 ? Topo<2>::NCLASS : Topo<3>::NCLASS;
-  const double gamma = G->p.eps * std::sqrt(G->p.dt * G->p.theta / (1.0 + G->p.dt * G->p.theta * G->p.sigma));
+  const double gamma = gamma_in >= 0.0 ? gamma_in
+                                       : G->p.eps * std::sqrt(G->p.dt * G->p.theta /
+                                                              (1.0 + G->p.dt * G->p.theta * G->p.sigma));
   Arena& A = G->arena;
   P.dim = dim;
   P.q_A = G->o.q_A;
@@ -447,6 +498,7 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
   P.nu_post = G->o.smooth_post;
   P.inv_a11 = 1.0 / (1.0 + G->p.dt * G->p.theta * G->p.sigma);
   P.dth = G->p.dt * G->p.theta;
+  P.plane3 = dim == 3 && G->o.tile_fine != 0;
   const double hiS = 0.5 * (dim + 2);
   cheb_coefs(G->o.smooth_lo_frac * hiS, hiS, std::max(P.nu_pre, P.nu_post), P.cS1, P.cS2, P.thS);
   cheb_coefs(0.5, 0.5 * (dim + 2), P.q_A, P.cM1, P.cM2, P.thM);
@@ -492,11 +544,28 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
     P.tt = A.alloc<T>(nv0);
     P.yy = A.alloc<T>(nv0);
   }
-  // coarsest level: dense S_hat and its inverse (float64 Gauss--Jordan on the GPU)
+  // coarsest level: dense S_hat and its inverse (float64 Gauss--Jordan on the
+  // GPU) up to COARSE_NC_MAX unknowns, else a Chebyshev solve on that level
   Level<T>& C = P.lv.back();
   const long long nc = C.g.nv;
   P.nc = nc;
-  {
+  const bool dense_coarse = nc <= COARSE_NC_MAX;
+  if (!dense_coarse) {
+    // D^{-1} S_hat with S_hat = M + gamma K, D = D_M + gamma D_K: x^T S_hat x >= x^T M x
+    // >= (1/2) x^T D_M x (the element bound of the mass interval) and x^T D x <=
+    // (1 + gamma rho) x^T D_M x, so its spectrum lies in [(1/2)/(1 + gamma rho), (d+2)/2]
+    const double h = 1.0 / C.n, hd = std::pow(h, dim), hk = std::pow(h, dim - 2);
+    double rho = 0.0;
+    for (int c = 0; c < NCLASS; ++c) rho = std::max(rho, hk * refK[c * NOFF] / (hd * refM[c * NOFF]));
+    const double lo = 0.5 / (1.0 + gamma * rho), hi = 0.5 * (dim + 2);
+    const double kap = hi / lo, sig = (std::sqrt(kap) + 1.0) / (std::sqrt(kap) - 1.0);
+    const double tol = std::is_same<T, double>::value ? 1e-13 : 1e-8;
+    // Chebyshev error after q steps <= 2 / (sig^q + sig^-q) <= tol
+    P.qC = std::max(2, (int)std::ceil(std::log(2.0 / tol) / std::log(sig)));
+    cheb_coefs(lo, hi, P.qC, P.cC1, P.cC2, P.thC);
+    P.cheb_coarse = true;
+  }
+  if (dense_coarse) {
     const double h = 1.0 / C.n, hd = std::pow(h, dim), hk = std::pow(h, dim - 2);
     std::vector<double> td(NCLASS * NOFF);
     for (int i = 0; i < NCLASS * NOFF; ++i) td[i] = hd * refM[i] + gamma * hk * refK[i];
@@ -555,7 +624,7 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
   // (On GB300 at 1025^2 the cluster launch is slower than separate launches:
   // 16 SMs leave most of each phase's windows serialised.)
   int low_cluster = 0, Lf = nl - 1;
-  if (tiles_ok && G->o.fuse_coarse == 2 && nl >= 3) {
+  if (tiles_ok && G->o.fuse_coarse == 2 && nl >= 3 && dense_coarse) {
     for (int l = 1; l < nl - 1; ++l)
       if (P.lv[l].g.n1 <= Prec<T>::LOW_N1) {
         Lf = l;
@@ -564,7 +633,7 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
     const int nlow = nl - 1 - Lf;
     if (nlow >= 1 && nlow <= LOW_MAXLEV) low_cluster = prepare_low_vcycle<T>(nc);
   }
-  if (G->o.fuse_coarse && low_cluster == 0 && nl - Lc >= 2) {
+  if (G->o.fuse_coarse && low_cluster == 0 && nl - Lc >= 2 && dense_coarse) {
     CoarseArgs<T>& ca = P.ca;
     ca.nlev = nl - Lc;
     long long off = 0;
@@ -1024,6 +1093,90 @@ void copy_out(ok_grid* G, double* dst, const double* src, long long count) {
   CK(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, G->s));
 }
 
+// x^T y of two device vectors (deterministic two-stage reduction), on the host
+double dot(ok_grid* G, const double* x, const double* y, long long n) {
+  launch_multidot(x, n, 1, y, n, G->rs, G->dsc + 2, G->s);
+  CKL();
+  return read_scalar(G, G->dsc + 2);
+}
+
+void energy_setup(ok_grid* G) {
+  if (G->ew) return;
+  std::unique_ptr<EnergyWork> E(new EnergyWork());
+  const int dim = G->dim;
+  const int NOFF = dim == 2 ? Topo<2>::NOFF : Topo<3>::NOFF;
+  const int NCLASS = dim == 2 ? Topo<2>::NCLASS : Topo<3>::NCLASS;
+  std::vector<double> refM(NCLASS * NOFF), refK(NCLASS * NOFF);
+  reference_tables(dim, refM.data(), refK.data());
+  build_prec<double>(G, E->mg, level_sizes(G->n, G->o.coarse_max), refM, refK, 1.0);   // M + K
+  E->mg.n_V = 2;
+  E->mg.prof = nullptr;
+  const long long nv = G->g0.nv;
+  Arena& A = G->arena;
+  for (double** v : {&E->ones, &E->lm, &E->f, &E->b, &E->x, &E->r, &E->z, &E->p, &E->q}) *v = A.alloc<double>(nv);
+  E->e = A.alloc<double>(2 * nv);
+  std::vector<double> one(nv, 1.0);
+  CK(cudaMemcpy(E->ones, one.data(), nv * sizeof(double), cudaMemcpyHostToDevice));
+  launch_op_apply<double, double, double>(dim, G->g0, G->WM0d, false, E->ones, E->lm, 1.0, (const double*)nullptr,
+                                          0.0, G->s);            // 1^T M, the lumped masses
+  CKL();
+  CK(cudaStreamSynchronize(G->s));
+  G->ew = E.release();
+}
+
+// The three terms of the Ohta--Kawasaki energy (Sec. 1) of the device vector u.
+void energy(ok_grid* G, const double* u, double out[3]) {
+  energy_setup(G);
+  EnergyWork& E = *G->ew;
+  const long long nv = G->g0.nv;
+  const int dim = G->dim;
+  cudaStream_t s = G->s;
+  launch_energy_local(dim, G->g0, G->refWK, G->rc, u, E.e, s);
+  CKL();
+  out[0] = dot(G, E.ones, E.e, nv);
+  out[1] = dot(G, E.ones, E.e + nv, nv);
+  // f = u - (1^T M u) / |Omega|, mean-free; b = M f
+  const double mean = dot(G, E.lm, u, nv) / dot(G, E.lm, E.ones, nv);
+  CK(cudaMemcpyAsync(E.f, u, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  launch_axpby<double, double>(nv, -mean, E.ones, 1.0, E.f, s);
+  launch_op_apply<double, double, double>(dim, G->g0, G->WM0d, false, E.f, E.b, 1.0, (const double*)nullptr, 0.0,
+                                          s);
+  CKL();
+  // conjugate gradients for K x = b (consistent: 1^T b = 0), preconditioned by
+  // two V-cycles for M + K (symmetric: the same Chebyshev polynomial before and
+  // after the coarse correction); stop at ||r|| <= 1e-12 ||b||
+  const double bn = std::sqrt(dot(G, E.b, E.b, nv));
+  CK(cudaMemsetAsync(E.x, 0, nv * sizeof(double), s));
+  double xb = 0.0;
+  E.last_its = 0;
+  if (bn > 0.0) {
+    CK(cudaMemcpyAsync(E.r, E.b, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    E.mg.solve_mg(E.r, E.z, s);
+    CK(cudaMemcpyAsync(E.p, E.z, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    double rz = dot(G, E.r, E.z, nv);
+    const double hk = G->rc.hk;
+    for (int it = 0; it < 500; ++it) {
+      launch_op_apply<double, double, double>(dim, G->g0, G->refWK, true, E.p, E.q, hk, (const double*)nullptr,
+                                              0.0, s);
+      CKL();
+      const double al = rz / dot(G, E.p, E.q, nv);
+      launch_axpby<double, double>(nv, al, E.p, 1.0, E.x, s);
+      launch_axpby<double, double>(nv, -al, E.q, 1.0, E.r, s);
+      E.last_its = it + 1;
+      const double rn = std::sqrt(dot(G, E.r, E.r, nv));
+      if (!std::isfinite(rn)) fail(OK_ERR_NONFINITE, "non-finite residual in the energy's Neumann solve");
+      if (rn <= 1e-12 * bn) break;
+      E.mg.solve_mg(E.r, E.z, s);
+      const double rz1 = dot(G, E.r, E.z, nv);
+      launch_axpby<double, double>(nv, 1.0, E.z, rz1 / rz, E.p, s);
+      CKL();
+      rz = rz1;
+    }
+    xb = dot(G, E.b, E.x, nv);
+  }
+  out[2] = 0.5 * G->p.sigma * xb;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1071,10 +1224,6 @@ int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid
   int st = guarded([&] {
     validate(dim, n, p, &od);
     std::vector<int> sizes = level_sizes(n, od.coarse_max);
-    const long long ncoarse = (long long)std::pow((double)(sizes.back() + 1), dim);
-    if (ncoarse > 4913)
-      fail(OK_ERR_INVALID_ARG, "the coarsest multigrid level has " + std::to_string(ncoarse) +
-                                   " unknowns (> 4913); use n = c 2^k with (c+1)^dim <= 4913");
     G = new ok_grid();
     G->dim = dim;
     G->n = n;
@@ -1185,6 +1334,7 @@ int ok_grid_create(int dim, int n, const ok_params* p, const ok_opts* o, ok_grid
 int ok_grid_destroy(ok_grid* G) {
   if (!G) return OK_SUCCESS;
   if (G->s) cudaStreamSynchronize(G->s);
+  delete G->ew;                        // its device memory belongs to the arena below
   for (auto& ge : G->graphs)
     if (ge) cudaGraphExecDestroy(ge);
   for (auto& ge : G->cgraphs)
@@ -1490,6 +1640,24 @@ int ok_ritz_values(ok_grid* G, double* re, double* im, int max, int* count, ok_s
   *count = k;
   g_last_error.clear();
   return OK_SUCCESS;
+}
+
+int ok_energy(ok_grid* G, const double* u, double* terms, double* E, ok_stream stream) {
+  if (!G || !u || (!terms && !E)) {
+    g_last_error = "NULL argument";
+    return OK_ERR_INVALID_ARG;
+  }
+  return guarded([&] {
+    StreamScope sc(G, (cudaStream_t)stream);
+    const long long nv = G->g0.nv;
+    const double* ud = stage_in(G, u, G->tmp, nv);
+    check_finite(G, ud, nv, "u");
+    double t[3];
+    energy(G, ud, t);
+    if (terms) std::memcpy(terms, t, sizeof(t));
+    if (E) *E = t[0] + t[1] + t[2];
+    if (G->ew->last_its >= 500) fail(OK_ERR_NOT_CONVERGED, "the energy's Neumann solve did not converge");
+  });
 }
 
 long long ok_launch_count(void) { return g_launch_count.load(); }

@@ -260,6 +260,49 @@ __global__ void __launch_bounds__(128) k_initw_rhs(Geom g, const double* __restr
 }
 
 // ---------------------------------------------------------------------------
+// Local terms of the Ohta--Kawasaki energy (Sec. 1) per vertex v:
+//   e[v]       = eps^2/2 u_v (K u)_v                       (sums to eps^2/2 u^T K u)
+//   e[N_v + v] = 1/4 sum over the simplices T at v of int_T (1 - u_h^2)^2 / (d+1)
+// (each simplex is shared by its d+1 vertices, so the second sums to
+// 1/4 int (1 - u_h^2)^2).  On T with vertex values u_0..u_d and power sums
+// p_k = sum u_c^k (Dirichlet moments, as above):
+//   int_T u_h^2 = |T| d!/(d+2)! (p1^2 + p2),
+//   int_T u_h^4 = |T| d!/(d+4)! (p1^4 + 6 p1^2 p2 + 3 p2^2 + 8 p1 p3 + 6 p4)
+// (the complete homogeneous symmetric polynomials h2 and h4 times 2! and 4!).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(128) k_energy_local(Geom g, const double* __restrict__ WK, ResidualCoefs rc,
+                                                      const double* __restrict__ u, double* __restrict__ e) {
+  pdl_entry();
+  using Tp = Topo<D>;
+  Vtx<D> v;
+  if (!vertex_of_thread<D>(g, v)) return;
+  double us[Tp::NOFF];
+  load_nb<D>(u, g, v, us);
+  const double ku = rc.hk * dot_w<D, Tp::NAX>(WK, v.cls, us);
+  double well = 0.0;
+  static_for<0, Tp::NINC>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (inc_valid<D, i>(v.c)) {
+      double p1 = 0.0, p2 = 0.0, p3 = 0.0, p4 = 0.0;
+      static_for<0, D + 1>([&](auto Tt) {
+        constexpr int o = inc_off(D, i, decltype(Tt)::value);
+        const double x = us[o], x2 = x * x;
+        p1 += x;
+        p2 += x2;
+        p3 = fma(x2, x, p3);
+        p4 = fma(x2, x2, p4);
+      });
+      const double q2 = fma(p1, p1, p2);
+      const double q4 = fma(p1 * p1, fma(p1, p1, 6.0 * p2), fma(3.0 * p2, p2, fma(8.0 * p1, p3, 6.0 * p4)));
+      well += fma(-2.0 * rc.a2, q2, fma(rc.a4, q4, 1.0));
+    }
+  });
+  e[v.idx] = 0.5 * rc.eps2 * us[0] * ku;
+  e[g.nv + v.idx] = 0.25 * rc.vol * well / (D + 1);
+}
+
+// ---------------------------------------------------------------------------
 // C = -eps^2 K - M_E(u) coefficients, symmetric storage:
 //   coef[0][v]   = C(v, v)
 //   coef[1+p][v] = C(v, v + pos_p)       (p = 0..NPOS-1)
@@ -502,6 +545,13 @@ void launch_initw_rhs(int dim, const Geom& g, const double* WK, const ResidualCo
   dim3 grd = grid_of(dim, g, 128);
   if (dim == 2) launch_k(k_initw_rhs<2>, grd, 128, 0, s, g, WK, rc, u, out);
   else launch_k(k_initw_rhs<3>, grd, 128, 0, s, g, WK, rc, u, out);
+}
+
+void launch_energy_local(int dim, const Geom& g, const double* WK, const ResidualCoefs& rc, const double* u,
+                         double* e, cudaStream_t s) {
+  dim3 grd = grid_of(dim, g, 128);
+  if (dim == 2) launch_k(k_energy_local<2>, grd, 128, 0, s, g, WK, rc, u, e);
+  else launch_k(k_energy_local<3>, grd, 128, 0, s, g, WK, rc, u, e);
 }
 
 void launch_assemble_c(int dim, const Geom& g, const ResidualCoefs& rc, const double* u, double* coef,

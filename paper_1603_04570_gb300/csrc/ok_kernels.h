@@ -35,6 +35,9 @@ void launch_residual(int dim, const Geom& g, const double* WM, const double* WK,
                      cudaStream_t s);
 void launch_initw_rhs(int dim, const Geom& g, const double* WK, const ResidualCoefs& rc, const double* u,
                       double* out, cudaStream_t s);
+// e[v] = eps^2/2 u_v (K u)_v, e[N_v + v] = vertex share of 1/4 int (1 - u_h^2)^2 (2 N_v values)
+void launch_energy_local(int dim, const Geom& g, const double* WK, const ResidualCoefs& rc, const double* u,
+                         double* e, cudaStream_t s);
 void launch_assemble_c(int dim, const Geom& g, const ResidualCoefs& rc, const double* u, double* coef,
                        float* coef32, cudaStream_t s);
 template <typename TZ>
@@ -85,6 +88,24 @@ cudaError_t prepare_coarse_gemv(long long nc);
 template <typename T, typename TX, typename TY>
 void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha,
                      const TY* y0, T beta, cudaStream_t s);
+// ---- 3D steps by z-marching blocks (ok_plane3.cu) -------------------------
+// The same operations as launch_resid_init / launch_cheb_step /
+// launch_cheb_last (with r) / launch_op_apply on a 3D level, bitwise equal;
+// each value of the stencil vector is read once per block (plane ring in
+// shared memory).
+template <typename T>
+void launch_resid_init3(const Geom& g, const T* W, const T* dinv, const T* b, const T* x, T* r, T* d, T inv_th,
+                        cudaStream_t s);
+template <typename T>
+void launch_cheb_step3(const Geom& g, const T* W, const T* dinv, T* x, T* r, const T* d_in, T* d_out, T c1, T c2,
+                       bool first, cudaStream_t s);
+template <typename T, typename TO>
+void launch_cheb_last3(const Geom& g, const T* W, T* x, T* r, const T* d_in, bool first, TO* out, T oscale,
+                       cudaStream_t s);
+template <typename T, typename TX, typename TY>
+void launch_op_apply3(const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha, const TY* y0, T beta,
+                      cudaStream_t s);
+
 // Fused coarse V-cycle: levels Lc..L of the hierarchy in one thread block with
 // every level vector in shared memory (x, b, r, d0, d1 at off[l]).
 constexpr int COARSE_MAXLEV = 8;

@@ -5,8 +5,8 @@ Sec. 4 reports the average number of outer Krylov iterations per Newton step
 dx = eps / 2 and dt = eps^2).  Flat counts are the preconditioner's claim.
 This module runs the same experiments through the library:
 
-    python -m paper_1603_04570_gb300.experiments table1 [--sizes 32 64 128 256] [--steps 3]
-    python -m paper_1603_04570_gb300.experiments table2 [--steps 3]
+    python -m paper_1603_04570_gb300.experiments table1 [--sizes 50 100 200 400] [--steps 3]
+    python -m paper_1603_04570_gb300.experiments table2 [--sizes 100 200 400] [--steps 3]
     python -m paper_1603_04570_gb300.experiments refine2d [--sizes 128 256 512 1024] [--steps 2]
     python -m paper_1603_04570_gb300.experiments spectrum [--workloads 2d_n1024 3d_n128] [--steps 2]
 
@@ -24,10 +24,14 @@ ten Chebyshev steps for A~^{-1}, two Richardson steps of S~^{-1} (k_R = 2),
 five V-cycles per S_hat^{-1}.  The paper does not state its Krylov and Newton
 tolerances; its solver (FEniCS over PETSc) defaults to a relative Krylov
 tolerance of 1e-5 and a relative Newton tolerance of 1e-8, which these runs
-use unless --gmres-rtol is given.  Meshes: n must be divisible by a power of
-two for the geometric hierarchy, so the sizes stand in for the paper's
-50..800 cells per side.  Each line printed is a JSON record; --markdown
-prints a table.
+use unless --gmres-rtol is given.  Meshes: the paper's own, n = 50 2^k cells
+per side (Table 1: 50, 100, 200, 400; the 800 row needs about 1e9 DoF, more
+than one GPU holds with FGMRES(30)); Table 2 takes dx = eps / 2, i.e.
+n = 2 / eps = 100, 200, 400 for eps = 0.02, 0.01, 0.005.  The geometric
+hierarchy halves n while it is even, down to the 26^3 level of n = 25,
+which is solved by Chebyshev iteration to round-off (it is too large for the
+dense inverse).  Each line printed is a JSON record; --markdown prints a
+table.
 """
 from __future__ import annotations
 
@@ -74,7 +78,7 @@ def table1(sizes, steps, k_R, **kw):
         yield run(oi.scaled(oi.PAPER_3D, n), steps, k_R, **kw)
 
 
-def table2(steps, k_R, ns=(64, 128, 256), **kw):
+def table2(steps, k_R, ns=(100, 200, 400), **kw):
     # dx = eps / 2: eps = 2 / n, dt = eps^2
     for n in ns:
         eps = 2.0 / n
@@ -140,9 +144,10 @@ def main(argv=None):
     a = ap.parse_args(argv)
     prec = OK_FP64 if a.fp64 else OK_MIXED
     if a.experiment == "table1":
-        rows = table1(a.sizes or [32, 64, 128, 256], a.steps, a.k_r or 2, precision=prec, gmres_rtol=a.gmres_rtol)
+        rows = table1(a.sizes or [50, 100, 200, 400], a.steps, a.k_r or 2, precision=prec, gmres_rtol=a.gmres_rtol)
     elif a.experiment == "table2":
-        rows = table2(a.steps, a.k_r or 2, precision=prec, gmres_rtol=a.gmres_rtol)
+        rows = table2(a.steps, a.k_r or 2, ns=tuple(a.sizes or (100, 200, 400)), precision=prec,
+                      gmres_rtol=a.gmres_rtol)
     elif a.experiment == "spectrum":
         rows = spectrum(a.workloads or ["2d_n1024", "paper_3d"], a.steps, precision=prec)
     else:

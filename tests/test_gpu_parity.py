@@ -112,11 +112,14 @@ def test_preconditioner_parity(dim, n, k_R, precision):
         assert rel_inf(zh[nv:], ref[nv:]) < tol
 
 
-@pytest.mark.parametrize("dim,n,cmax", [(2, 64, 16), (2, 160, 40), (3, 24, 12)])
+@pytest.mark.parametrize("dim,n,cmax", [(2, 64, 16), (2, 160, 40), (3, 24, 12), (2, 150, 4), (3, 50, 4)])
 @pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
 def test_preconditioner_parity_large_coarse_level(dim, n, cmax, precision):
     """Coarsest level solved exactly at 17^2, 41^2 (multi-block solve) and 13^3
-    unknowns: the oracle with the same hierarchy."""
+    unknowns; above 4913 unknowns (76^2 from n = 150, and the 26^3 of n = 50,
+    the coarsest level of the paper's meshes n = 50 2^k) the GPU solves it by
+    Chebyshev--Jacobi iteration to 1e-13 (float64) / 1e-8 (float32) and the
+    oracle exactly (sparse LU): the same tolerances hold."""
     sysm, p, rng = make(dim, n, seed=12, dt=1e-4)
     nv = sysm.mesh.nv
     u = rng.uniform(-1.0, 1.0, nv)
@@ -371,6 +374,30 @@ def test_tile_kernels_are_bitwise_identical(n, precision):
         assert np.array_equal(out[0], out[k]), k
 
 
+@pytest.mark.parametrize("n,coarse_max", [(24, 4), (30, 15), (16, 16), (36, 9), (64, 16)])
+@pytest.mark.parametrize("k_R", [1, 2])
+@pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
+def test_plane_kernels_3d_are_bitwise_identical(n, coarse_max, k_R, precision):
+    """3D stencil steps by z-marching blocks (tile_fine != 0) against one
+    thread per vertex (tile_fine = 0): the same arithmetic, the same bits, on
+    grids whose sides are not multiples of the 32 x 8 tile or the 16-plane
+    chunk (25^3, 31^3 over a dense 16^3 level, 17^3 alone (only the mass
+    solve and M apply step), 37^3, 65^3), with k_R = 1 and 2 (which adds the
+    dt theta K y product)."""
+    sysm, p, rng = make(3, n, seed=16, dt=1e-4)
+    nv = sysm.mesh.nv
+    u = dev(rng.uniform(-1.0, 1.0, nv))
+    v = dev(rng.standard_normal(2 * nv))
+    out = []
+    for tile in (0, 1):
+        with ok.Grid(3, n, **p, precision=precision, tile_fine=tile, k_R=k_R, coarse_max=coarse_max,
+                     n_V=2) as g:
+            z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+            g.apply_preconditioner(u, v, z)
+            out.append(host(z))
+    assert np.array_equal(out[0], out[1])
+
+
 @pytest.mark.parametrize("dim,n", [(2, 128), (3, 16)])
 @pytest.mark.parametrize("graphs", [0, 1])
 def test_programmatic_dependent_launch_is_bitwise_identical(dim, n, graphs):
@@ -398,6 +425,11 @@ def test_experiments_module_runs():
     assert [r["n"] for r in rows] == [8, 16]
     for r in rows:
         assert r["newton_steps"] >= 1 and 1 <= r["its_per_newton"] <= 30
+    # the paper's smallest mesh (Table 1, n = 50: 265,302 DoF; hierarchy 50, 25
+    # with the 26^3 coarsest level solved by Chebyshev iteration): the paper
+    # reports 8.2 iterations per Newton step
+    (r,) = experiments.table1([50], steps=1, k_R=2)
+    assert r["dofs"] == 265302 and r["newton_steps"] >= 1 and r["its_per_newton"] <= 12
     # spectral diagnostics on the 32^2 workload: Ritz values of the Newton solve
     # and of a random right-hand side inside Lemma 2's enclosure (widened for
     # the inexact preconditioner), the eigenvalue 1 found
@@ -533,3 +565,45 @@ def test_arnoldi_matrix_and_ritz_values_parity(dim, n, precision):
     est = _lsq_resid(H, np.linalg.norm(f)) / np.linalg.norm(f)
     assert abs(est - info.rel_resid) <= 1e-2 * info.rel_resid + 1e-14
 
+
+
+@pytest.mark.parametrize("dim,n", [(2, 8), (2, 33), (2, 160), (3, 4), (3, 24)])
+@pytest.mark.parametrize("precision", [ok.OK_FP64, ok.OK_MIXED])
+def test_energy_parity(dim, n, precision):
+    """The Ohta--Kawasaki energy (Sec. 1) term by term against the oracle: the
+    interfacial and double-well terms are sums of exact per-vertex integrals
+    (1e-12 relative), the nonlocal term goes through the GPU's preconditioned
+    CG solve of the Neumann problem to 1e-12 (1e-9 relative); the energy is
+    float64 whatever the solver precision."""
+    sysm, p, rng = make(dim, n, seed=40)
+    nv = sysm.mesh.nv
+    u = p["m"] + 0.6 * rng.uniform(-1, 1, nv)
+    ref = sysm.energy(u)
+    with ok.Grid(dim, n, **p, precision=precision) as g:
+        terms, total = g.energy(dev(u))
+        terms_h, _ = g.energy(u)                     # host array: the staging path
+    assert abs(terms[0] - ref["gradient"]) <= 1e-12 * ref["gradient"]
+    assert abs(terms[1] - ref["double_well"]) <= 1e-12 * ref["double_well"]
+    assert abs(terms[2] - ref["nonlocal"]) <= 1e-9 * ref["nonlocal"]
+    assert abs(total - ref["total"]) <= 1e-9 * ref["total"] and terms_h == terms
+
+
+def test_energy_of_constant_state_and_along_timesteps():
+    """A constant state has only the double-well term, (1 - c^2)^2 / 4; along
+    implicit (theta = 1) timesteps of the 32^2 workload from a larger
+    perturbation the energy decreases every step (the equations are the
+    H^{-1} gradient flow of E)."""
+    wl = oi.SMALL_2D
+    with ok.Grid(2, 32, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, gmres_rtol=1e-12, newton_extra=1) as g:
+        nv = g.nv
+        terms, total = g.energy(torch.full((nv,), 0.3, dtype=torch.float64, device="cuda"))
+        assert abs(terms[0]) < 1e-14 and abs(terms[2]) < 1e-14 and abs(total - 0.25 * (1 - 0.09) ** 2) < 1e-14
+        u = dev(0.3 * np.random.default_rng(3).uniform(-1, 1, nv))
+        w = torch.empty_like(u)
+        g.init_w(u, w)
+        prev = g.energy(u)[1]
+        for _ in range(4):
+            g.timestep(u, w)
+            e = g.energy(u)[1]
+            assert e < prev
+            prev = e

@@ -13,7 +13,8 @@ import math
 import numpy as np
 import pytest
 
-from oracle.fem import Mesh, Params, System, mass_matrix, me_matrix, nonlinear_term, stiffness_matrix
+from oracle.fem import (Mesh, Params, System, double_well_integral, mass_matrix, me_matrix, nonlinear_term,
+                        stiffness_matrix)
 
 
 def center_index(dim, n):
@@ -206,3 +207,66 @@ def test_initial_w_chebyshev_equals_lu(dim, n):
     u0 = 0.1 + 0.5 * np.random.default_rng(4).uniform(-1, 1, sysm.mesh.nv)
     a, b = sysm.initial_w(u0), sysm.initial_w(u0, solver="chebyshev")
     assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+# --------------------------------------------------------------------------
+# the Ohta--Kawasaki energy (Sec. 1)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n", [(2, 3), (3, 2)])
+def test_double_well_integral_vs_quadrature(dim, n):
+    """int (1 - u_h^2)^2 against the independent collapsed Gauss--Legendre rule
+    (exact for the degree-4 integrand)."""
+    u = np.random.default_rng(8).uniform(-1.3, 1.3, Mesh(dim, n).nv)
+    mesh = Mesh(dim, n)
+    lam, wts = duffy_rule(dim)
+    ref = 0.0
+    for s, vol in zip(mesh.simplices, mesh.volume):
+        uh = lam @ u[s]
+        ref += math.factorial(dim) * vol * np.sum(wts * (1 - uh ** 2) ** 2)
+    assert abs(double_well_integral(mesh, u) - ref) <= 1e-14 * abs(ref)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 5), (3, 3)])
+def test_energy_of_constant_state(dim, n):
+    """u = c: no gradient, f = u - m is constant so its mean-free part vanishes,
+    and the double well integrates to (1 - c^2)^2 |Omega| / 4 with |Omega| = 1."""
+    c = 0.3
+    sysm = System(Mesh(dim, n), Params(0.05, 70.0, -0.2, 0.5, 1e-3))
+    E = sysm.energy(np.full(sysm.mesh.nv, c))
+    assert abs(E["gradient"]) < 1e-15 and abs(E["nonlocal"]) < 1e-14
+    assert abs(E["double_well"] - 0.25 * (1 - c * c) ** 2) < 1e-15
+
+
+@pytest.mark.parametrize("dim,n", [(2, 6), (3, 3)])
+def test_energy_of_a_discrete_eigenmode(dim, n):
+    """u = m + a v with K v = lam M v (so 1^T M v = 0 for lam > 0): the inverse
+    Neumann Laplacian of a v is a v / lam, so
+        gradient = eps^2/2 a^2 lam v^T M v,   nonlocal = sigma/2 a^2 v^T M v / lam,
+    closed forms that do not go through the oracle's bordered solve."""
+    import scipy.linalg as sla
+    eps, sigma, m, a = 0.06, 120.0, 0.15, 0.4
+    sysm = System(Mesh(dim, n), Params(eps, sigma, m, 0.5, 1e-3))
+    lam, Q = sla.eigh(sysm.K.toarray(), sysm.M.toarray())
+    for k in (1, 3, len(lam) // 2):
+        v = Q[:, k]
+        vMv = v @ (sysm.M @ v)
+        E = sysm.energy(m + a * v)
+        assert abs(E["gradient"] - 0.5 * eps ** 2 * a * a * lam[k] * vMv) <= 1e-12 * E["gradient"]
+        assert abs(E["nonlocal"] - 0.5 * sigma * a * a * vMv / lam[k]) <= 1e-10 * E["nonlocal"]
+
+
+def test_energy_decreases_along_implicit_timesteps():
+    """The Ohta--Kawasaki equation is the H^{-1} gradient flow of E (Sec. 1);
+    with theta = 1 and a small step the discrete energy decreases every step
+    (the 32^2 workload's parameters, a larger initial perturbation)."""
+    from oracle.solvers import Options, timestep
+    rng = np.random.default_rng(12)
+    sysm = System(Mesh(2, 16), Params(0.04, 100.0, 0.0, 1.0, 1e-4))
+    u = 0.3 * rng.uniform(-1, 1, sysm.mesh.nv)
+    w = sysm.initial_w(u)
+    prev = sysm.energy(u)["total"]
+    for _ in range(4):
+        u, w, info = timestep(sysm, u, w, Options(linear="direct", newton_atol=1e-12, newton_extra=1))
+        e = sysm.energy(u)["total"]
+        assert info["converged"] and e < prev
+        prev = e

@@ -376,3 +376,19 @@ def test_residual_at_the_previous_state_is_the_full_explicit_step(theta):
     ua, wa = rng.uniform(-1, 1, nv), rng.uniform(-1, 1, nv)
     F1 = System(Mesh(2, 5), Params(p.eps, p.sigma, p.m, 1.0, p.dt)).residual(ua, wa, un, wn)[:nv]
     assert np.abs(F1 - (F[:nv] + sysm.M @ (un - ua))).max() <= 1e-14 * np.abs(F1).max()
+
+
+def test_large_coarse_level_is_solved_exactly():
+    """A coarsest level above 5000 unknowns (2D n = 150 -> 75: 76^2) is solved by
+    sparse LU: the coarse solve satisfies S_hat x = b to round-off, like the
+    dense solve of the small coarse levels."""
+    mg = Multigrid(2, 150, 3e-3, coarse_max=4)
+    assert mg.sizes == [150, 75] and mg.coarse_lu is not None
+    b = np.random.default_rng(5).standard_normal(76 * 76)
+    x = mg.coarse_solve(b)
+    A = mg.A[-1]
+    assert np.abs(A @ x - b).max() <= 1e-13 * (abs(A) @ np.abs(x)).max()      # backward error
+    assert np.abs(A @ x - b).max() <= 1e-9 * np.abs(b).max()
+    small = Multigrid(2, 16, 3e-3, coarse_max=4)
+    xs = small.coarse_solve(b[:25])
+    assert np.linalg.norm(small.A[-1] @ xs - b[:25]) <= 1e-12 * np.linalg.norm(b[:25])
