@@ -103,10 +103,13 @@ typedef struct ok_opts {
                          one thread-block cluster (when the device supports
                          it), otherwise as 1 [1]                                 */
   int tile_fine;      /* 2D: register-strip tile kernels on the fine levels:
-                         0 off, 1 automatic window width, 2 / 3 force 32 / 64
+                         0 off, 1 window width per level chosen by the
+                         autotuner (ok_grid_tuning), 2 / 3 force 32 / 64
                          columns; 3D: any nonzero value runs the multigrid's
-                         stencil steps by z-marching blocks (0: one thread per
-                         vertex; both give the same bits) [1]                   */
+                         stencil steps by z-marching blocks, with 1 their block
+                         shape per level from the autotuner, 4 + k shape k on
+                         every level, 2 and 3 shape 0 (0: one thread per
+                         vertex; all give the same bits) [1]                    */
   int use_pdl;        /* programmatic dependent launch between kernels [1]      */
   int reorth;         /* Gram--Schmidt: 0 second pass only when the first one
                          cancels more than half of ||w||^2, 1 always two
@@ -340,6 +343,18 @@ int ok_hessenberg_eigenvalues(int k, const double* H, int ldh, double* re, doubl
  * Errors are reported through ok_last_error(). */
 int ok_apply_jacobian_noalloc(int dim, int n, const ok_params* p, const double* u_k, const double* z,
                               double* y, ok_stream stream);
+
+/* Choices of the autotuner (no counterpart in the paper).  With
+ * tile_fine = 1, ok_grid_create times the compiled kernel shapes of each
+ * multigrid level once per (device, dim, n, precision) in the process and
+ * keeps the fastest: in 2D the register-strip window width (32 or 64
+ * columns) of every tiled level, in 3D the block shape of the z-marching
+ * stencil kernels (0: 32 x 8 columns by 16 planes, 1: 32 x 4 by 32, 2: 64 x 4
+ * by 16, 3: 32 x 8 by 32).  All choices give the same bits.  Writes up to
+ * `max` (level cells per side, choice) pairs, finest level first, into the
+ * HOST arrays level_n and choice, their number into *count (0 when nothing
+ * was tuned). */
+int ok_grid_tuning(const ok_grid* g, int* level_n, int* choice, int max, int* count);
 
 /* The Ohta--Kawasaki free energy (Sec. 1, the functional E[u] whose H^{-1}
  * gradient flow eqns oka/okb are) of the P1 function with nodal values u

@@ -113,6 +113,7 @@ def load(build: bool = True):
         "ok_profile_read": (c_int, [P, POINTER(KernelStat), c_int, POINTER(c_int)]),
         "ok_launch_count": (c_longlong, []),
         "ok_energy": (c_int, [P, P, P, P, P]),
+        "ok_grid_tuning": (c_int, [P, POINTER(c_int), POINTER(c_int), c_int, POINTER(c_int)]),
         "ok_apply_jacobian_noalloc": (c_int, [c_int, c_int, POINTER(Params), P, P, P, P]),
         "ok_arnoldi_hessenberg": (c_int, [P, P, c_int, c_int, POINTER(c_int), P]),
         "ok_ritz_values": (c_int, [P, P, P, c_int, POINTER(c_int), P]),
@@ -322,6 +323,13 @@ def ok_energy(h, nv, u, stream=None):
     return [terms[0], terms[1], terms[2]], total.value
 
 
+def ok_grid_tuning(h):
+    """[(level cells per side, choice)] the autotuner recorded for the handle."""
+    n, c, k = (c_int * 64)(), (c_int * 64)(), c_int()
+    _check(load().ok_grid_tuning(h, n, c, 64, byref(k)))
+    return [(n[i], c[i]) for i in range(k.value)]
+
+
 def ok_launch_count() -> int:
     return load().ok_launch_count()
 
@@ -411,6 +419,9 @@ class Grid:
 
     def timestep(self, u, w, stream=None, check=True):
         return ok_timestep(self.handle, self.nv, u, w, stream, check)
+
+    def tuning(self):
+        return ok_grid_tuning(self.handle)
 
     def energy(self, u, stream=None):
         return ok_energy(self.handle, self.nv, u, stream)

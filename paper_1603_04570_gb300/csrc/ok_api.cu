@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <new>
 #include <string>
@@ -313,6 +314,13 @@ template <typename T> struct Prec {
   }
 
   bool plane3 = false;         // 3D: stencil steps by z-marching blocks (ok_plane3.cu)
+  std::vector<int> pshape;     // per level: block shape of the z-marching kernels
+  std::vector<std::pair<int, int>> tuned;   // (cells per side, choice) the autotuner recorded
+  int plane_shape(const Geom& g) const {
+    for (size_t l = 0; l < lv.size(); ++l)
+      if (lv[l].g.n == g.n) return l < pshape.size() ? pshape[l] : 0;
+    return 0;
+  }
 
   // out = n_V V-cycles from zero on the level-0 system with right-hand side rhs
   void solve_mg(const T* rhs, T* out, cudaStream_t s) {
@@ -329,25 +337,27 @@ template <typename T> struct Prec {
             int steps, double th, const std::vector<double>& c1, const std::vector<double>& c2, TO* out,
             T oscale, bool want_r, cudaStream_t s, int tag = -1) {
     if (x_zero) launch_cheb_init<T, TB>(dim, g, dinv, b, (T)1, r, d0, (T)(1.0 / th), s);
-    else if (plane3) launch_resid_init3<T>(g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s);
+    else if (plane3) launch_resid_init3<T>(g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s, plane_shape(g));
     else launch_resid_init<T>(dim, g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s);
     T* d[2] = {d0, d1};
     int cur = 0;
     for (int k = 0; k + 1 < steps; ++k) {
       if (k == 0 && prof) prof->begin(tag, s);
       if (plane3)
-        launch_cheb_step3<T>(g, W, dinv, x, r, d[cur], d[1 - cur], (T)c1[k], (T)c2[k], x_zero && k == 0, s);
+        launch_cheb_step3<T>(g, W, dinv, x, r, d[cur], d[1 - cur], (T)c1[k], (T)c2[k], x_zero && k == 0, s,
+                             plane_shape(g));
       else
         launch_cheb_step<T>(dim, g, W, dinv, x, r, d[cur], d[1 - cur], (T)c1[k], (T)c2[k], x_zero && k == 0, s);
       if (k == 0 && prof) prof->end(tag, s);
       cur ^= 1;
     }
-    if (plane3 && want_r) launch_cheb_last3<T, TO>(g, W, x, r, d[cur], x_zero && steps == 1, out, oscale, s);
+    if (plane3 && want_r)
+      launch_cheb_last3<T, TO>(g, W, x, r, d[cur], x_zero && steps == 1, out, oscale, s, plane_shape(g));
     else launch_cheb_last<T, TO>(dim, g, W, x, want_r ? r : nullptr, d[cur], x_zero && steps == 1, out, oscale, s);
   }
   // y = alpha W x on level g (M x, or dt theta K y for k_R = 2)
   void op(const Geom& g, const T* W, bool axis_only, const T* x, T* y, T alpha, cudaStream_t s) {
-    if (plane3) launch_op_apply3<T, T, T>(g, W, axis_only, x, y, alpha, (const T*)nullptr, (T)0, s);
+    if (plane3) launch_op_apply3<T, T, T>(g, W, axis_only, x, y, alpha, (const T*)nullptr, (T)0, s, plane_shape(g));
     else launch_op_apply<T, T, T>(dim, g, W, axis_only, x, y, alpha, (const T*)nullptr, (T)0, s);
   }
 
@@ -477,6 +487,101 @@ struct EnergyWork {
 };
 
 namespace {
+
+// ---------------------------------------------------------------------------
+// autotuner: the tile width (2D register-strip kernels) or block shape (3D
+// z-marching kernels) of each multigrid level, chosen by timing the level's
+// kernels once per (device, dim, n, precision) and cached for the process.
+// Every choice computes the same bits, so only the time depends on it.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::array<int, 5>, int> g_tune;   // (device, dim, n, sizeof(T), 0) -> choice
+
+template <typename F>
+float time_launches(F&& launch, int reps) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  launch();
+  launch();                                        // warm-up
+  CK(cudaEventRecord(e0, 0));
+  for (int k = 0; k < reps; ++k) launch();
+  CK(cudaEventRecord(e1, 0));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CKL();
+  return ms / reps;
+}
+
+template <typename T>
+void autotune(ok_grid* G, Prec<T>& P) {
+  const int nl = (int)P.lv.size();
+  P.pshape.assign(nl, G->o.tile_fine >= 4 ? G->o.tile_fine - 4 : 0);   // 3D: 4 + k forces shape k
+  if (G->o.tile_fine != 1) return;
+  auto cached = [&](int n, int& out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find({G->device, G->dim, n, (int)sizeof(T), 0});
+    if (it == g_tune.end()) return false;
+    out = it->second;
+    return true;
+  };
+  auto store = [&](int n, int v) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[{G->device, G->dim, n, (int)sizeof(T), 0}] = v;
+  };
+  if (P.tiled) {                                   // 2D: window width 32 or 64 per tiled level
+    const int top = P.fused ? P.Lc : nl - 1;
+    for (int l = 0; l < top && l + 1 < nl; ++l) {
+      Level<T>& L = P.lv[l];
+      Level<T>& C = P.lv[l + 1];
+      int best = 0;
+      if (!cached(L.n, best)) {
+        T* fine[] = {L.x, L.xa, L.b};
+        T* coarse[] = {C.b, C.x};
+        for (T* v : fine) CK(cudaMemset(v, 0, L.g.nv * sizeof(T)));
+        for (T* v : coarse) CK(cudaMemset(v, 0, C.g.nv * sizeof(T)));
+        float tbest = 0.f;
+        const int widths[] = {32, 64};
+        for (int w : widths) {
+          TileSmooth<T> ts = P.ts[l];
+          ts.tile = w;
+          const float t = time_launches([&] {
+            launch_tile_pre<T>(ts, (const T*)nullptr, L.b, L.xa, C.b, 0);
+            launch_tile_post<T, T>(ts, L.xa, C.x, L.b, L.x, (T*)nullptr, (T*)nullptr, (T)1, 0);
+          }, 5);
+          if (best == 0 || t < tbest) best = w, tbest = t;
+        }
+        store(L.n, best);
+      }
+      P.ts[l].tile = best;
+      P.tuned.push_back({L.n, best});
+    }
+  } else if (P.plane3) {                           // 3D: block shape per level of the z-marching kernels
+    const int top = P.fused ? P.Lc : nl;
+    for (int l = 0; l < top; ++l) {
+      Level<T>& L = P.lv[l];
+      if (l + 1 == nl && !P.cheb_coarse) break;    // dense coarsest solve: no stencil steps
+      int best = -1;
+      if (!cached(L.n, best)) {
+        T* vs[] = {L.x, L.r, L.d0, L.d1};
+        for (T* v : vs) CK(cudaMemset(v, 0, L.g.nv * sizeof(T)));
+        float tbest = 0.f;
+        for (int sh = 0; sh < PLANE_SHAPES; ++sh) {
+          const float t = time_launches([&] {
+            launch_cheb_step3<T>(L.g, L.WS, L.dinvS, L.x, L.r, L.d0, L.d1, (T)0.5, (T)0.5, false, 0, sh);
+          }, 5);
+          if (best < 0 || t < tbest) best = sh, tbest = t;
+        }
+        store(L.n, best);
+      }
+      P.pshape[l] = best;
+      P.tuned.push_back({L.n, best});
+    }
+  }
+}
 
 // The multigrid hierarchy of M + gamma K (gamma < 0: S_hat's eps sqrt(c)) and
 // the rest of the block preconditioner's workspace.
@@ -733,6 +838,8 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
       P.low_cluster = low_cluster;
     }
   }
+  autotune<T>(G, P);
+  CK(cudaStreamSynchronize(0));
 }
 
 void validate(int dim, int n, const ok_params* p, const ok_opts* o) {
@@ -756,7 +863,8 @@ void validate(int dim, int n, const ok_params* p, const ok_opts* o) {
     fail(OK_ERR_INVALID_ARG, "tolerances must be positive");
   if (!(o->smooth_lo_frac > 0 && o->smooth_lo_frac < 1)) fail(OK_ERR_INVALID_ARG, "smooth_lo_frac in (0,1)");
   if (o->coarse_max < 1) fail(OK_ERR_INVALID_ARG, "coarse_max must be >= 1");
-  if (o->tile_fine < 0 || o->tile_fine > 3) fail(OK_ERR_INVALID_ARG, "tile_fine must be 0, 1, 2 or 3");
+  if (o->tile_fine < 0 || o->tile_fine > (dim == 3 ? 7 : 3))
+    fail(OK_ERR_INVALID_ARG, "tile_fine must be 0, 1, 2 or 3 (3D: also 4..7)");
   if (o->reorth < 0 || o->reorth > 2) fail(OK_ERR_INVALID_ARG, "reorth must be 0, 1 or 2");
   if (o->fuse_coarse < 0 || o->fuse_coarse > 2) fail(OK_ERR_INVALID_ARG, "fuse_coarse must be 0, 1 or 2");
 }
@@ -1141,6 +1249,12 @@ void energy(ok_grid* G, const double* u, double out[3]) {
   launch_axpby<double, double>(nv, -mean, E.ones, 1.0, E.f, s);
   launch_op_apply<double, double, double>(dim, G->g0, G->WM0d, false, E.f, E.b, 1.0, (const double*)nullptr, 0.0,
                                           s);
+  CKL();
+  // 1^T b = 1^T M f = 0 up to rounding; remove that rounding (the component of
+  // b along the null vector 1 of K), else CG stalls at its size when f is
+  // itself at rounding level (a constant u)
+  const double bsum = dot(G, E.ones, E.b, nv);
+  launch_axpby<double, double>(nv, -bsum / (double)nv, E.ones, 1.0, E.b, s);
   CKL();
   // conjugate gradients for K x = b (consistent: 1^T b = 0), preconditioned by
   // two V-cycles for M + K (symmetric: the same Chebyshev polynomial before and
@@ -1639,6 +1753,21 @@ int ok_ritz_values(ok_grid* G, double* re, double* im, int max, int* count, ok_s
   }
   *count = k;
   g_last_error.clear();
+  return OK_SUCCESS;
+}
+
+int ok_grid_tuning(const ok_grid* G, int* level_n, int* choice, int max, int* count) {
+  if (!G || !count || max < 0 || (max > 0 && (!level_n || !choice))) {
+    g_last_error = "NULL argument or max < 0";
+    return OK_ERR_INVALID_ARG;
+  }
+  const auto& t = G->o.precision == OK_FP64 ? G->pd.tuned : G->pf.tuned;
+  const int k = std::min<int>(max, (int)t.size());
+  for (int i = 0; i < k; ++i) {
+    level_n[i] = t[i].first;
+    choice[i] = t[i].second;
+  }
+  *count = k;
   return OK_SUCCESS;
 }
 

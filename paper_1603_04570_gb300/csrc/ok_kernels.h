@@ -93,18 +93,21 @@ void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const T
 // launch_cheb_last (with r) / launch_op_apply on a 3D level, bitwise equal;
 // each value of the stencil vector is read once per block (plane ring in
 // shared memory).
+// `shape` selects the block shape (0..PLANE_SHAPES-1: 32x8 columns x 16
+// planes, 32x4 x 32, 64x4 x 16, 32x8 x 32).
+constexpr int PLANE_SHAPES = 4;
 template <typename T>
 void launch_resid_init3(const Geom& g, const T* W, const T* dinv, const T* b, const T* x, T* r, T* d, T inv_th,
-                        cudaStream_t s);
+                        cudaStream_t s, int shape);
 template <typename T>
 void launch_cheb_step3(const Geom& g, const T* W, const T* dinv, T* x, T* r, const T* d_in, T* d_out, T c1, T c2,
-                       bool first, cudaStream_t s);
+                       bool first, cudaStream_t s, int shape);
 template <typename T, typename TO>
 void launch_cheb_last3(const Geom& g, const T* W, T* x, T* r, const T* d_in, bool first, TO* out, T oscale,
-                       cudaStream_t s);
+                       cudaStream_t s, int shape);
 template <typename T, typename TX, typename TY>
 void launch_op_apply3(const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha, const TY* y0, T beta,
-                      cudaStream_t s);
+                      cudaStream_t s, int shape);
 
 // Fused coarse V-cycle: levels Lc..L of the hierarchy in one thread block with
 // every level vector in shared memory (x, b, r, d0, d1 at off[l]).

@@ -1,7 +1,8 @@
 // ok_plane3.cu -- 3D stencil steps by z-marching thread blocks.
 //
 // A thread block owns a PX x PY tile of (x, y) columns, one thread per column,
-// and walks a chunk of PZ z-planes.  The vector the stencil reads is staged
+// and walks a chunk of PZ z-planes (four compiled shapes, chosen per level by
+// timing at setup).  The vector the stencil reads is staged
 // plane by plane into a ring of four shared-memory planes of (PY + 2) x
 // (PX + 2) values (the tile and a one-vertex ring around it, zero outside the
 // domain, which is the value load_nb gives an absent neighbour).  The 15
@@ -26,10 +27,18 @@
 
 namespace okg {
 
-constexpr int PX = 32, PY = 8, PZ = 16;            // columns per tile, z-planes per block
-constexpr int PW = PX + 2, PH = PY + 2;            // padded plane
-constexpr int PNT = PX * PY;                       // threads
-constexpr int PSLOT = (PW * PH + PNT - 1) / PNT;   // padded-plane elements loaded per thread
+// Block shapes (PX x PY columns, PZ planes); the autotuner of the multigrid
+// setup picks one per level by timing (all give the same bits).
+template <int PX_, int PY_, int PZ_> struct PShape {
+  static constexpr int PX = PX_, PY = PY_, PZ = PZ_;
+  static constexpr int PW = PX + 2, PH = PY + 2;            // padded plane
+  static constexpr int PNT = PX * PY;                       // threads
+  static constexpr int PSLOT = (PW * PH + PNT - 1) / PNT;   // padded-plane elements staged per thread
+};
+using PShape0 = PShape<32, 8, 16>;
+using PShape1 = PShape<32, 4, 32>;
+using PShape2 = PShape<64, 4, 16>;
+using PShape3 = PShape<32, 8, 32>;
 constexpr int NTAB3 = Topo<3>::NCLASS * Topo<3>::NOFF;
 
 enum PlaneMode { PM_RESID = 0, PM_STEP = 1, PM_LAST = 2, PM_OP = 3 };
@@ -97,9 +106,10 @@ __device__ __forceinline__ void plane_update(const PlaneArgs<T, TS, TO>& a, cons
   }
 }
 
-template <typename T, typename TS, typename TO, int MODE>
-__global__ void __launch_bounds__(PNT) k_plane3(PlaneArgs<T, TS, TO> a) {
+template <typename T, typename TS, typename TO, int MODE, class C>
+__global__ void __launch_bounds__(C::PNT) k_plane3(PlaneArgs<T, TS, TO> a) {
   using Tp = Topo<3>;
+  constexpr int PX = C::PX, PY = C::PY, PZ = C::PZ, PW = C::PW, PH = C::PH, PNT = C::PNT, PSLOT = C::PSLOT;
   __shared__ T sW[NTAB3];
   __shared__ T sD[Tp::NCLASS];
   __shared__ T ring[4][PH][PW];
@@ -205,13 +215,24 @@ __global__ void __launch_bounds__(PNT) k_plane3(PlaneArgs<T, TS, TO> a) {
   }
 }
 
+template <class C>
 static inline dim3 plane_grid(const Geom& g) {
-  return dim3((g.n1 + PX - 1) / PX, (g.n1 + PY - 1) / PY, (g.n1 + PZ - 1) / PZ);
+  return dim3((g.n1 + C::PX - 1) / C::PX, (g.n1 + C::PY - 1) / C::PY, (g.n1 + C::PZ - 1) / C::PZ);
+}
+
+template <typename T, typename TS, typename TO, int MODE>
+static void launch_plane(const PlaneArgs<T, TS, TO>& a, int shape, cudaStream_t s) {
+  switch (shape) {
+    case 1: launch_k(k_plane3<T, TS, TO, MODE, PShape1>, plane_grid<PShape1>(a.g), PShape1::PNT, 0, s, a); break;
+    case 2: launch_k(k_plane3<T, TS, TO, MODE, PShape2>, plane_grid<PShape2>(a.g), PShape2::PNT, 0, s, a); break;
+    case 3: launch_k(k_plane3<T, TS, TO, MODE, PShape3>, plane_grid<PShape3>(a.g), PShape3::PNT, 0, s, a); break;
+    default: launch_k(k_plane3<T, TS, TO, MODE, PShape0>, plane_grid<PShape0>(a.g), PShape0::PNT, 0, s, a);
+  }
 }
 
 template <typename T>
 void launch_resid_init3(const Geom& g, const T* W, const T* dinv, const T* b, const T* x, T* r, T* d, T inv_th,
-                        cudaStream_t s) {
+                        cudaStream_t s, int shape) {
   PlaneArgs<T, T, T> a = {};
   a.g = g;
   a.W = W;
@@ -221,12 +242,12 @@ void launch_resid_init3(const Geom& g, const T* W, const T* dinv, const T* b, co
   a.d = d;
   a.b = b;
   a.inv_th = inv_th;
-  launch_k(k_plane3<T, T, T, PM_RESID>, plane_grid(g), PNT, 0, s, a);
+  launch_plane<T, T, T, PM_RESID>(a, shape, s);
 }
 
 template <typename T>
 void launch_cheb_step3(const Geom& g, const T* W, const T* dinv, T* x, T* r, const T* d_in, T* d_out, T c1, T c2,
-                       bool first, cudaStream_t s) {
+                       bool first, cudaStream_t s, int shape) {
   PlaneArgs<T, T, T> a = {};
   a.g = g;
   a.W = W;
@@ -238,12 +259,12 @@ void launch_cheb_step3(const Geom& g, const T* W, const T* dinv, T* x, T* r, con
   a.c1 = c1;
   a.c2 = c2;
   a.first = first ? 1 : 0;
-  launch_k(k_plane3<T, T, T, PM_STEP>, plane_grid(g), PNT, 0, s, a);
+  launch_plane<T, T, T, PM_STEP>(a, shape, s);
 }
 
 template <typename T, typename TO>
 void launch_cheb_last3(const Geom& g, const T* W, T* x, T* r, const T* d_in, bool first, TO* out, T oscale,
-                       cudaStream_t s) {
+                       cudaStream_t s, int shape) {
   PlaneArgs<T, T, TO> a = {};
   a.g = g;
   a.W = W;
@@ -253,12 +274,12 @@ void launch_cheb_last3(const Geom& g, const T* W, T* x, T* r, const T* d_in, boo
   a.out = out;
   a.oscale = oscale;
   a.first = first ? 1 : 0;
-  launch_k(k_plane3<T, T, TO, PM_LAST>, plane_grid(g), PNT, 0, s, a);
+  launch_plane<T, T, TO, PM_LAST>(a, shape, s);
 }
 
 template <typename T, typename TX, typename TY>
 void launch_op_apply3(const Geom& g, const T* W, bool axis_only, const TX* x, TY* y, T alpha, const TY* y0, T beta,
-                      cudaStream_t s) {
+                      cudaStream_t s, int shape) {
   PlaneArgs<T, TX, TY> a = {};
   a.g = g;
   a.W = W;
@@ -268,24 +289,25 @@ void launch_op_apply3(const Geom& g, const T* W, bool axis_only, const TX* x, TY
   a.alpha = alpha;
   a.beta = beta;
   a.axis_only = axis_only ? 1 : 0;
-  launch_k(k_plane3<T, TX, TY, PM_OP>, plane_grid(g), PNT, 0, s, a);
+  launch_plane<T, TX, TY, PM_OP>(a, shape, s);
 }
 
 #define OK_PLANE_INST(T)                                                                                      \
   template void launch_resid_init3<T>(const Geom&, const T*, const T*, const T*, const T*, T*, T*, T,         \
-                                      cudaStream_t);                                                          \
+                                      cudaStream_t, int);                                                     \
   template void launch_cheb_step3<T>(const Geom&, const T*, const T*, T*, T*, const T*, T*, T, T, bool,       \
-                                     cudaStream_t);                                                           \
-  template void launch_cheb_last3<T, T>(const Geom&, const T*, T*, T*, const T*, bool, T*, T, cudaStream_t);  \
+                                     cudaStream_t, int);                                                      \
+  template void launch_cheb_last3<T, T>(const Geom&, const T*, T*, T*, const T*, bool, T*, T, cudaStream_t,   \
+                                        int);                                                                 \
   template void launch_op_apply3<T, T, T>(const Geom&, const T*, bool, const T*, T*, T, const T*, T,          \
-                                          cudaStream_t);
+                                          cudaStream_t, int);
 OK_PLANE_INST(float)
 OK_PLANE_INST(double)
 template void launch_cheb_last3<float, double>(const Geom&, const float*, float*, float*, const float*, bool,
-                                               double*, float, cudaStream_t);
+                                               double*, float, cudaStream_t, int);
 template void launch_cheb_last3<float, __half>(const Geom&, const float*, float*, float*, const float*, bool,
-                                               __half*, float, cudaStream_t);
+                                               __half*, float, cudaStream_t, int);
 template void launch_cheb_last3<double, float>(const Geom&, const double*, double*, double*, const double*, bool,
-                                               float*, double, cudaStream_t);
+                                               float*, double, cudaStream_t, int);
 
 }  // namespace okg

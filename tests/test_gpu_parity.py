@@ -370,6 +370,11 @@ def test_tile_kernels_are_bitwise_identical(n, precision):
             z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
             g.apply_preconditioner(u, v, z)
             out.append(host(z))
+            if tile == 1:                              # the autotuner's window widths
+                tuned = g.tuning()
+                assert tuned and tuned[0][0] == n and all(c in (32, 64) for _, c in tuned)
+            elif tile != 1:
+                assert g.tuning() == []
     for k in range(1, len(out)):
         assert np.array_equal(out[0], out[k]), k
 
@@ -389,13 +394,17 @@ def test_plane_kernels_3d_are_bitwise_identical(n, coarse_max, k_R, precision):
     u = dev(rng.uniform(-1.0, 1.0, nv))
     v = dev(rng.standard_normal(2 * nv))
     out = []
-    for tile in (0, 1):
+    for tile in (0, 1, 4, 5, 6, 7):                  # per vertex, autotuned, each block shape forced
         with ok.Grid(3, n, **p, precision=precision, tile_fine=tile, k_R=k_R, coarse_max=coarse_max,
                      n_V=2) as g:
             z = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
             g.apply_preconditioner(u, v, z)
             out.append(host(z))
-    assert np.array_equal(out[0], out[1])
+            if tile == 1:
+                tuned = g.tuning()
+                assert tuned and all(0 <= c < 4 for _, c in tuned) and tuned[0][0] == n
+    for k in range(1, len(out)):
+        assert np.array_equal(out[0], out[k]), k
 
 
 @pytest.mark.parametrize("dim,n", [(2, 128), (3, 16)])
