@@ -219,10 +219,20 @@ typedef struct ok_batch_info {
   double seconds;      /* wall time of the whole batch                     */
 } ok_batch_info;
 
-/* Run every request to completion, one after another, on `stream` (no
- * counterpart in the paper).  Requests on distinct handles are independent;
- * a failing request does not stop the others.  Returns the status of the
- * first failed request. */
+/* Run every request to completion (no counterpart in the paper; the batching
+ * is this library's serving form).  Requests whose handles have the same grid
+ * (dim, n), options and multigrid structure form cohorts of up to 8 on
+ * distinct handles, in request order; a cohort advances timestep by timestep
+ * in lockstep, and every kernel of an Arnoldi step (the preconditioner's
+ * stencil and multigrid kernels, J z, the classical Gram--Schmidt passes) is
+ * ONE launch over all of its members still iterating.  Each member keeps its
+ * own Newton and FGMRES decisions, so its results are bitwise those of
+ * ok_timestep alone.  Cohorts need reorth = 1 (CGS2) and fuse_coarse != 2;
+ * other requests, and cohorts of one, run through ok_timestep.  Cohorts run
+ * one after another, ordered after `stream` and the members' earlier work;
+ * `stream` waits for the whole batch.  A failing request does not stop the
+ * others (its state is left as ok_timestep would leave it).  Returns the
+ * status of the first failed request. */
 int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream stream);
 
 /* Serving (no counterpart in the paper): whole simulations admitted

@@ -249,6 +249,7 @@ template <typename T> struct Prec {
   bool fused = false;          // coarse levels Lc..L run as one shared-memory kernel
   int Lc = 0;
   CoarseArgs<T> ca{};
+  CoarseArgs<T>* ca_dev = nullptr;   // device copy of ca (batched launches read it from there)
   size_t csmem = 0;
   bool low = false;            // 2D tiles: levels Lf.. and the coarsest solve in one cluster launch
   int Lf = 0, low_cluster = 0;
@@ -560,10 +561,13 @@ void autotune(ok_grid* G, Prec<T>& P) {
       P.tuned.push_back({L.n, best});
     }
   } else if (P.plane3) {                           // 3D: block shape per level of the z-marching kernels
+    // the levels whose stencil steps run by z-marching blocks: the finest (the
+    // mass solve and M apply run there) and every smoothed level above the
+    // fused part, the coarsest only when it is solved by Chebyshev iteration
     const int top = P.fused ? P.Lc : nl;
     for (int l = 0; l < top; ++l) {
       Level<T>& L = P.lv[l];
-      if (l + 1 == nl && !P.cheb_coarse) break;    // dense coarsest solve: no stencil steps
+      if (l > 0 && l + 1 == nl && !P.cheb_coarse) break;
       int best = -1;
       if (!cached(L.n, best)) {
         T* vs[] = {L.x, L.r, L.d0, L.d1};
@@ -767,6 +771,8 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
     ca.nu_post = P.nu_post;
     P.csmem = (size_t)off * sizeof(T);
     CK(prepare_coarse_vcycle<T>(dim, P.csmem));
+    P.ca_dev = (CoarseArgs<T>*)A.alloc<char>(sizeof(CoarseArgs<T>));
+    CK(cudaMemcpy(P.ca_dev, &P.ca, sizeof(CoarseArgs<T>), cudaMemcpyHostToDevice));
     P.fused = true;
     P.Lc = Lc;
   }
@@ -1291,6 +1297,538 @@ void energy(ok_grid* G, const double* u, double out[3]) {
   out[2] = 0.5 * G->p.sigma * xb;
 }
 
+// ---------------------------------------------------------------------------
+// Cohorts (ok_solve_batch): problems with the same grid, options and
+// multigrid structure advance in lockstep, and every kernel of an Arnoldi step
+// (the preconditioner's stencil and multigrid kernels, J z and the CGS2
+// orthogonalisation) runs as one launch over all of them.  Each problem's
+// arithmetic is the one it gets alone: same kernel bodies, same reduction
+// shapes, same stop decisions (taken per problem), so the results are bitwise
+// those of ok_timestep.
+// ---------------------------------------------------------------------------
+template <typename T>
+bool same_structure(const Prec<T>& a, const Prec<T>& b) {
+  if (a.lv.size() != b.lv.size() || a.tiled != b.tiled || a.fused != b.fused || a.Lc != b.Lc ||
+      a.low != b.low || a.cheb_coarse != b.cheb_coarse || a.plane3 != b.plane3 || a.pshape != b.pshape ||
+      (a.gemv_inv == nullptr) != (b.gemv_inv == nullptr) || a.gemv_ldA != b.gemv_ldA || a.k_R != b.k_R ||
+      a.n_V != b.n_V || a.q_A != b.q_A || a.nu_pre != b.nu_pre || a.nu_post != b.nu_post || a.csmem != b.csmem)
+    return false;
+  if (a.tiled)
+    for (size_t l = 0; l + 1 < a.lv.size(); ++l)
+      if (a.ts[l].tile != b.ts[l].tile) return false;
+  return true;
+}
+
+// may handles a and b share launches?
+bool cohort_compatible(const ok_grid* a, const ok_grid* b) {
+  const ok_opts &x = a->o, &y = b->o;
+  if (a->dim != b->dim || a->n != b->n || a->device != b->device || x.precision != y.precision ||
+      x.restart != y.restart || x.reorth != 1 || y.reorth != 1 || x.use_pdl != y.use_pdl ||
+      x.max_gmres != y.max_gmres || x.fuse_coarse == 2 || y.fuse_coarse == 2)
+    return false;
+  return x.precision == OK_FP64 ? same_structure(a->pd, b->pd) : same_structure(a->pf, b->pf);
+}
+
+template <typename T>
+struct CohortPrec {
+  std::vector<Prec<T>*> P;
+  int dim = 0;
+  int B() const { return (int)P.size(); }
+  Prec<T>& p0() { return *P[0]; }
+
+  // ---- 2D register-strip path (Prec::apply_tiled) -------------------------
+  template <typename TO>
+  void vcycle_t(int l, bool x_zero, T* const* rhs, TO* const* out, T* const* mx, cudaStream_t s) {
+    Prec<T>& P0 = p0();
+    const int nb = B();
+    if (P0.fused && l == P0.Lc) {
+      CoarseVItem<T> it[BATCH_MAX];
+      for (int i = 0; i < nb; ++i) it[i] = {P[i]->ca_dev, rhs[i], x_zero ? (const T*)nullptr : P[i]->X(l), P[i]->X(l)};
+      launch_coarse_vcycle_b<T>(dim, it, nb, P0.csmem, s);
+      return;
+    }
+    if (l + 1 == (int)P0.lv.size()) {
+      if (P0.cheb_coarse) {
+        for (int i = 0; i < nb; ++i) P[i]->coarse_solve(rhs[i], P[i]->X(l), s);
+      } else {
+        GemvItem<T> it[BATCH_MAX];
+        for (int i = 0; i < nb; ++i)
+          it[i] = {P0.gemv_inv ? P[i]->gemv_inv : P[i]->coarse_inv, rhs[i], P[i]->X(l)};
+        launch_coarse_solve_b<T>(P0.nc, P0.gemv_ldA, P0.gemv_inv != nullptr, it, nb, s);
+      }
+      return;
+    }
+    StripPreItem<T> pre[BATCH_MAX];
+    T* nb_rhs[BATCH_MAX];
+    for (int i = 0; i < nb; ++i) {
+      Prec<T>& Q = *P[i];
+      pre[i] = {Q.ts[l], x_zero ? (const T*)nullptr : Q.X(l), rhs[i], Q.Xalt(l), Q.lv[l + 1].b};
+      nb_rhs[i] = Q.lv[l + 1].b;
+    }
+    launch_tile_pre_b<T>(pre, nb, s);
+    for (int i = 0; i < nb; ++i) P[i]->cur[l] ^= 1;
+    T* none[BATCH_MAX] = {};
+    vcycle_t<T>(l + 1, true, nb_rhs, none, none, s);
+    StripPostItem<T, TO> post[BATCH_MAX];
+    for (int i = 0; i < nb; ++i) {
+      Prec<T>& Q = *P[i];
+      post[i] = {Q.ts[l], Q.X(l), Q.X(l + 1), rhs[i], Q.Xalt(l), mx[i], out[i], (T)1};
+    }
+    launch_tile_post_b<T, TO>(post, nb, s);
+    for (int i = 0; i < nb; ++i) P[i]->cur[l] ^= 1;
+  }
+  template <typename TO>
+  void mg_solve_t(T* const* rhs, TO* const* out, T* const* mx, cudaStream_t s) {
+    for (auto* Q : P) std::fill(Q->cur.begin(), Q->cur.end(), 0);
+    TO* no_out[BATCH_MAX] = {};
+    T* no_mx[BATCH_MAX] = {};
+    for (int c = 0; c < p0().n_V; ++c) {
+      const bool last = c + 1 == p0().n_V;
+      vcycle_t<TO>(0, c == 0, rhs, last ? out : no_out, last ? mx : no_mx, s);
+    }
+  }
+
+  // ---- per-level steps (3D, or untiled): Prec::cheb with shared launches ---
+  template <typename TB, typename TO>
+  void cheb(int l, bool mass, const TB* const* b, bool x_zero, int steps, TO* const* out, T oscale, bool want_r,
+            cudaStream_t s) {
+    Prec<T>& P0 = p0();
+    const int nb = B();
+    const Geom& g = P0.lv[l].g;
+    const double th = mass ? P0.thM : P0.thS;
+    const std::vector<double>& c1 = mass ? P0.cM1 : P0.cS1;
+    const std::vector<double>& c2 = mass ? P0.cM2 : P0.cS2;
+    auto W = [&](int i) { return mass ? P[i]->WM : P[i]->lv[l].WS; };
+    auto dinv = [&](int i) { return mass ? P[i]->dinvM : P[i]->lv[l].dinvS; };
+    auto X = [&](int i) { return mass ? P[i]->cx : P[i]->lv[l].x; };
+    auto R = [&](int i) { return mass ? P[i]->cr : P[i]->lv[l].r; };
+    auto D0 = [&](int i) { return mass ? P[i]->cd0 : P[i]->lv[l].d0; };
+    auto D1 = [&](int i) { return mass ? P[i]->cd1 : P[i]->lv[l].d1; };
+    const int shape = P0.plane_shape(g);
+    if (x_zero) {
+      ChebInitItem<T, TB> it[BATCH_MAX];
+      for (int i = 0; i < nb; ++i) it[i] = {dinv(i), b[i], (T)1, R(i), D0(i), (T)(1.0 / th)};
+      launch_cheb_init_b<T, TB>(dim, g, it, nb, s);
+    } else if (P0.plane3) {
+      PlaneArgs<T, T, T> it[BATCH_MAX];
+      for (int i = 0; i < nb; ++i) {
+        it[i] = {};
+        it[i].g = g, it[i].W = W(i), it[i].dinv = dinv(i), it[i].s = X(i), it[i].r = R(i), it[i].d = D0(i);
+        it[i].b = (const T*)b[i], it[i].inv_th = (T)(1.0 / th);
+      }
+      launch_plane3_b<T, T, T>(PM_RESID, it, nb, shape, s);
+    } else {
+      for (int i = 0; i < nb; ++i)
+        launch_resid_init<T>(dim, g, W(i), dinv(i), (const T*)b[i], X(i), R(i), D0(i), (T)(1.0 / th), s);
+    }
+    int cur = 0;
+    for (int k = 0; k + 1 < steps; ++k) {
+      const bool first = x_zero && k == 0;
+      if (P0.plane3) {
+        PlaneArgs<T, T, T> it[BATCH_MAX];
+        for (int i = 0; i < nb; ++i) {
+          T* d[2] = {D0(i), D1(i)};
+          it[i] = {};
+          it[i].g = g, it[i].W = W(i), it[i].dinv = dinv(i), it[i].s = d[cur], it[i].x = X(i), it[i].r = R(i);
+          it[i].d = d[1 - cur], it[i].c1 = (T)c1[k], it[i].c2 = (T)c2[k], it[i].first = first ? 1 : 0;
+        }
+        launch_plane3_b<T, T, T>(PM_STEP, it, nb, shape, s);
+      } else {
+        for (int i = 0; i < nb; ++i) {
+          T* d[2] = {D0(i), D1(i)};
+          launch_cheb_step<T>(dim, g, W(i), dinv(i), X(i), R(i), d[cur], d[1 - cur], (T)c1[k], (T)c2[k], first, s);
+        }
+      }
+      cur ^= 1;
+    }
+    const bool first = x_zero && steps == 1;
+    if (P0.plane3 && want_r) {
+      PlaneArgs<T, T, T> it[BATCH_MAX];
+      for (int i = 0; i < nb; ++i) {
+        T* d[2] = {D0(i), D1(i)};
+        it[i] = {};
+        it[i].g = g, it[i].W = W(i), it[i].s = d[cur], it[i].x = X(i), it[i].r = R(i), it[i].first = first ? 1 : 0;
+        it[i].out = (T*)out[i], it[i].oscale = oscale;
+      }
+      launch_plane3_b<T, T, T>(PM_LAST, it, nb, shape, s);
+    } else {
+      ChebLastItem<T, TO> it[BATCH_MAX];
+      for (int i = 0; i < nb; ++i) {
+        T* d[2] = {D0(i), D1(i)};
+        it[i] = {W(i), X(i), want_r ? R(i) : (T*)nullptr, d[cur], first ? 1 : 0, out[i], oscale};
+      }
+      launch_cheb_last_b<T, TO>(dim, g, it, nb, s);
+    }
+  }
+
+  template <typename TO>
+  void vcycle(int l, bool x_zero, TO* const* out, cudaStream_t s) {
+    Prec<T>& P0 = p0();
+    const int nb = B();
+    const bool coarsest = l + 1 == (int)P0.lv.size();
+    if ((P0.fused && l == P0.Lc) || coarsest) {
+      if (P0.fused && l == P0.Lc) {
+        CoarseVItem<T> it[BATCH_MAX];
+        for (int i = 0; i < nb; ++i) {
+          Level<T>& L = P[i]->lv[l];
+          it[i] = {P[i]->ca_dev, L.b, x_zero ? (const T*)nullptr : L.x, L.x};
+        }
+        launch_coarse_vcycle_b<T>(dim, it, nb, P0.csmem, s);
+      } else if (P0.cheb_coarse) {
+        for (int i = 0; i < nb; ++i) P[i]->coarse_solve(P[i]->lv[l].b, P[i]->lv[l].x, s);
+      } else {
+        GemvItem<T> it[BATCH_MAX];
+        for (int i = 0; i < nb; ++i)
+          it[i] = {P0.gemv_inv ? P[i]->gemv_inv : P[i]->coarse_inv, P[i]->lv[l].b, P[i]->lv[l].x};
+        launch_coarse_solve_b<T>(P0.nc, P0.gemv_ldA, P0.gemv_inv != nullptr, it, nb, s);
+      }
+      for (int i = 0; i < nb; ++i)
+        if (out[i]) launch_axpby<T, TO>(P[i]->lv[l].g.nv, 1.0, P[i]->lv[l].x, 0.0, out[i], s);
+      return;
+    }
+    T* none[BATCH_MAX] = {};
+    T* bl[BATCH_MAX];
+    for (int i = 0; i < nb; ++i) bl[i] = P[i]->lv[l].b;
+    cheb<T, T>(l, false, bl, x_zero, P0.nu_pre, none, (T)1, true, s);
+    const Geom& gf = P0.lv[l].g;
+    const Geom& gc = P0.lv[l + 1].g;
+    TransferItem<T> tr[BATCH_MAX];
+    for (int i = 0; i < nb; ++i) tr[i] = {P[i]->lv[l].r, P[i]->lv[l + 1].b};
+    launch_restrict_b<T>(dim, gf, gc, tr, nb, s);
+    vcycle<T>(l + 1, true, none, s);
+    for (int i = 0; i < nb; ++i) tr[i] = {P[i]->lv[l].x, P[i]->lv[l + 1].x};
+    launch_prolong_add_b<T>(dim, gf, gc, tr, nb, s);
+    cheb<T, TO>(l, false, bl, false, P0.nu_post, out, (T)1, false, s);
+  }
+  template <typename TO>
+  void mg_solve(TO* const* out, cudaStream_t s) {
+    TO* none[BATCH_MAX] = {};
+    for (int c = 0; c < p0().n_V; ++c) vcycle<TO>(0, c == 0, c + 1 == p0().n_V ? out : none, s);
+  }
+
+  // z_i = P_i^{-1} v_i for every member
+  template <typename TZ>
+  void apply(const double* const* v, TZ* const* z, cudaStream_t s) {
+    Prec<T>& P0 = p0();
+    const int nb = B();
+    const long long nv = P0.lv[0].g.nv;
+    if (P0.tiled) {
+      AmassItem<T, TZ> am[BATCH_MAX];
+      T *b0[BATCH_MAX], *b2[BATCH_MAX];
+      TZ* z2[BATCH_MAX];
+      T* none[BATCH_MAX] = {};
+      TZ* nonez[BATCH_MAX] = {};
+      for (int i = 0; i < nb; ++i) {
+        am[i] = {P[i]->tm, v[i], z[i], P[i]->lv[0].b};
+        b0[i] = P[i]->lv[0].b;
+        b2[i] = P[i]->b2;
+        z2[i] = z[i] + nv;
+      }
+      launch_tile_amass_b<T, TZ>(am, nb, s);
+      mg_solve_t<T>(b0, none, b2, s);                                 // b2 = M S_hat^{-1} t
+      (void)nonez;
+      mg_solve_t<TZ>(b2, z2, none, s);                                // z2 = S_hat^{-1} b2
+      return;
+    }
+    if (P0.k_R != 1) {                                                // two Richardson steps: per problem
+      for (int i = 0; i < nb; ++i) P[i]->template apply<TZ>(v[i], z[i], s);
+      return;
+    }
+    const Geom& g = P0.lv[0].g;
+    cheb<double, TZ>(0, true, v, true, P0.q_A, z, (T)P0.inv_a11, false, s);         // z1 = A~^{-1} r1
+    CStepItem<T, double> cs[BATCH_MAX];
+    for (int i = 0; i < nb; ++i) cs[i] = {P[i]->coef, v[i] + nv, (T)1, P[i]->cx, (T)P[i]->inv_a11, P[i]->lv[0].b};
+    launch_cstep_b<T, double>(dim, g, cs, nb, s);                     // t = r2 - C z1
+    T* none[BATCH_MAX] = {};
+    mg_solve<T>(none, s);                                             // S_hat^{-1} t
+    if (P0.plane3) {                                                  // M .
+      PlaneArgs<T, T, T> it[BATCH_MAX];
+      for (int i = 0; i < nb; ++i) {
+        it[i] = {};
+        it[i].g = g, it[i].W = P[i]->WM, it[i].s = P[i]->lv[0].x, it[i].out = P[i]->lv[0].b, it[i].alpha = (T)1;
+      }
+      launch_plane3_b<T, T, T>(PM_OP, it, nb, P0.plane_shape(g), s);
+    } else {
+      for (int i = 0; i < nb; ++i) P[i]->op(g, P[i]->WM, false, P[i]->lv[0].x, P[i]->lv[0].b, (T)1, s);
+    }
+    TZ* z2[BATCH_MAX];
+    for (int i = 0; i < nb; ++i) z2[i] = z[i] + nv;
+    mg_solve<TZ>(z2, s);                                              // S_hat^{-1} .
+  }
+};
+
+// Arnoldi step j of every member: z_j = P^{-1} v_j, w = J z_j, CGS2 of w
+template <typename TZ>
+void arnoldi_b(const std::vector<ok_grid*>& Gs, const std::vector<TZ*>& Zs, int j, cudaStream_t s) {
+  const int nb = (int)Gs.size();
+  ok_grid* G0 = Gs[0];
+  const long long N = 2 * G0->g0.nv;
+  const double* v[BATCH_MAX];
+  TZ* z[BATCH_MAX];
+  for (int i = 0; i < nb; ++i) {
+    v[i] = Gs[i]->V + (long long)j * N;
+    z[i] = Zs[i] + (long long)j * N;
+  }
+  if constexpr (std::is_same<TZ, double>::value) {        // float64 Z: the float64 preconditioner
+    CohortPrec<double> cp;
+    cp.dim = G0->dim;
+    for (auto* G : Gs) cp.P.push_back(&G->pd);
+    cp.apply<TZ>(v, z, s);
+  } else {                                                 // float32 / float16 Z: the float32 one
+    CohortPrec<float> cp;
+    cp.dim = G0->dim;
+    for (auto* G : Gs) cp.P.push_back(&G->pf);
+    cp.apply<TZ>(v, z, s);
+  }
+  ApplyJItem<TZ> aj[BATCH_MAX];
+  KrylovItem kr[BATCH_MAX];
+  for (int i = 0; i < nb; ++i) {
+    ok_grid* G = Gs[i];
+    double* w = G->V + (long long)(j + 1) * N;
+    aj[i] = {G->jc, G->coef, z[i], w};
+    kr[i] = {G->V, N, w, N, G->rs.partials, G->rs.counter, G->ks, 0};
+  }
+  launch_apply_j_b<TZ>(G0->dim, G0->g0, G0->refWM, G0->refWK, aj, nb, s);
+  launch_cgs2_batch(kr, nb, j + 1, j, s);
+  CKL();
+}
+
+// Lockstep restarted FGMRES for the members' systems J_i x_i = f_i (the
+// members' own f and xs buffers); per-member iteration counts and relative
+// residuals; a member that fails gets its status and leaves the cohort.
+template <typename TZ>
+void fgmres_b(const std::vector<ok_grid*>& Gs, const std::vector<TZ*>& Zs, std::vector<int>& its,
+              std::vector<double>& rel, std::vector<int>& status, cudaStream_t s) {
+  const int nb = (int)Gs.size();
+  ok_grid* G0 = Gs[0];
+  const long long N = 2 * G0->g0.nv;
+  const int m = G0->o.restart;
+  const double rtol = G0->o.gmres_rtol;
+  std::vector<double> fnorm(nb, 0.0), beta(nb, 0.0);
+  std::vector<int> active;
+  for (int i = 0; i < nb; ++i) {
+    ok_grid* G = Gs[i];
+    its[i] = 0;
+    rel[i] = 0.0;
+    launch_norm(G->f, N, G->rs, G->dsc, s);
+    CKL();
+    CK(cudaMemcpyAsync(G->hpin, G->dsc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(G->xs, 0, N * sizeof(double), s));
+  }
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < nb; ++i) {
+    ok_grid* G = Gs[i];
+    fnorm[i] = G->hpin[0];
+    if (!std::isfinite(fnorm[i])) {
+      status[i] = OK_ERR_NONFINITE;
+      continue;
+    }
+    if (fnorm[i] == 0.0) continue;
+    CK(cudaMemcpyAsync(G->rv, G->f, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(G->dsc + 1, G->dsc, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    beta[i] = fnorm[i];
+    if (beta[i] > rtol * fnorm[i]) active.push_back(i);
+  }
+  while (!active.empty()) {
+    std::vector<int> jmax(nb, 0), jused(nb, 0);
+    for (int i : active) {
+      ok_grid* G = Gs[i];
+      launch_cycle_start(G->ks, G->dsc + 1, rtol * fnorm[i], s);
+      launch_axpby<double, double>(N, 1.0, G->rv, 0.0, G->V, s);
+      launch_scale_by(G->V, N, ks_beta_ptr(G->ks) + 1, s);
+      CKL();
+      jmax[i] = std::min(m, G->o.max_gmres - its[i]);
+    }
+    std::vector<int> cyc = active;
+    for (int j = 0; !cyc.empty(); ++j) {
+      std::vector<ok_grid*> g;
+      std::vector<TZ*> z;
+      for (int i : cyc) g.push_back(Gs[i]), z.push_back(Zs[i]);
+      arnoldi_b<TZ>(g, z, j, s);
+      for (int i : cyc)
+        CK(cudaMemcpyAsync(Gs[i]->hpin, ks_eta_ptr(Gs[i]->ks), 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::vector<int> next;
+      for (int i : cyc) {
+        its[i] += 1;
+        jused[i] = j + 1;
+        const double est = Gs[i]->hpin[2], go = Gs[i]->hpin[3];
+        if (!std::isfinite(est)) {
+          status[i] = OK_ERR_NONFINITE;
+          continue;
+        }
+        if (go != 0.0 && j + 1 < jmax[i]) next.push_back(i);
+      }
+      cyc.swap(next);
+    }
+    std::vector<int> still;
+    for (int i : active) {
+      if (status[i] != OK_SUCCESS) continue;
+      ok_grid* G = Gs[i];
+      launch_lsq(G->ks, jused[i], s);
+      launch_multi_axpy<TZ>(Zs[i], N, jused[i], G->ks, G->xs, N, s);
+      JCoefs jc = G->jc;
+      jc.alpha = -1.0;
+      jc.beta = 1.0;
+      launch_apply_j<double>(G->dim, G->g0, G->refWM, G->refWK, jc, G->coef, G->xs, G->rv, G->f, s);
+      launch_norm(G->rv, N, G->rs, G->dsc + 1, s);
+      CKL();
+      CK(cudaMemcpyAsync(G->hpin + 4, G->dsc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    for (int i : active) {
+      if (status[i] != OK_SUCCESS) continue;
+      beta[i] = Gs[i]->hpin[4];
+      if (!std::isfinite(beta[i])) {
+        status[i] = OK_ERR_NONFINITE;
+        continue;
+      }
+      if (beta[i] > rtol * fnorm[i] && its[i] < Gs[i]->o.max_gmres) still.push_back(i);
+    }
+    active.swap(still);
+  }
+  for (int i = 0; i < nb; ++i)
+    if (fnorm[i] > 0.0 && std::isfinite(fnorm[i])) rel[i] = beta[i] / fnorm[i];
+}
+
+// Every member's stream is the cohort's stream while the cohort runs (the
+// per-member helpers enqueue on G->s), restored afterwards.
+struct CohortStreams {
+  std::vector<ok_grid*> Gs;
+  std::vector<cudaStream_t> saved;
+  CohortStreams(const std::vector<ok_grid*>& g, cudaStream_t s) : Gs(g) {
+    for (auto* G : Gs) saved.push_back(G->s), G->s = s;
+    g_pdl = Gs[0]->o.use_pdl != 0;
+  }
+  ~CohortStreams() {
+    for (size_t i = 0; i < Gs.size(); ++i) Gs[i]->s = saved[i];
+  }
+};
+
+// One theta-method timestep for every member (state in/out through u[i],
+// w[i]), Newton in lockstep: the members that still need a Newton step share
+// the linear solve's launches.
+void timestep_b(const std::vector<ok_grid*>& Gs, double* const* u, double* const* w, std::vector<ok_step_info>& info,
+                std::vector<int>& status, cudaStream_t s) {
+  const int nb = (int)Gs.size();
+  const long long nv = Gs[0]->g0.nv;
+  std::vector<double> fn(nb, 0.0), r0(nb, 0.0);
+  std::vector<int> extra(nb, 0), done(nb, 0), ok(nb, 0);
+  for (int i = 0; i < nb; ++i) {
+    ok_grid* G = Gs[i];
+    std::memset(&info[i], 0, sizeof(ok_step_info));
+    CK(cudaMemcpyAsync(G->un, u[i], nv * sizeof(double), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(G->wn, w[i], nv * sizeof(double), cudaMemcpyDefault, s));
+    CK(cudaMemsetAsync(G->dflag, 0, sizeof(int), s));
+    launch_check_finite(G->un, nv, G->dflag, s);
+    launch_check_finite(G->wn, nv, G->dflag, s);
+    CK(cudaMemcpyAsync(G->uk, G->un, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(G->wk, G->wn, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CKL();
+  }
+  for (int i = 0; i < nb; ++i) {
+    ok_grid* G = Gs[i];
+    int flag = 0;
+    CK(cudaMemcpyAsync(G->hpin, G->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::memcpy(&flag, G->hpin, sizeof(int));
+    if (flag) {
+      status[i] = OK_ERR_NONFINITE;
+      done[i] = 1;
+      continue;
+    }
+    fn[i] = r0[i] = residual(G, G->un, G->wn, G->uk, G->wk, G->f);
+    info[i].newton_resid0 = r0[i];
+  }
+  std::vector<int> linear_failed(nb, 0);
+  auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    std::vector<int> need;
+    for (int i = 0; i < nb; ++i) {
+      if (done[i]) continue;
+      ok_grid* G = Gs[i];
+      if (!std::isfinite(fn[i])) {
+        status[i] = OK_ERR_NONFINITE;
+        done[i] = 1;
+        continue;
+      }
+      if (fn[i] <= std::max(G->o.newton_atol, G->o.newton_rtol * r0[i])) {
+        ok[i] = 1;
+        if (extra[i] >= G->o.newton_extra) {
+          done[i] = 1;
+          continue;
+        }
+        ++extra[i];
+      }
+      if (info[i].newton_its >= G->o.max_newton) {
+        done[i] = 1;
+        continue;
+      }
+      need.push_back(i);
+    }
+    if (need.empty()) break;
+    std::vector<ok_grid*> g;
+    for (int i : need) {
+      assemble_c(Gs[i], Gs[i]->uk);
+      g.push_back(Gs[i]);
+    }
+    std::vector<int> its(need.size(), 0), st(need.size(), OK_SUCCESS);
+    std::vector<double> rel(need.size(), 0.0);
+    const int prec = Gs[0]->o.precision;
+    if (prec == OK_MIXED) {
+      std::vector<float*> z;
+      for (auto* G : g) z.push_back(G->Zf);
+      fgmres_b<float>(g, z, its, rel, st, s);
+    } else if (prec == OK_MIXED_HALF) {
+      std::vector<__half*> z;
+      for (auto* G : g) z.push_back(G->Zh);
+      fgmres_b<__half>(g, z, its, rel, st, s);
+    } else {
+      std::vector<double*> z;
+      for (auto* G : g) z.push_back(G->Zd);
+      fgmres_b<double>(g, z, its, rel, st, s);
+    }
+    for (size_t k = 0; k < need.size(); ++k) {
+      const int i = need[k];
+      ok_grid* G = Gs[i];
+      info[i].gmres_its += its[k];
+      info[i].last_gmres_its = its[k];
+      info[i].rel_resid = rel[k];
+      if (st[k] != OK_SUCCESS) {
+        status[i] = st[k];
+        done[i] = linear_failed[i] = 1;
+        continue;
+      }
+      launch_axpby<double, double>(nv, 1.0, G->xs, 1.0, G->uk, s);
+      launch_axpby<double, double>(nv, 1.0, G->xs + nv, 1.0, G->wk, s);
+      CKL();
+      info[i].newton_its += 1;
+      if (rel[k] > G->o.gmres_rtol) {
+        status[i] = OK_ERR_NOT_CONVERGED;
+        done[i] = linear_failed[i] = 1;
+        continue;
+      }
+      fn[i] = residual(G, G->un, G->wn, G->uk, G->wk, G->f);
+    }
+  }
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < nb; ++i) {
+    ok_grid* G = Gs[i];
+    info[i].newton_resid = fn[i];
+    info[i].converged = ok[i];
+    info[i].solve_ms = ms;
+    if (status[i] == OK_SUCCESS && !ok[i]) status[i] = OK_ERR_NOT_CONVERGED;
+    // as ok_timestep: the state is written back after a completed Newton loop
+    // (also when it hit its step cap), not after a failed linear solve or a
+    // non-finite value
+    if (status[i] == OK_SUCCESS || (status[i] == OK_ERR_NOT_CONVERGED && !linear_failed[i])) {
+      copy_out(G, u[i], G->uk, nv);
+      copy_out(G, w[i], G->wk, nv);
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1797,34 +2335,112 @@ int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream st
     return OK_ERR_INVALID_ARG;
   }
   auto t0 = std::chrono::steady_clock::now();
-  int done = 0, failed = 0;
+  auto now = [&] { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+  std::vector<int> valid;
   for (int i = 0; i < count; ++i) {
     ok_request& r = reqs[i];
     r.status = OK_SUCCESS;
     r.newton_its = r.gmres_its = 0;
-    if (!r.grid || !r.u || !r.w || r.steps < 0) {
-      r.status = OK_ERR_INVALID_ARG;
-      ++failed;
-      continue;
-    }
-    for (int k = 0; k < r.steps; ++k) {
-      ok_step_info info = {};
-      int st = ok_timestep(r.grid, r.u, r.w, &info, stream);
-      r.newton_its += info.newton_its;
-      r.gmres_its += info.gmres_its;
-      if (st != OK_SUCCESS) {
-        r.status = st;
-        break;
+    r.seconds = 0.0;
+    if (!r.grid || !r.u || !r.w || r.steps < 0) r.status = OK_ERR_INVALID_ARG;
+    else valid.push_back(i);
+  }
+  // cohorts: requests on distinct handles of the same grid, options and
+  // multigrid structure, at most BATCH_MAX together, in request order
+  std::vector<std::vector<int>> cohorts;
+  std::vector<int> taken(count, 0);
+  for (size_t a = 0; a < valid.size(); ++a) {
+    const int i = valid[a];
+    if (taken[i]) continue;
+    std::vector<int> c{i};
+    taken[i] = 1;
+    for (size_t b = a + 1; b < valid.size() && (int)c.size() < BATCH_MAX; ++b) {
+      const int k = valid[b];
+      if (taken[k]) continue;
+      bool distinct = true;
+      for (int m : c) distinct = distinct && reqs[m].grid != reqs[k].grid;
+      if (distinct && cohort_compatible(reqs[i].grid, reqs[k].grid)) {
+        c.push_back(k);
+        taken[k] = 1;
       }
     }
-    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (r.status == OK_SUCCESS) ++done;
-    else ++failed;
+    cohorts.push_back(c);
   }
+  for (const auto& c : cohorts) {
+    if (c.size() == 1) {                                  // alone: the timestep path itself
+      ok_request& r = reqs[c[0]];
+      for (int k = 0; k < r.steps; ++k) {
+        ok_step_info info = {};
+        const int st = ok_timestep(r.grid, r.u, r.w, &info, stream);
+        r.newton_its += info.newton_its;
+        r.gmres_its += info.gmres_its;
+        if (st != OK_SUCCESS) {
+          r.status = st;
+          break;
+        }
+      }
+      r.seconds = now();
+      continue;
+    }
+    std::vector<ok_grid*> Gs;
+    for (int i : c) Gs.push_back(reqs[i].grid);
+    std::string msg;
+    const int st = guarded([&] {
+      ok_grid* G0 = Gs[0];
+      cudaStream_t cs = G0->s;
+      // the cohort's stream follows the caller's stream and every member's
+      // earlier work; the caller's stream follows the cohort at the end
+      CK(cudaEventRecord(G0->ev_in, (cudaStream_t)stream));
+      CK(cudaStreamWaitEvent(cs, G0->ev_in, 0));
+      for (auto* G : Gs)
+        if (G != G0) {
+          CK(cudaEventRecord(G->ev_in, G->s));
+          CK(cudaStreamWaitEvent(cs, G->ev_in, 0));
+        }
+      {
+        CohortStreams swap(Gs, cs);
+        int steps = 0;
+        for (int i : c) steps = std::max(steps, reqs[i].steps);
+        for (int t = 0; t < steps; ++t) {
+          std::vector<ok_grid*> g;
+          std::vector<double*> u, w;
+          std::vector<int> idx;
+          for (int i : c)
+            if (reqs[i].status == OK_SUCCESS && t < reqs[i].steps) {
+              g.push_back(reqs[i].grid);
+              u.push_back(reqs[i].u);
+              w.push_back(reqs[i].w);
+              idx.push_back(i);
+            }
+          if (g.empty()) break;
+          std::vector<ok_step_info> info(g.size());
+          std::vector<int> status(g.size(), OK_SUCCESS);
+          timestep_b(g, u.data(), w.data(), info, status, cs);
+          for (size_t k = 0; k < idx.size(); ++k) {
+            ok_request& r = reqs[idx[k]];
+            r.newton_its += info[k].newton_its;
+            r.gmres_its += info[k].gmres_its;
+            if (status[k] != OK_SUCCESS) r.status = status[k];
+            if (status[k] != OK_SUCCESS || t + 1 == r.steps) r.seconds = now();
+          }
+        }
+      }
+      CK(cudaEventRecord(G0->ev_out, cs));
+      CK(cudaStreamWaitEvent((cudaStream_t)stream, G0->ev_out, 0));
+      for (auto* G : Gs)
+        if (G != G0) CK(cudaStreamWaitEvent(G->s, G0->ev_out, 0));
+    });
+    if (st != OK_SUCCESS) {                               // a CUDA or host failure of the cohort itself
+      for (int i : c)
+        if (reqs[i].status == OK_SUCCESS) reqs[i].status = st, reqs[i].seconds = now();
+    }
+  }
+  int done = 0, failed = 0;
+  for (int i = 0; i < count; ++i) (reqs[i].status == OK_SUCCESS ? done : failed) += 1;
   if (out) {
     out->completed = done;
     out->failed = failed;
-    out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    out->seconds = now();
   }
   if (failed == 0) return OK_SUCCESS;
   for (int i = 0; i < count; ++i)

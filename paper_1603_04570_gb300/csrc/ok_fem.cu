@@ -472,17 +472,16 @@ __device__ __forceinline__ void load_nb_d(const TX* __restrict__ x, const Geom& 
 // y = alpha J z + beta y0, J = [a11 M, dth K; C, M]  (eqn newton)
 // ---------------------------------------------------------------------------
 template <int D, typename TZ>
-__global__ void __launch_bounds__(128) k_apply_j(Geom g, const double* __restrict__ WM,
-                                                 const double* __restrict__ WK, JCoefs jc,
-                                                 const double* __restrict__ coef, const TZ* __restrict__ z,
-                                                 double* __restrict__ y, const double* __restrict__ y0) {
-  pdl_launch_dependents();
+__device__ __forceinline__ void apply_j_body(const Geom& g, int kz, const double* __restrict__ WM,
+                                             const double* __restrict__ WK, const JCoefs& jc,
+                                             const double* __restrict__ coef, const TZ* __restrict__ z,
+                                             double* __restrict__ y, const double* __restrict__ y0) {
   using Tp = Topo<D>;
   __shared__ double sWM[Tp::NCLASS * Tp::NOFF], sWK[Tp::NCLASS * Tp::NOFF];
   stage_tables<D>(sWM, sWK, WM, WK);
   pdl_wait();
   Vtx<D> v;
-  if (!vertex_of_thread<D>(g, v)) return;
+  if (!vertex_of_thread_at<D>(g, kz, v)) return;
   double z1[Tp::NOFF], z2[Tp::NOFF];
   load_nb_d<D, TZ>(z, g, v, z1);
   load_nb_d<D, TZ>(z + g.nv, g, v, z2);
@@ -494,6 +493,21 @@ __global__ void __launch_bounds__(128) k_apply_j(Geom g, const double* __restric
   }
   y[v.idx] = y1;
   y[v.idx + g.nv] = y2;
+}
+template <int D, typename TZ>
+__global__ void __launch_bounds__(128) k_apply_j(Geom g, const double* __restrict__ WM,
+                                                 const double* __restrict__ WK, JCoefs jc,
+                                                 const double* __restrict__ coef, const TZ* __restrict__ z,
+                                                 double* __restrict__ y, const double* __restrict__ y0) {
+  pdl_launch_dependents();
+  apply_j_body<D, TZ>(g, D == 3 ? (int)blockIdx.z : 0, WM, WK, jc, coef, z, y, y0);
+}
+template <int D, typename TZ>
+__global__ void __launch_bounds__(128) k_apply_j_b(Batch<ApplyJItem<TZ>> B, Geom g, const double* __restrict__ WM,
+                                                   const double* __restrict__ WK) {
+  pdl_launch_dependents();
+  const ApplyJItem<TZ>& a = B.a[batch_problem<D>(g)];
+  apply_j_body<D, TZ>(g, batch_plane<D>(g), WM, WK, a.jc, a.coef, a.z, a.y, (const double*)nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -507,6 +521,15 @@ __global__ void __launch_bounds__(128) k_cstep(Geom g, const T* __restrict__ coe
   if (!vertex_of_thread<D>(g, v)) return;
   T cy = capply_at<D, T>(g, v, coef, y1, yscale);
   t[v.idx] = (T)v2[v.idx] * vscale - cy;
+}
+template <int D, typename T, typename TV>
+__global__ void __launch_bounds__(128) k_cstep_b(Batch<CStepItem<T, TV>> B, Geom g) {
+  pdl_entry();
+  const CStepItem<T, TV>& a = B.a[batch_problem<D>(g)];
+  Vtx<D> v;
+  if (!vertex_of_thread_at<D>(g, batch_plane<D>(g), v)) return;
+  T cy = capply_at<D, T>(g, v, a.coef, a.y1, a.yscale);
+  a.t[v.idx] = (T)a.v2[v.idx] * a.vscale - cy;
 }
 
 // Richardson residual for k_R = 2:  out = t - (M y - C a)   (S y = M y - C A~^{-1} B y)
@@ -568,6 +591,33 @@ void launch_apply_j(int dim, const Geom& g, const double* WM, const double* WK, 
   if (dim == 2) launch_k(k_apply_j<2, TZ>, grd, 128, 0, s, g, WM, WK, jc, coef, z, y, y0);
   else launch_k(k_apply_j<3, TZ>, grd, 128, 0, s, g, WM, WK, jc, coef, z, y, y0);
 }
+template <typename TZ>
+void launch_apply_j_b(int dim, const Geom& g, const double* WM, const double* WK, const ApplyJItem<TZ>* items,
+                      int count, cudaStream_t s) {
+  Batch<ApplyJItem<TZ>> B;
+  for (int i = 0; i < count; ++i) B.a[i] = items[i];
+  dim3 grd = grid_of(dim, g, 128);
+  grd.z *= count;
+  if (dim == 2) launch_k(k_apply_j_b<2, TZ>, grd, 128, 0, s, B, g, WM, WK);
+  else launch_k(k_apply_j_b<3, TZ>, grd, 128, 0, s, B, g, WM, WK);
+}
+template void launch_apply_j_b<double>(int, const Geom&, const double*, const double*, const ApplyJItem<double>*,
+                                       int, cudaStream_t);
+template void launch_apply_j_b<float>(int, const Geom&, const double*, const double*, const ApplyJItem<float>*,
+                                      int, cudaStream_t);
+template void launch_apply_j_b<__half>(int, const Geom&, const double*, const double*, const ApplyJItem<__half>*,
+                                       int, cudaStream_t);
+template <typename T, typename TV>
+void launch_cstep_b(int dim, const Geom& g, const CStepItem<T, TV>* items, int count, cudaStream_t s) {
+  Batch<CStepItem<T, TV>> B;
+  for (int i = 0; i < count; ++i) B.a[i] = items[i];
+  dim3 grd = grid_of(dim, g, 128);
+  grd.z *= count;
+  if (dim == 2) launch_k(k_cstep_b<2, T, TV>, grd, 128, 0, s, B, g);
+  else launch_k(k_cstep_b<3, T, TV>, grd, 128, 0, s, B, g);
+}
+template void launch_cstep_b<double, double>(int, const Geom&, const CStepItem<double, double>*, int, cudaStream_t);
+template void launch_cstep_b<float, double>(int, const Geom&, const CStepItem<float, double>*, int, cudaStream_t);
 template void launch_apply_j<double>(int, const Geom&, const double*, const double*, const JCoefs&,
                                      const double*, const double*, double*, const double*, cudaStream_t);
 template void launch_apply_j<float>(int, const Geom&, const double*, const double*, const JCoefs&,

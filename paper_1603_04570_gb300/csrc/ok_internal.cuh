@@ -169,12 +169,13 @@ template <int D> struct Vtx {
 };
 
 // thread -> vertex for the launch shape grid(ceil(n1/bx), n1, D==3 ? n1 : 1)
+// (kz: the z-plane; batched launches fold the problem index into blockIdx.z)
 template <int D>
-__device__ __forceinline__ bool vertex_of_thread(const Geom& g, Vtx<D>& v) {
+__device__ __forceinline__ bool vertex_of_thread_at(const Geom& g, int kz, Vtx<D>& v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n1) return false;
   int j = blockIdx.y;
-  int k = D == 3 ? blockIdx.z : 0;
+  int k = D == 3 ? kz : 0;
   v.p[0] = i;
   v.p[1] = j;
   v.p[2] = k;
@@ -184,6 +185,19 @@ __device__ __forceinline__ bool vertex_of_thread(const Geom& g, Vtx<D>& v) {
   v.c[2] = D == 3 ? axis_class(k, g.n) : 1;
   v.cls = v.c[0] + 3 * v.c[1] + (D == 3 ? 9 * v.c[2] : 0);
   return true;
+}
+template <int D>
+__device__ __forceinline__ bool vertex_of_thread(const Geom& g, Vtx<D>& v) {
+  return vertex_of_thread_at<D>(g, D == 3 ? (int)blockIdx.z : 0, v);
+}
+// batched grid (x, n1, (D == 3 ? n1 : 1) * count): problem index and z-plane
+template <int D>
+__device__ __forceinline__ int batch_problem(const Geom& g) {
+  return D == 3 ? (int)blockIdx.z / g.n1 : (int)blockIdx.z;
+}
+template <int D>
+__device__ __forceinline__ int batch_plane(const Geom& g) {
+  return D == 3 ? (int)blockIdx.z % g.n1 : 0;
 }
 
 // Is the neighbour at offset O inside the domain?
@@ -274,6 +288,14 @@ template <typename T> struct OpTables {
 // Host: reference (h = 1) tables of M and K for every class, double.
 // WM[cls*NOFF+o] * h^d and WK[cls*NOFF+o] * h^(d-2) are the assembled weights.
 void reference_tables(int dim, double* WM, double* WK);
+
+// Batched launches (ok_solve_batch's cohorts): the arguments of up to
+// BATCH_MAX independent problems travel by value in the kernel parameters;
+// blockIdx.y (or a folded blockIdx.z) selects the problem.
+constexpr int BATCH_MAX = 8;
+template <typename A> struct Batch {
+  A a[BATCH_MAX];
+};
 
 // reduction scratch layout helpers
 constexpr int RED_MAX_BLOCKS = 1024;

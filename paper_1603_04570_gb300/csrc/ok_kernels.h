@@ -46,6 +46,27 @@ void launch_apply_j(int dim, const Geom& g, const double* WM, const double* WK, 
 template <typename T, typename TV>
 void launch_cstep(int dim, const Geom& g, const T* coef, const TV* v2, T vscale, const T* y1, T yscale, T* t,
                   cudaStream_t s);
+// batched forms (same grid size, `count` <= BATCH_MAX problems; the reference
+// tables WM, WK are the same for every problem of a grid size)
+template <typename TZ> struct ApplyJItem {
+  JCoefs jc;
+  const double* coef;
+  const TZ* z;
+  double* y;
+};
+template <typename TZ>
+void launch_apply_j_b(int dim, const Geom& g, const double* WM, const double* WK, const ApplyJItem<TZ>* items,
+                      int count, cudaStream_t s);
+template <typename T, typename TV> struct CStepItem {
+  const T* coef;
+  const TV* v2;
+  T vscale;
+  const T* y1;
+  T yscale;
+  T* t;
+};
+template <typename T, typename TV>
+void launch_cstep_b(int dim, const Geom& g, const CStepItem<T, TV>* items, int count, cudaStream_t s);
 template <typename T>
 void launch_schur_resid(int dim, const Geom& g, const T* WM, T hd, const T* coef, const T* t, const T* y,
                         const T* a, T ascale, T* out, cudaStream_t s);
@@ -96,6 +117,25 @@ void launch_op_apply(int dim, const Geom& g, const T* W, bool axis_only, const T
 // `shape` selects the block shape (0..PLANE_SHAPES-1: 32x8 columns x 16
 // planes, 32x4 x 32, 64x4 x 16, 32x8 x 32).
 constexpr int PLANE_SHAPES = 4;
+enum PlaneMode { PM_RESID = 0, PM_STEP = 1, PM_LAST = 2, PM_OP = 3 };
+template <typename T, typename TS, typename TO> struct PlaneArgs {
+  Geom g;
+  const T* W;          // class table of the operator (level-scaled)
+  const T* dinv;       // 1 / diagonal per class (RESID, STEP)
+  const TS* s;         // the vector the stencil reads: x (RESID, OP) or d (STEP, LAST)
+  T* x;                // STEP, LAST: iterate (in-out)
+  T* r;                // RESID: out; STEP, LAST: in-out
+  T* d;                // RESID: d out; STEP: d_out
+  const T* b;          // RESID: right-hand side
+  TO* out;             // LAST: optional cast of x; OP: y
+  const TO* y0;        // OP: optional y0
+  T c1, c2, inv_th, oscale, alpha, beta;
+  int first;           // STEP, LAST: x starts from zero
+  int axis_only;       // OP: first 2d + 1 offsets (K-like tables)
+};
+// batched form: one launch of `mode` for `count` <= BATCH_MAX problems on grids of one size
+template <typename T, typename TS, typename TO>
+void launch_plane3_b(int mode, const PlaneArgs<T, TS, TO>* items, int count, int shape, cudaStream_t s);
 template <typename T>
 void launch_resid_init3(const Geom& g, const T* W, const T* dinv, const T* b, const T* x, T* r, T* d, T inv_th,
                         cudaStream_t s, int shape);
@@ -170,6 +210,34 @@ template <typename T, typename TZ>
 void launch_tile_amass(const TileMass<T>& a, const double* v, TZ* z1, T* t_out, cudaStream_t s);
 template <typename T>
 cudaError_t prepare_tiles(int q);
+// batched forms: one launch for `count` <= BATCH_MAX problems of the same grid
+// and window width (items[i] carries problem i's arguments; blockIdx.z = i)
+template <typename T> struct StripPreItem {
+  TileSmooth<T> a;
+  const T* x_in;
+  const T* b;
+  T* x_out;
+  T* bc;
+};
+template <typename T, typename TO> struct StripPostItem {
+  TileSmooth<T> a;
+  const T *x_in, *xc, *b;
+  T *x_out, *mx_out;
+  TO* out;
+  T oscale;
+};
+template <typename T, typename TZ> struct AmassItem {
+  TileMass<T> a;
+  const double* v;
+  TZ* z1;
+  T* t_out;
+};
+template <typename T>
+void launch_tile_pre_b(const StripPreItem<T>* items, int count, cudaStream_t s);
+template <typename T, typename TO>
+void launch_tile_post_b(const StripPostItem<T, TO>* items, int count, cudaStream_t s);
+template <typename T, typename TZ>
+void launch_tile_amass_b(const AmassItem<T, TZ>* items, int count, cudaStream_t s);
 // thread blocks of a pre-smoothing launch on level g with window width `tile`
 template <typename T>
 long long strip_blocks(const Geom& g, int tile);
@@ -198,6 +266,56 @@ template <typename T>
 int prepare_low_vcycle(long long nc);
 template <typename T>
 void launch_low_vcycle(const LowArgs<T>& a, int cluster, cudaStream_t s);
+
+// ---- batched multigrid steps (one launch for `count` <= BATCH_MAX problems
+// on grids of the same size; items[i] carries problem i's arguments) --------
+template <typename T, typename TB> struct ChebInitItem {
+  const T* dinv;
+  const TB* b;
+  T bscale;
+  T* r;
+  T* d;
+  T inv_th;
+};
+template <typename T, typename TO> struct ChebLastItem {
+  const T* W;
+  T *x, *r;
+  const T* din;
+  int first;
+  TO* out;
+  T oscale;
+};
+template <typename T> struct TransferItem {
+  T* fine;          // restrict: fine residual (read); prolong: fine iterate (updated)
+  T* coarse;        // restrict: coarse right-hand side (written); prolong: coarse correction (read)
+};
+template <typename T> struct GemvItem {
+  const T* A;
+  const T* b;
+  T* x;
+};
+template <typename T> struct CoarseVItem {
+  const CoarseArgs<T>* a;   // device copy of the problem's CoarseArgs
+  const T* b_in;
+  const T* x_in;
+  T* x_out;
+};
+template <typename T, typename TB>
+void launch_cheb_init_b(int dim, const Geom& g, const ChebInitItem<T, TB>* items, int count, cudaStream_t s);
+template <typename T, typename TO>
+void launch_cheb_last_b(int dim, const Geom& g, const ChebLastItem<T, TO>* items, int count, cudaStream_t s);
+template <typename T>
+void launch_restrict_b(int dim, const Geom& gf, const Geom& gc, const TransferItem<T>* items, int count,
+                       cudaStream_t s);
+template <typename T>
+void launch_prolong_add_b(int dim, const Geom& gf, const Geom& gc, const TransferItem<T>* items, int count,
+                          cudaStream_t s);
+// the coarsest solve x = A^{-1} b: many-block GEMV (gemv, padded stride ld) or one block per problem
+template <typename T>
+void launch_coarse_solve_b(long long nc, long long ld, bool gemv, const GemvItem<T>* items, int count,
+                           cudaStream_t s);
+template <typename T>
+void launch_coarse_vcycle_b(int dim, const CoarseVItem<T>* items, int count, size_t smem, cudaStream_t s);
 
 // dense matrix of a level operator (row-major nv x nv) from its class table
 void launch_dense_from_table(int dim, const Geom& g, const double* W, double* A, cudaStream_t s);
@@ -228,6 +346,19 @@ void launch_update_norm_check(const double* V, long long ldv, int K, double* w, 
                               KrylovState* ks, int j, cudaStream_t s, bool single = false);
 // w *= ks->inv_eta
 void launch_scale_by(double* w, long long N, const double* factor, cudaStream_t s);
+// one problem of a batched Arnoldi orthogonalisation
+struct KrylovItem {
+  const double* V;       // basis v_0..v_j, leading dimension ldv
+  long long ldv;
+  double* w;             // the vector being orthogonalised (becomes v_{j+1})
+  long long N;
+  double* partials;      // the problem's reduction scratch
+  unsigned int* counter;
+  KrylovState* ks;
+  int h_out_is_h2;       // internal: multidot result into h2 instead of h1
+};
+// CGS2 orthogonalisation of step j for `count` <= BATCH_MAX problems per launch
+void launch_cgs2_batch(const KrylovItem* items, int count, int K, int j, cudaStream_t s);
 // out = ||x||_2 (device scalar)
 void launch_norm(const double* x, long long N, RedScratch rs, double* out, cudaStream_t s);
 // cycle start: v0 = r / beta with beta = ||r|| on device; ks reset

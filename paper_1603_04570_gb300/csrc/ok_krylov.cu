@@ -131,12 +131,11 @@ __device__ __forceinline__ void final_sums(const double* __restrict__ partials, 
 // out[k] = v_k . w (k < K); with NORM also *nrm = w . w.  A kernel given a
 // skip flag returns at once when the flag is set.
 template <int K, bool NORM>
-__global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ V, long long ldv,
-                                                 const double* __restrict__ w, long long N,
-                                                 double* __restrict__ partials, unsigned int* counter,
-                                                 double* __restrict__ out, const int* __restrict__ skip,
-                                                 double* __restrict__ nrm) {
-  pdl_entry();
+__device__ __forceinline__ void multidot_body(const double* __restrict__ V, long long ldv,
+                                              const double* __restrict__ w, long long N,
+                                              double* __restrict__ partials, unsigned int* counter,
+                                              double* __restrict__ out, const int* __restrict__ skip,
+                                              double* __restrict__ nrm) {
   if (skip && *skip) return;
   constexpr int NA = K + (NORM ? 1 : 0);
   double acc[NA];
@@ -159,13 +158,21 @@ __global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ V, l
     }
   }
 }
+template <int K, bool NORM>
+__global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ V, long long ldv,
+                                                 const double* __restrict__ w, long long N,
+                                                 double* __restrict__ partials, unsigned int* counter,
+                                                 double* __restrict__ out, const int* __restrict__ skip,
+                                                 double* __restrict__ nrm) {
+  pdl_entry();
+  multidot_body<K, NORM>(V, ldv, w, N, partials, counter, out, skip, nrm);
+}
 
 template <int K>
-__global__ void __launch_bounds__(RT) k_update_multidot(const double* __restrict__ V, long long ldv,
-                                                        const double* __restrict__ hin, double* __restrict__ w,
-                                                        long long N, double* __restrict__ partials,
-                                                        unsigned int* counter, double* __restrict__ out) {
-  pdl_entry();
+__device__ __forceinline__ void update_multidot_body(const double* __restrict__ V, long long ldv,
+                                                     const double* __restrict__ hin, double* __restrict__ w,
+                                                     long long N, double* __restrict__ partials,
+                                                     unsigned int* counter, double* __restrict__ out) {
   __shared__ double hs[K];
   if (threadIdx.x < K) hs[threadIdx.x] = hin[threadIdx.x];
   __syncthreads();
@@ -185,6 +192,14 @@ __global__ void __launch_bounds__(RT) k_update_multidot(const double* __restrict
   }
   block_partials<K>(acc, K, partials);
   if (last_block(counter)) final_sums(partials, K, out);
+}
+template <int K>
+__global__ void __launch_bounds__(RT) k_update_multidot(const double* __restrict__ V, long long ldv,
+                                                        const double* __restrict__ hin, double* __restrict__ w,
+                                                        long long N, double* __restrict__ partials,
+                                                        unsigned int* counter, double* __restrict__ out) {
+  pdl_entry();
+  update_multidot_body<K>(V, ldv, hin, w, N, partials, counter, out);
 }
 
 // Column j of H from h1 (+ h2 when `two`), eta = sqrt(s); Givens rotations
@@ -222,12 +237,11 @@ __device__ void arnoldi_column(KrylovState* ks, int j, double s, bool two) {
 // (h1 + h2), Givens rotations, residual estimate.  Returns at once when
 // `skip` is set.
 template <int K>
-__global__ void __launch_bounds__(RT) k_update_norm_givens(const double* __restrict__ V, long long ldv,
-                                                           double* __restrict__ w, long long N,
-                                                           double* __restrict__ partials, unsigned int* counter,
-                                                           KrylovState* ks, int j, int K0,
-                                                           const int* __restrict__ skip) {
-  pdl_entry();
+__device__ __forceinline__ void update_norm_givens_body(const double* __restrict__ V, long long ldv,
+                                                        double* __restrict__ w, long long N,
+                                                        double* __restrict__ partials, unsigned int* counter,
+                                                        KrylovState* ks, int j, int K0,
+                                                        const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ double hs[K];
   if (threadIdx.x < K) hs[threadIdx.x] = ks->h2[K0 + threadIdx.x];
@@ -250,6 +264,15 @@ __global__ void __launch_bounds__(RT) k_update_norm_givens(const double* __restr
     if (skip) ks->passes2 += 1;
     arnoldi_column(ks, j, s, true);
   }
+}
+template <int K>
+__global__ void __launch_bounds__(RT) k_update_norm_givens(const double* __restrict__ V, long long ldv,
+                                                           double* __restrict__ w, long long N,
+                                                           double* __restrict__ partials, unsigned int* counter,
+                                                           KrylovState* ks, int j, int K0,
+                                                           const int* __restrict__ skip) {
+  pdl_entry();
+  update_norm_givens_body<K>(V, ldv, w, N, partials, counter, ks, j, K0, skip);
 }
 
 // First-pass update w -= V h1 (h1 = ks->h1[K0..K0+K)), ||w||^2; last block:
@@ -286,10 +309,9 @@ __global__ void __launch_bounds__(RT) k_update_norm_check(const double* __restri
 }
 
 template <int K>
-__global__ void __launch_bounds__(RT) k_update_only(const double* __restrict__ V, long long ldv,
-                                                    const double* __restrict__ h, double* __restrict__ w,
-                                                    long long N, const int* __restrict__ skip) {
-  pdl_entry();
+__device__ __forceinline__ void update_only_body(const double* __restrict__ V, long long ldv,
+                                                 const double* __restrict__ h, double* __restrict__ w, long long N,
+                                                 const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ double hs[K];
   if (threadIdx.x < K) hs[threadIdx.x] = h[threadIdx.x];
@@ -303,6 +325,48 @@ __global__ void __launch_bounds__(RT) k_update_only(const double* __restrict__ V
     for (int k = 0; k < K; ++k) we = fma(-hs[k], vals[k], we);
     w[e] = we;
   }
+}
+template <int K>
+__global__ void __launch_bounds__(RT) k_update_only(const double* __restrict__ V, long long ldv,
+                                                    const double* __restrict__ h, double* __restrict__ w,
+                                                    long long N, const int* __restrict__ skip) {
+  pdl_entry();
+  update_only_body<K>(V, ldv, h, w, N, skip);
+}
+
+// ---- batched forms: problem blockIdx.y of the batch -----------------------
+template <int K, bool NORM>
+__global__ void __launch_bounds__(RT) k_multidot_b(Batch<KrylovItem> B, int k0) {
+  pdl_entry();
+  const KrylovItem& a = B.a[blockIdx.y];
+  multidot_body<K, NORM>(a.V + k0 * a.ldv, a.ldv, a.w, a.N, a.partials, a.counter,
+                         (a.h_out_is_h2 ? a.ks->h2 : a.ks->h1) + k0, (const int*)nullptr,
+                         NORM ? &a.ks->nw0 : (double*)nullptr);
+}
+template <int K>
+__global__ void __launch_bounds__(RT) k_update_multidot_b(Batch<KrylovItem> B) {
+  pdl_entry();
+  const KrylovItem& a = B.a[blockIdx.y];
+  update_multidot_body<K>(a.V, a.ldv, a.ks->h1, a.w, a.N, a.partials, a.counter, a.ks->h2);
+}
+template <int K>
+__global__ void __launch_bounds__(RT) k_update_only_b(Batch<KrylovItem> B, int k0, int second) {
+  pdl_entry();
+  const KrylovItem& a = B.a[blockIdx.y];
+  update_only_body<K>(a.V + k0 * a.ldv, a.ldv, (second ? a.ks->h2 : a.ks->h1) + k0, a.w, a.N, (const int*)nullptr);
+}
+template <int K>
+__global__ void __launch_bounds__(RT) k_update_norm_givens_b(Batch<KrylovItem> B, int j, int k0) {
+  pdl_entry();
+  const KrylovItem& a = B.a[blockIdx.y];
+  update_norm_givens_body<K>(a.V + k0 * a.ldv, a.ldv, a.w, a.N, a.partials, a.counter, a.ks, j, k0,
+                             (const int*)nullptr);
+}
+__global__ void __launch_bounds__(RT) k_scale_by_b(Batch<KrylovItem> B) {
+  pdl_entry();
+  const KrylovItem& a = B.a[blockIdx.y];
+  const double f = a.ks->inv_eta;
+  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < a.N; e += (long long)gridDim.x * RT) a.w[e] *= f;
 }
 
 // run F.template operator()<K>() for the runtime K in 1..KC
@@ -521,6 +585,38 @@ template void launch_axpby<float, __half>(long long, double, const float*, doubl
 
 void launch_check_finite(const double* x, long long N, int* flag, cudaStream_t s) {
   launch_k(k_check_finite, krylov_blocks(), RT, 0, s, x, N, flag);
+}
+
+// One CGS2 Arnoldi orthogonalisation (h1 = V^T w; w -= V h1, h2 = V^T w;
+// w -= V h2, column j, Givens; w /= eta) of `count` problems per launch, the
+// same kernels' arithmetic as launch_multidot / launch_update_multidot /
+// launch_update_norm_givens / launch_scale_by.  K = j + 1 basis vectors.
+void launch_cgs2_batch(const KrylovItem* items, int count, int K, int j, cudaStream_t s) {
+  Batch<KrylovItem> B;
+  for (int i = 0; i < count; ++i) B.a[i] = items[i];
+  const dim3 grid(krylov_blocks(), count);
+  for (int k0 = 0; k0 < K; k0 += KC) {                    // h1
+    const int kk = K - k0 < KC ? K - k0 : KC;
+    with_k(kk, [&](auto KK) { launch_k(k_multidot_b<decltype(KK)::value, false>, grid, RT, 0, s, B, k0); });
+  }
+  if (K <= KC) {                                          // w -= V h1, h2 = V^T w
+    with_k(K, [&](auto KK) { launch_k(k_update_multidot_b<decltype(KK)::value>, grid, RT, 0, s, B); });
+  } else {
+    for (int k0 = 0; k0 < K; k0 += KC) {
+      const int kk = K - k0 < KC ? K - k0 : KC;
+      with_k(kk, [&](auto KK) { launch_k(k_update_only_b<decltype(KK)::value>, grid, RT, 0, s, B, k0, 0); });
+    }
+    Batch<KrylovItem> B2 = B;                             // h2 = V^T w into h2: multidot writes h1 + k0
+    for (int i = 0; i < count; ++i) B2.a[i].h_out_is_h2 = 1;
+    for (int k0 = 0; k0 < K; k0 += KC) {
+      const int kk = K - k0 < KC ? K - k0 : KC;
+      with_k(kk, [&](auto KK) { launch_k(k_multidot_b<decltype(KK)::value, false>, grid, RT, 0, s, B2, k0); });
+    }
+  }
+  int k0 = 0;                                             // w -= V h2, ||w||, column j
+  for (; K - k0 > KC; k0 += KC) launch_k(k_update_only_b<KC>, grid, RT, 0, s, B, k0, 1);
+  with_k(K - k0, [&](auto KK) { launch_k(k_update_norm_givens_b<decltype(KK)::value>, grid, RT, 0, s, B, j, k0); });
+  launch_k(k_scale_by_b, grid, RT, 0, s, B);
 }
 
 }  // namespace okg

@@ -118,6 +118,48 @@ __global__ void __launch_bounds__(512) k_coarse_solve(long long nc, const T* __r
   coarse_rows<T>(nc, A, b, x, threadIdx.x >> 5, blockDim.x >> 5);
 }
 
+// ---- batched forms (grid z folds the problem index, see batch_problem) -----
+template <int D, typename T, typename TB>
+__global__ void __launch_bounds__(BX) k_cheb_init_b(Batch<ChebInitItem<T, TB>> B, Geom g) {
+  OK_LEVEL_SMEM(D, T);
+  const ChebInitItem<T, TB>& a = B.a[batch_problem<D>(g)];
+  stage_level<D, T>(sW, sD, (const T*)nullptr, a.dinv);
+  Vtx<D> v;
+  if (!vertex_of_thread_at<D>(g, batch_plane<D>(g), v)) return;
+  cheb_init_at<D, T, TB>(v, sD, a.b, a.bscale, a.r, a.d, a.inv_th);
+}
+template <int D, typename T, typename TO>
+__global__ void __launch_bounds__(BX) k_cheb_last_b(Batch<ChebLastItem<T, TO>> B, Geom g) {
+  OK_LEVEL_SMEM(D, T);
+  const ChebLastItem<T, TO>& a = B.a[batch_problem<D>(g)];
+  stage_level<D, T>(sW, sD, a.r ? a.W : (const T*)nullptr, (const T*)nullptr);
+  Vtx<D> v;
+  if (!vertex_of_thread_at<D>(g, batch_plane<D>(g), v)) return;
+  cheb_last_at<D, T, TO>(g, v, sW, a.x, a.r, a.din, a.first != 0, a.out, a.oscale);
+}
+template <int D, typename T>
+__global__ void __launch_bounds__(BX) k_restrict_b(Batch<TransferItem<T>> B, Geom gf, Geom gc) {
+  pdl_entry();
+  const TransferItem<T>& a = B.a[batch_problem<D>(gc)];
+  Vtx<D> v;
+  if (!vertex_of_thread_at<D>(gc, batch_plane<D>(gc), v)) return;
+  restrict_at<D, T>(gf, v, a.fine, a.coarse);
+}
+template <int D, typename T>
+__global__ void __launch_bounds__(BX) k_prolong_add_b(Batch<TransferItem<T>> B, Geom gf, Geom gc) {
+  pdl_entry();
+  const TransferItem<T>& a = B.a[batch_problem<D>(gf)];
+  Vtx<D> v;
+  if (!vertex_of_thread_at<D>(gf, batch_plane<D>(gf), v)) return;
+  prolong_add_at<D, T>(gc, v, a.fine, a.coarse);
+}
+template <typename T>
+__global__ void __launch_bounds__(512) k_coarse_solve_b(Batch<GemvItem<T>> B, long long nc) {
+  pdl_entry();
+  const GemvItem<T>& a = B.a[blockIdx.x];
+  coarse_rows<T>(nc, a.A, a.b, a.x, threadIdx.x >> 5, blockDim.x >> 5);
+}
+
 // ---------------------------------------------------------------------------
 // fused coarse V-cycle: levels Lc..L in one thread block, vectors in shared
 // memory; the same sequence of steps as Prec::vcycle on the host, each step a
@@ -220,9 +262,8 @@ __device__ void fused_smooth(const CoarseArgs<T>& a, int l, T* sm, bool x_zero, 
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseArgs<T> a, const T* __restrict__ b_in,
-                                                        const T* x_in, T* x_out) {
-  pdl_entry();   // x_in may equal x_out
+__device__ __forceinline__ void coarse_vcycle_body(const CoarseArgs<T>& a, const T* __restrict__ b_in,
+                                                   const T* x_in, T* x_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int L = a.nlev - 1;
@@ -281,6 +322,19 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseArgs<T> a, const T
     fused_smooth<D, T>(a, l, sm, false, a.nu_post, false);
   }
   for (long long i = threadIdx.x; i < a.g[0].nv; i += blockDim.x) x_out[i] = sm[a.off[0] + i];
+}
+template <int D, typename T>
+__global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseArgs<T> a, const T* __restrict__ b_in,
+                                                        const T* x_in, T* x_out) {
+  pdl_entry();   // x_in may equal x_out
+  coarse_vcycle_body<D, T>(a, b_in, x_in, x_out);
+}
+// batched: one block per problem (the problems' level tables differ)
+template <int D, typename T>
+__global__ void __launch_bounds__(1024) k_coarse_vcycle_b(Batch<CoarseVItem<T>> B) {
+  pdl_entry();
+  const CoarseVItem<T>& it = B.a[blockIdx.x];
+  coarse_vcycle_body<D, T>(*it.a, it.b_in, it.x_in, it.x_out);
 }
 
 template <int D, typename T, typename TX, typename TY>
@@ -356,9 +410,8 @@ __global__ void k_gj_extract(long long n, const double* __restrict__ w, double* 
 constexpr int GEMV_WARPS = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(GEMV_WARPS * 32) k_coarse_gemv(long long nc, long long ld, const T* __restrict__ A,
-                                                                const T* __restrict__ b, T* __restrict__ x) {
-  pdl_launch_dependents();
+__device__ __forceinline__ void coarse_gemv_body(long long nc, long long ld, const T* __restrict__ A,
+                                                 const T* __restrict__ b, T* __restrict__ x) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sb = reinterpret_cast<T*>(smraw);
   const long long r = (long long)blockIdx.x * GEMV_WARPS + (threadIdx.x >> 5);
@@ -370,6 +423,18 @@ __global__ void __launch_bounds__(GEMV_WARPS * 32) k_coarse_gemv(long long nc, l
   if (r >= nc) return;
   const T acc = gemv_finish<T>(ld, A, sb, r, a0);
   if ((threadIdx.x & 31) == 0) x[r] = acc;
+}
+template <typename T>
+__global__ void __launch_bounds__(GEMV_WARPS * 32) k_coarse_gemv(long long nc, long long ld, const T* __restrict__ A,
+                                                                const T* __restrict__ b, T* __restrict__ x) {
+  pdl_launch_dependents();
+  coarse_gemv_body<T>(nc, ld, A, b, x);
+}
+template <typename T>
+__global__ void __launch_bounds__(GEMV_WARPS * 32) k_coarse_gemv_b(Batch<GemvItem<T>> B, long long nc, long long ld) {
+  pdl_launch_dependents();
+  const GemvItem<T>& a = B.a[blockIdx.y];
+  coarse_gemv_body<T>(nc, ld, a.A, a.b, a.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -433,7 +498,10 @@ cudaError_t prepare_coarse_gemv(long long nc) {
   // per-kernel limit shared by all handles: the largest coarsest level's need
   (void)nc;
   const size_t need = (size_t)gemv_staged<T>(gemv_ld(COARSE_NC_MAX, sizeof(T))) * sizeof(T);
-  return cudaFuncSetAttribute(k_coarse_gemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_coarse_gemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)std::max(need, (size_t)48 * 1024));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_coarse_gemv_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)std::max(need, (size_t)48 * 1024));
 }
 template <typename T, typename TX, typename TY>
@@ -452,8 +520,13 @@ template <typename T>
 cudaError_t prepare_coarse_vcycle(int dim, size_t smem) {
   if (smem > COARSE_SMEM_MAX) return cudaErrorInvalidValue;
   const int lim = (int)COARSE_SMEM_MAX;             // shared by all handles: never lowered
-  if (dim == 2) return cudaFuncSetAttribute(k_coarse_vcycle<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  return cudaFuncSetAttribute(k_coarse_vcycle<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (dim == 2) {
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_vcycle<2, T>, at, lim);
+    return e != cudaSuccess ? e : cudaFuncSetAttribute(k_coarse_vcycle_b<2, T>, at, lim);
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_coarse_vcycle<3, T>, at, lim);
+  return e != cudaSuccess ? e : cudaFuncSetAttribute(k_coarse_vcycle_b<3, T>, at, lim);
 }
 template void launch_coarse_vcycle<double>(int, const CoarseArgs<double>&, size_t, const double*, const double*,
                                            double*, cudaStream_t);
@@ -477,6 +550,75 @@ void launch_gauss_jordan(long long n, const double* A, double* work, double* Ain
   }
   launch_k(k_gj_extract, blocks, 256, 0, s, n, work, Ainv);
 }
+
+// ---- batched launchers ----------------------------------------------------
+template <int D>
+static inline dim3 grid_b(const Geom& g, int count) {
+  return dim3((g.n1 + BX - 1) / BX, g.n1, (D == 3 ? g.n1 : 1) * count);
+}
+template <typename I>
+static inline Batch<I> pack(const I* items, int count) {
+  Batch<I> B;
+  for (int i = 0; i < count; ++i) B.a[i] = items[i];
+  return B;
+}
+template <typename T, typename TB>
+void launch_cheb_init_b(int dim, const Geom& g, const ChebInitItem<T, TB>* items, int count, cudaStream_t s) {
+  auto B = pack(items, count);
+  if (dim == 2) launch_k(k_cheb_init_b<2, T, TB>, grid_b<2>(g, count), BX, 0, s, B, g);
+  else launch_k(k_cheb_init_b<3, T, TB>, grid_b<3>(g, count), BX, 0, s, B, g);
+}
+template <typename T, typename TO>
+void launch_cheb_last_b(int dim, const Geom& g, const ChebLastItem<T, TO>* items, int count, cudaStream_t s) {
+  auto B = pack(items, count);
+  if (dim == 2) launch_k(k_cheb_last_b<2, T, TO>, grid_b<2>(g, count), BX, 0, s, B, g);
+  else launch_k(k_cheb_last_b<3, T, TO>, grid_b<3>(g, count), BX, 0, s, B, g);
+}
+template <typename T>
+void launch_restrict_b(int dim, const Geom& gf, const Geom& gc, const TransferItem<T>* items, int count,
+                       cudaStream_t s) {
+  auto B = pack(items, count);
+  if (dim == 2) launch_k(k_restrict_b<2, T>, grid_b<2>(gc, count), BX, 0, s, B, gf, gc);
+  else launch_k(k_restrict_b<3, T>, grid_b<3>(gc, count), BX, 0, s, B, gf, gc);
+}
+template <typename T>
+void launch_prolong_add_b(int dim, const Geom& gf, const Geom& gc, const TransferItem<T>* items, int count,
+                          cudaStream_t s) {
+  auto B = pack(items, count);
+  if (dim == 2) launch_k(k_prolong_add_b<2, T>, grid_b<2>(gf, count), BX, 0, s, B, gf, gc);
+  else launch_k(k_prolong_add_b<3, T>, grid_b<3>(gf, count), BX, 0, s, B, gf, gc);
+}
+template <typename T>
+void launch_coarse_solve_b(long long nc, long long ld, bool gemv, const GemvItem<T>* items, int count,
+                           cudaStream_t s) {
+  auto B = pack(items, count);
+  if (gemv) {
+    const unsigned blocks = (unsigned)((nc + GEMV_WARPS - 1) / GEMV_WARPS);
+    launch_k(k_coarse_gemv_b<T>, dim3(blocks, count), GEMV_WARPS * 32, gemv_staged<T>(ld) * sizeof(T), s, B, nc, ld);
+  } else {
+    launch_k(k_coarse_solve_b<T>, count, 512, 0, s, B, nc);
+  }
+}
+template <typename T>
+void launch_coarse_vcycle_b(int dim, const CoarseVItem<T>* items, int count, size_t smem, cudaStream_t s) {
+  auto B = pack(items, count);
+  if (dim == 2) launch_k(k_coarse_vcycle_b<2, T>, count, 1024, smem, s, B);
+  else launch_k(k_coarse_vcycle_b<3, T>, count, 1024, smem, s, B);
+}
+#define OK_INST_B(T)                                                                                          \
+  template void launch_restrict_b<T>(int, const Geom&, const Geom&, const TransferItem<T>*, int, cudaStream_t); \
+  template void launch_prolong_add_b<T>(int, const Geom&, const Geom&, const TransferItem<T>*, int,          \
+                                        cudaStream_t);                                                        \
+  template void launch_coarse_solve_b<T>(long long, long long, bool, const GemvItem<T>*, int, cudaStream_t);  \
+  template void launch_coarse_vcycle_b<T>(int, const CoarseVItem<T>*, int, size_t, cudaStream_t);             \
+  template void launch_cheb_init_b<T, T>(int, const Geom&, const ChebInitItem<T, T>*, int, cudaStream_t);     \
+  template void launch_cheb_last_b<T, T>(int, const Geom&, const ChebLastItem<T, T>*, int, cudaStream_t);
+OK_INST_B(float)
+OK_INST_B(double)
+template void launch_cheb_init_b<float, double>(int, const Geom&, const ChebInitItem<float, double>*, int,
+                                                cudaStream_t);
+template void launch_cheb_last_b<float, __half>(int, const Geom&, const ChebLastItem<float, __half>*, int,
+                                                cudaStream_t);
 
 #define OK_INST_T(T)                                                                                          \
   template void launch_resid_init<T>(int, const Geom&, const T*, const T*, const T*, const T*, T*, T*, T,      \

@@ -41,23 +41,6 @@ using PShape2 = PShape<64, 4, 16>;
 using PShape3 = PShape<32, 8, 32>;
 constexpr int NTAB3 = Topo<3>::NCLASS * Topo<3>::NOFF;
 
-enum PlaneMode { PM_RESID = 0, PM_STEP = 1, PM_LAST = 2, PM_OP = 3 };
-
-template <typename T, typename TS, typename TO> struct PlaneArgs {
-  Geom g;
-  const T* W;          // class table of the operator (level-scaled)
-  const T* dinv;       // 1 / diagonal per class (RESID, STEP)
-  const TS* s;         // the vector the stencil reads: x (RESID, OP) or d (STEP, LAST)
-  T* x;                // STEP, LAST: iterate (in-out)
-  T* r;                // RESID: out; STEP, LAST: in-out
-  T* d;                // RESID: d out; STEP: d_out
-  const T* b;          // RESID: right-hand side
-  TO* out;             // LAST: optional cast of x; OP: y
-  const TO* y0;        // OP: optional y0
-  T c1, c2, inv_th, oscale, alpha, beta;
-  int first;           // STEP, LAST: x starts from zero
-  int axis_only;       // OP: first 2d + 1 offsets (K-like tables)
-};
 
 // the update of one vertex given its 15 stencil values (INT: interior class,
 // weights in registers)
@@ -107,7 +90,7 @@ __device__ __forceinline__ void plane_update(const PlaneArgs<T, TS, TO>& a, cons
 }
 
 template <typename T, typename TS, typename TO, int MODE, class C>
-__global__ void __launch_bounds__(C::PNT) k_plane3(PlaneArgs<T, TS, TO> a) {
+__device__ __forceinline__ void plane3_body(const PlaneArgs<T, TS, TO>& a, int zchunk) {
   using Tp = Topo<3>;
   constexpr int PX = C::PX, PY = C::PY, PZ = C::PZ, PW = C::PW, PH = C::PH, PNT = C::PNT, PSLOT = C::PSLOT;
   __shared__ T sW[NTAB3];
@@ -121,7 +104,7 @@ __global__ void __launch_bounds__(C::PNT) k_plane3(PlaneArgs<T, TS, TO> a) {
   const int n = g.n;
   const int tx = threadIdx.x % PX, ty = threadIdx.x / PX;
   const int gx = blockIdx.x * PX + tx, gy = blockIdx.y * PY + ty;
-  const int z0 = blockIdx.z * PZ;
+  const int z0 = zchunk * PZ;
   const int z1 = min(z0 + PZ, n + 1);
   // padded-plane elements this thread stages: (ey, ex) -> global (x0 + ex - 1, y0 + ey - 1)
   long long eoff[PSLOT];
@@ -214,6 +197,15 @@ __global__ void __launch_bounds__(C::PNT) k_plane3(PlaneArgs<T, TS, TO> a) {
     else plane_update<T, TS, TO, MODE, false>(a, rw, sW, sD, cx + 3 * cy + 9 * axis_class(z, n), xs, gi, xv, rv, bv);
   }
 }
+template <typename T, typename TS, typename TO, int MODE, class C>
+__global__ void __launch_bounds__(C::PNT) k_plane3(PlaneArgs<T, TS, TO> a) {
+  plane3_body<T, TS, TO, MODE, C>(a, blockIdx.z);
+}
+// batched: blockIdx.z = problem * (z-chunks) + chunk
+template <typename T, typename TS, typename TO, int MODE, class C>
+__global__ void __launch_bounds__(C::PNT) k_plane3_b(Batch<PlaneArgs<T, TS, TO>> B, int nzc) {
+  plane3_body<T, TS, TO, MODE, C>(B.a[blockIdx.z / nzc], blockIdx.z % nzc);
+}
 
 template <class C>
 static inline dim3 plane_grid(const Geom& g) {
@@ -227,6 +219,35 @@ static void launch_plane(const PlaneArgs<T, TS, TO>& a, int shape, cudaStream_t 
     case 2: launch_k(k_plane3<T, TS, TO, MODE, PShape2>, plane_grid<PShape2>(a.g), PShape2::PNT, 0, s, a); break;
     case 3: launch_k(k_plane3<T, TS, TO, MODE, PShape3>, plane_grid<PShape3>(a.g), PShape3::PNT, 0, s, a); break;
     default: launch_k(k_plane3<T, TS, TO, MODE, PShape0>, plane_grid<PShape0>(a.g), PShape0::PNT, 0, s, a);
+  }
+}
+
+template <typename T, typename TS, typename TO, int MODE, class C>
+static void launch_plane_b1(const Batch<PlaneArgs<T, TS, TO>>& B, const Geom& g, int count, cudaStream_t s) {
+  dim3 gr = plane_grid<C>(g);
+  const int nzc = (int)gr.z;
+  gr.z = nzc * count;
+  launch_k(k_plane3_b<T, TS, TO, MODE, C>, gr, C::PNT, 0, s, B, nzc);
+}
+template <typename T, typename TS, typename TO>
+void launch_plane3_b(int mode, const PlaneArgs<T, TS, TO>* items, int count, int shape, cudaStream_t s) {
+  Batch<PlaneArgs<T, TS, TO>> B;
+  for (int i = 0; i < count; ++i) B.a[i] = items[i];
+  const Geom& g = items[0].g;
+  auto go = [&](auto M) {
+    constexpr int MODE = decltype(M)::value;
+    switch (shape) {
+      case 1: launch_plane_b1<T, TS, TO, MODE, PShape1>(B, g, count, s); break;
+      case 2: launch_plane_b1<T, TS, TO, MODE, PShape2>(B, g, count, s); break;
+      case 3: launch_plane_b1<T, TS, TO, MODE, PShape3>(B, g, count, s); break;
+      default: launch_plane_b1<T, TS, TO, MODE, PShape0>(B, g, count, s);
+    }
+  };
+  switch (mode) {
+    case PM_RESID: go(std::integral_constant<int, PM_RESID>{}); break;
+    case PM_STEP: go(std::integral_constant<int, PM_STEP>{}); break;
+    case PM_LAST: go(std::integral_constant<int, PM_LAST>{}); break;
+    default: go(std::integral_constant<int, PM_OP>{});
   }
 }
 
@@ -303,6 +324,10 @@ void launch_op_apply3(const Geom& g, const T* W, bool axis_only, const TX* x, TY
                                           cudaStream_t, int);
 OK_PLANE_INST(float)
 OK_PLANE_INST(double)
+template void launch_plane3_b<float, float, float>(int, const PlaneArgs<float, float, float>*, int, int,
+                                                   cudaStream_t);
+template void launch_plane3_b<double, double, double>(int, const PlaneArgs<double, double, double>*, int, int,
+                                                      cudaStream_t);
 template void launch_cheb_last3<float, double>(const Geom&, const float*, float*, float*, const float*, bool,
                                                double*, float, cudaStream_t, int);
 template void launch_cheb_last3<float, __half>(const Geom&, const float*, float*, float*, const float*, bool,

@@ -300,10 +300,9 @@ __device__ __forceinline__ void strip_pre_body(const TileSmooth<T>& a, const Pos
 }
 
 template <typename T, class G>
-__global__ void __launch_bounds__(G::NT) k_strip_pre(TileSmooth<T> a, const T* __restrict__ x_in,
-                                                      const T* __restrict__ b, T* __restrict__ x_out,
-                                                      T* __restrict__ bc) {
-  pdl_launch_dependents();
+__device__ __forceinline__ void strip_pre_kernel(const TileSmooth<T>& a, const T* __restrict__ x_in,
+                                                 const T* __restrict__ b, T* __restrict__ x_out,
+                                                 T* __restrict__ bc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
   T* buf1 = buf0 + G::SB;
@@ -317,6 +316,19 @@ __global__ void __launch_bounds__(G::NT) k_strip_pre(TileSmooth<T> a, const T* _
     strip_pre_body<T, G, true>(a, p, buf0, buf1, sW, sD, x_in, b, x_out, bc);
   else
     strip_pre_body<T, G, false>(a, p, buf0, buf1, sW, sD, x_in, b, x_out, bc);
+}
+template <typename T, class G>
+__global__ void __launch_bounds__(G::NT) k_strip_pre(TileSmooth<T> a, const T* __restrict__ x_in,
+                                                      const T* __restrict__ b, T* __restrict__ x_out,
+                                                      T* __restrict__ bc) {
+  pdl_launch_dependents();
+  strip_pre_kernel<T, G>(a, x_in, b, x_out, bc);
+}
+template <typename T, class G>
+__global__ void __launch_bounds__(G::NT) k_strip_pre_b(Batch<StripPreItem<T>> B) {
+  pdl_launch_dependents();
+  const StripPreItem<T>& it = B.a[blockIdx.z];
+  strip_pre_kernel<T, G>(it.a, it.x_in, it.b, it.x_out, it.bc);
 }
 
 // ---------------------------------------------------------------------------
@@ -415,11 +427,10 @@ __device__ __forceinline__ void strip_post_body(const TileSmooth<T>& a, const Po
 }
 
 template <typename T, typename TO, class G>
-__global__ void __launch_bounds__(G::NT) k_strip_post(TileSmooth<T> a, const T* __restrict__ x_in,
-                                                       const T* __restrict__ xc, const T* __restrict__ b,
-                                                       T* __restrict__ x_out, T* __restrict__ mx_out,
-                                                       TO* __restrict__ out, T oscale) {
-  pdl_launch_dependents();
+__device__ __forceinline__ void strip_post_kernel(const TileSmooth<T>& a, const T* __restrict__ x_in,
+                                                  const T* __restrict__ xc, const T* __restrict__ b,
+                                                  T* __restrict__ x_out, T* __restrict__ mx_out,
+                                                  TO* __restrict__ out, T oscale) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
   T* buf1 = buf0 + G::SB;
@@ -435,6 +446,20 @@ __global__ void __launch_bounds__(G::NT) k_strip_post(TileSmooth<T> a, const T* 
     strip_post_body<T, TO, G, true>(a, p, buf0, buf1, sW, sD, sM, x_in, xc, b, x_out, mx_out, out, oscale);
   else
     strip_post_body<T, TO, G, false>(a, p, buf0, buf1, sW, sD, sM, x_in, xc, b, x_out, mx_out, out, oscale);
+}
+template <typename T, typename TO, class G>
+__global__ void __launch_bounds__(G::NT) k_strip_post(TileSmooth<T> a, const T* __restrict__ x_in,
+                                                       const T* __restrict__ xc, const T* __restrict__ b,
+                                                       T* __restrict__ x_out, T* __restrict__ mx_out,
+                                                       TO* __restrict__ out, T oscale) {
+  pdl_launch_dependents();
+  strip_post_kernel<T, TO, G>(a, x_in, xc, b, x_out, mx_out, out, oscale);
+}
+template <typename T, typename TO, class G>
+__global__ void __launch_bounds__(G::NT) k_strip_post_b(Batch<StripPostItem<T, TO>> B) {
+  pdl_launch_dependents();
+  const StripPostItem<T, TO>& it = B.a[blockIdx.z];
+  strip_post_kernel<T, TO, G>(it.a, it.x_in, it.xc, it.b, it.x_out, it.mx_out, it.out, it.oscale);
 }
 
 // ---------------------------------------------------------------------------
@@ -547,9 +572,8 @@ __device__ __forceinline__ void strip_amass_body(const TileMass<T>& a, const Pos
 }
 
 template <typename T, typename TZ, class G, int K0, int K1, bool FIRST, bool LAST>
-__global__ void __launch_bounds__(G::NT) k_strip_amass(TileMass<T> a, const double* __restrict__ v,
-                                                        TZ* __restrict__ z1, T* __restrict__ t_out) {
-  pdl_launch_dependents();
+__device__ __forceinline__ void strip_amass_kernel(const TileMass<T>& a, const double* __restrict__ v,
+                                                   TZ* __restrict__ z1, T* __restrict__ t_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
   T* buf1 = buf0 + G::SB;
@@ -563,6 +587,18 @@ __global__ void __launch_bounds__(G::NT) k_strip_amass(TileMass<T> a, const doub
     strip_amass_body<T, TZ, G, true, K0, K1, FIRST, LAST>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
   else
     strip_amass_body<T, TZ, G, false, K0, K1, FIRST, LAST>(a, p, buf0, buf1, sW, sD, v, z1, t_out);
+}
+template <typename T, typename TZ, class G, int K0, int K1, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(G::NT) k_strip_amass(TileMass<T> a, const double* __restrict__ v,
+                                                        TZ* __restrict__ z1, T* __restrict__ t_out) {
+  pdl_launch_dependents();
+  strip_amass_kernel<T, TZ, G, K0, K1, FIRST, LAST>(a, v, z1, t_out);
+}
+template <typename T, typename TZ, class G, int K0, int K1, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(G::NT) k_strip_amass_b(Batch<AmassItem<T, TZ>> B) {
+  pdl_launch_dependents();
+  const AmassItem<T, TZ>& it = B.a[blockIdx.z];
+  strip_amass_kernel<T, TZ, G, K0, K1, FIRST, LAST>(it.a, it.v, it.z1, it.t_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -738,6 +774,52 @@ void launch_tile_amass(const TileMass<T>& a, const double* v, TZ* z1, T* t_out, 
 }
 
 template <typename T>
+void launch_tile_pre_b(const StripPreItem<T>* items, int count, cudaStream_t s) {
+  using Big = typename StripCfg<T>::template Big<4>;
+  using Small = typename StripCfg<T>::template Small<4>;
+  Batch<StripPreItem<T>> B;
+  for (int i = 0; i < count; ++i) B.a[i] = items[i];
+  const TileSmooth<T>& a = items[0].a;
+  if (a.tile == 64) {
+    dim3 gr = strip_grid<Big>(a.g);
+    gr.z = count;
+    launch_k(k_strip_pre_b<T, Big>, gr, Big::NT, strip_smem<Big, T>(false), s, B);
+  } else {
+    dim3 gr = strip_grid<Small>(a.g);
+    gr.z = count;
+    launch_k(k_strip_pre_b<T, Small>, gr, Small::NT, strip_smem<Small, T>(false), s, B);
+  }
+}
+template <typename T, typename TO>
+void launch_tile_post_b(const StripPostItem<T, TO>* items, int count, cudaStream_t s) {
+  using Big = typename StripCfg<T>::template Big<3>;
+  using Small = typename StripCfg<T>::template Small<3>;
+  Batch<StripPostItem<T, TO>> B;
+  for (int i = 0; i < count; ++i) B.a[i] = items[i];
+  const TileSmooth<T>& a = items[0].a;
+  if (a.tile == 64) {
+    dim3 gr = strip_grid<Big>(a.g);
+    gr.z = count;
+    launch_k(k_strip_post_b<T, TO, Big>, gr, Big::NT, strip_smem<Big, T>(true), s, B);
+  } else {
+    dim3 gr = strip_grid<Small>(a.g);
+    gr.z = count;
+    launch_k(k_strip_post_b<T, TO, Small>, gr, Small::NT, strip_smem<Small, T>(true), s, B);
+  }
+}
+template <typename T, typename TZ>
+void launch_tile_amass_b(const AmassItem<T, TZ>* items, int count, cudaStream_t s) {
+  using Mass = typename StripCfg<T>::Mass;
+  Batch<AmassItem<T, TZ>> B;
+  for (int i = 0; i < count; ++i) B.a[i] = items[i];
+  dim3 gr = strip_grid<Mass>(items[0].a.g);
+  gr.z = count;
+  launch_k(k_strip_amass_b<T, TZ, Mass, 0, QSPLIT, true, false>, gr, Mass::NT, strip_smem<Mass, T>(false), s, B);
+  launch_k(k_strip_amass_b<T, TZ, Mass, QSPLIT, QTILE - 1, false, true>, gr, Mass::NT, strip_smem<Mass, T>(false), s,
+           B);
+}
+
+template <typename T>
 cudaError_t prepare_tiles(int q) {
   (void)q;
   using Cfg = StripCfg<T>;
@@ -758,6 +840,26 @@ cudaError_t prepare_tiles(int q) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, float, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, double, MA, 0, QSPLIT, true, false>, attr, ms);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, double, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_pre_b<T, BP>, attr, (int)strip_smem<BP, T>(false));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_pre_b<T, SP>, attr, (int)strip_smem<SP, T>(false));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, T, BQ>, attr, (int)strip_smem<BQ, T>(true));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, T, SQ>, attr, (int)strip_smem<SQ, T>(true));
+  if constexpr (std::is_same<T, float>::value) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, float, BQ>, attr, (int)strip_smem<BQ, T>(true));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, float, SQ>, attr, (int)strip_smem<SQ, T>(true));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, __half, BQ>, attr, (int)strip_smem<BQ, T>(true));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, __half, SQ>, attr, (int)strip_smem<SQ, T>(true));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass_b<T, float, MA, 0, QSPLIT, true, false>, attr, ms);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_strip_amass_b<T, float, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass_b<T, __half, MA, 0, QSPLIT, true, false>, attr, ms);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_strip_amass_b<T, __half, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
+  } else {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass_b<T, double, MA, 0, QSPLIT, true, false>, attr, ms);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_strip_amass_b<T, double, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, __half, BQ>, attr, (int)strip_smem<BQ, T>(true));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, __half, SQ>, attr, (int)strip_smem<SQ, T>(true));
@@ -798,5 +900,13 @@ template void launch_tile_post<float, __half>(const TileSmooth<float>&, const fl
                                               float*, float*, __half*, float, cudaStream_t);
 template void launch_tile_amass<float, __half>(const TileMass<float>&, const double*, __half*, float*,
                                                cudaStream_t);
+template void launch_tile_pre_b<float>(const StripPreItem<float>*, int, cudaStream_t);
+template void launch_tile_pre_b<double>(const StripPreItem<double>*, int, cudaStream_t);
+template void launch_tile_post_b<float, float>(const StripPostItem<float, float>*, int, cudaStream_t);
+template void launch_tile_post_b<float, __half>(const StripPostItem<float, __half>*, int, cudaStream_t);
+template void launch_tile_post_b<double, double>(const StripPostItem<double, double>*, int, cudaStream_t);
+template void launch_tile_amass_b<float, float>(const AmassItem<float, float>*, int, cudaStream_t);
+template void launch_tile_amass_b<float, __half>(const AmassItem<float, __half>*, int, cudaStream_t);
+template void launch_tile_amass_b<double, double>(const AmassItem<double, double>*, int, cudaStream_t);
 
 }  // namespace okg

@@ -616,3 +616,72 @@ def test_energy_of_constant_state_and_along_timesteps():
             e = g.energy(u)[1]
             assert e < prev
             prev = e
+
+
+def _cohort_requests(dim, n, count, precision, seed):
+    """`count` requests on one grid with different (eps, sigma, m, theta, dt) and
+    initial states, the serving stream's parameter ranges."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        eps = 0.01 + 0.04 * rng.uniform()
+        p = dict(eps=eps, sigma=10.0 ** (1 + 2 * rng.uniform()), m=-0.3 + 0.6 * rng.uniform(),
+                 theta=0.5 if k % 2 else 1.0, dt=0.25 * eps * eps)
+        nv = (n + 1) ** dim
+        u0 = p["m"] + 0.01 * rng.uniform(-1, 1, nv)
+        out.append((p, u0, 2 + (k % 3)))
+    return out
+
+
+@pytest.mark.parametrize("dim,n,precision", [(2, 64, ok.OK_MIXED), (2, 100, ok.OK_FP64), (3, 24, ok.OK_MIXED),
+                                             (3, 32, ok.OK_FP64), (2, 48, ok.OK_MIXED_HALF)])
+def test_batch_cohort_is_bitwise_the_solo_result(dim, n, precision):
+    """ok_solve_batch on requests of one grid with different parameters, states
+    and step counts: they run as one cohort (every Arnoldi step's kernels one
+    launch over the members still iterating), and each request's u and w after
+    its steps equal, bit for bit, what ok_timestep gives it alone; a request on
+    another grid in the same call runs alone.  The cohort launches far fewer
+    kernels than the members would one by one."""
+    reqs = _cohort_requests(dim, n, 5, precision, seed=dim * 100 + n)
+    opts = dict(precision=precision, gmres_rtol=1e-8, newton_atol=1e-9)
+    solo, grids, states = [], [], []
+    launches_solo = 0
+    for p, u0, steps in reqs:
+        with ok.Grid(dim, n, **p, **opts) as g:
+            u, w = dev(u0), torch.zeros_like(dev(u0))
+            g.init_w(u, w)
+            w0 = host(w)
+            torch.cuda.synchronize()
+            c0 = ok.ok_launch_count()
+            for _ in range(steps):
+                g.timestep(u, w)
+            torch.cuda.synchronize()
+            launches_solo += ok.ok_launch_count() - c0
+            solo.append((host(u), host(w)))
+            states.append((u0, w0))
+    for p, _, _ in reqs:
+        grids.append(ok.Grid(dim, n, **p, **opts))
+    other = ok.Grid(2, 16, 0.05, 50.0, 0.0, 1.0, 1e-3)
+    try:
+        batch = [(g, dev(u0), dev(w0), steps) for g, (u0, w0), (_, _, steps) in zip(grids, states, reqs)]
+        ou, ow = dev(0.01 * np.random.default_rng(2).uniform(-1, 1, other.nv)), None
+        ow = torch.zeros_like(ou)
+        other.init_w(ou, ow)
+        ref_other = (ou.clone(), ow.clone())
+        torch.cuda.synchronize()
+        c0 = ok.ok_launch_count()
+        st, out, info = ok.ok_solve_batch(batch + [(other, ou, ow, 2)])
+        torch.cuda.synchronize()
+        launches_batch = ok.ok_launch_count() - c0
+        assert st == ok.OK_SUCCESS and info.completed == len(batch) + 1
+        for (g, u, w, steps), (us, ws) in zip(batch, solo):
+            assert np.array_equal(host(u), us) and np.array_equal(host(w), ws)
+        for k in range(2):
+            other.timestep(*ref_other)
+        assert torch.equal(ou, ref_other[0]) and torch.equal(ow, ref_other[1])
+        # shared launches: the five members together launch well under the sum of their solo runs
+        assert launches_batch < 0.6 * launches_solo, (launches_batch, launches_solo)
+    finally:
+        for g in grids:
+            g.close()
+        other.close()
