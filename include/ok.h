@@ -239,14 +239,20 @@ int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream st
  * continuously.  Requests are taken in order of `arrival` (seconds after the
  * call starts); one is admitted when it has arrived, fewer than
  * `max_inflight` are in flight and its estimated device footprint (Krylov
- * basis dominant) fits in `mem_budget` bytes beside those in flight.  Each
- * admitted request runs on its own host thread and non-blocking stream:
- * ok_grid_create, ok_init_w when init_w != 0, `steps` ok_timestep calls,
- * ok_grid_destroy, so the work of requests in flight overlaps on the device.
- * A request's arithmetic does not depend on what else runs: its results are
- * bitwise those it gets alone.  Returns the status of the first failed
- * request (all requests run regardless); OK_ERR_NOMEM marks a request whose
- * footprint exceeds the whole budget. */
+ * basis dominant) fits in `mem_budget` bytes beside those in flight.  An
+ * admitted request's handle (ok_grid_create) and w0 (ok_init_w when
+ * init_w != 0) are set up on a thread of its own; it then joins the group of
+ * requests with its (dim, n, options), whose host thread and non-blocking
+ * stream advance the group's members a timestep at a time as one cohort
+ * (the shared launches of ok_solve_batch, up to 8 members; a member joins at
+ * the next timestep boundary and leaves after its last step, when its handle
+ * is destroyed and its slot and bytes are released).  Groups run
+ * concurrently.  During the call the device blocks of destroyed handles are
+ * reused by later handles of the same sizes instead of being freed and
+ * allocated again.  A request's arithmetic does not depend on what else runs:
+ * its results are bitwise those it gets alone.  Returns the status of the
+ * first failed request (all requests run regardless); OK_ERR_NOMEM marks a
+ * request whose footprint exceeds the whole budget. */
 typedef struct ok_serve_request {
   int dim, n;               /* in: grid                                              */
   ok_params params;         /* in                                                    */
@@ -268,6 +274,8 @@ typedef struct ok_serve_info {
   int peak_inflight;        /* most requests in flight at once                       */
   long long peak_bytes;     /* most estimated bytes in flight at once                */
   double seconds;           /* wall time of the call                                 */
+  int peak_cohort;          /* most requests advanced by one cohort timestep         */
+  int cohort_steps;         /* cohort timesteps with two or more members             */
 } ok_serve_info;
 
 int ok_serve(ok_serve_request* reqs, int count, int max_inflight, long long mem_budget, ok_serve_info* info);

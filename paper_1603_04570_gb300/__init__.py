@@ -63,7 +63,7 @@ class ServeRequest(Structure):
 
 class ServeInfo(Structure):
     _fields_ = [("completed", c_int), ("failed", c_int), ("peak_inflight", c_int), ("peak_bytes", c_longlong),
-                ("seconds", c_double)]
+                ("seconds", c_double), ("peak_cohort", c_int), ("cohort_steps", c_int)]
 
 
 class KernelStat(Structure):

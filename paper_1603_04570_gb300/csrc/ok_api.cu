@@ -10,6 +10,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <deque>
 #include <mutex>
 #include <thread>
 #include <cmath>
@@ -171,26 +172,86 @@ struct Profiler {
 // ---------------------------------------------------------------------------
 // device memory owned by a handle
 // ---------------------------------------------------------------------------
+// While ok_serve runs, the device blocks of destroyed handles are kept per
+// (device, size) and handed to later handles that ask for the same sizes
+// (requests of one grid and options ask for identical lists), so admitting a
+// request does not call cudaMalloc / cudaFree next to the requests in flight;
+// the blocks are freed when the last ok_serve returns.
+struct DevicePool {
+  std::mutex mu;
+  int users = 0;
+  std::multimap<std::pair<int, size_t>, void*> blocks;
+};
+DevicePool g_pool;
+
+struct PoolScope {                    // pooling on for the lifetime of an ok_serve call
+  PoolScope() {
+    std::lock_guard<std::mutex> lk(g_pool.mu);
+    ++g_pool.users;
+  }
+  ~PoolScope() {
+    std::lock_guard<std::mutex> lk(g_pool.mu);
+    if (--g_pool.users == 0) {
+      for (auto& kv : g_pool.blocks) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(kv.first.first);
+        cudaFree(kv.second);
+        cudaSetDevice(cur);
+      }
+      g_pool.blocks.clear();
+    }
+  }
+};
+
 struct Arena {
-  std::vector<void*> ptrs;
+  struct Block {
+    void* p;
+    size_t bytes;
+    int device;
+  };
+  std::vector<Block> blocks;
   size_t bytes = 0;
   template <typename T>
   T* alloc(size_t count) {
-    void* p = nullptr;
     size_t b = count * sizeof(T);
     if (b == 0) b = 16;
-    cudaError_t e = cudaMalloc(&p, b);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      fail(OK_ERR_NOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    void* p = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(g_pool.mu);
+      auto it = g_pool.blocks.find({dev, b});
+      if (it != g_pool.blocks.end()) {
+        p = it->second;
+        g_pool.blocks.erase(it);
+      }
     }
-    ptrs.push_back(p);
+    if (!p) {
+      cudaError_t e = cudaMalloc(&p, b);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(OK_ERR_NOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+      }
+    }
+    blocks.push_back({p, b, dev});
     bytes += b;
     return (T*)p;
   }
   void release() {
-    for (void* p : ptrs) cudaFree(p);
-    ptrs.clear();
+    std::lock_guard<std::mutex> lk(g_pool.mu);
+    for (const Block& k : blocks) {
+      if (g_pool.users > 0) {
+        g_pool.blocks.insert({{k.device, k.bytes}, k.p});
+      } else {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != k.device) cudaSetDevice(k.device);
+        cudaFree(k.p);
+        if (cur != k.device) cudaSetDevice(cur);
+      }
+    }
+    blocks.clear();
     bytes = 0;
   }
   ~Arena() { release(); }
@@ -497,6 +558,8 @@ namespace {
 // ---------------------------------------------------------------------------
 std::mutex g_tune_mu;
 std::map<std::array<int, 5>, int> g_tune;   // (device, dim, n, sizeof(T), 0) -> choice
+std::mutex g_tune_run_mu;                   // one tuning at a time: concurrent setups of one
+                                            // shape then find the first one's choices
 
 template <typename F>
 float time_launches(F&& launch, int reps) {
@@ -522,6 +585,7 @@ void autotune(ok_grid* G, Prec<T>& P) {
   const int nl = (int)P.lv.size();
   P.pshape.assign(nl, G->o.tile_fine >= 4 ? G->o.tile_fine - 4 : 0);   // 3D: 4 + k forces shape k
   if (G->o.tile_fine != 1) return;
+  std::lock_guard<std::mutex> run(g_tune_run_mu);
   auto cached = [&](int n, int& out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find({G->device, G->dim, n, (int)sizeof(T), 0});
@@ -2484,19 +2548,43 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
     g_last_error = "no CUDA device";
     return OK_ERR_CUDA;
   }
+  PoolScope pool;
   const auto t0 = std::chrono::steady_clock::now();
   auto now = [&] { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return reqs[a].arrival < reqs[b].arrival; });
+
+  // One group per (dim, n, options): its own host thread and stream run the
+  // group's admitted requests in cohorts, a timestep at a time; a request
+  // joins at the next timestep after its setup and leaves after its last.
+  struct Group {
+    std::deque<int> ready;            // set up, waiting to join
+    std::vector<int> active;          // stepping
+    std::thread th;
+  };
   std::mutex mu;
   std::condition_variable cv;
-  int inflight = 0, peak_inflight = 0;
+  bool closing = false;
+  int inflight = 0, peak_inflight = 0, peak_cohort = 0, cohort_steps = 0;
   long long bytes = 0, peak_bytes = 0;
-  std::vector<std::thread> workers;
-  workers.reserve(count);
-  // returns a request's slot and bytes (outlives every worker: they are joined below)
-  auto release = [&](ok_serve_request& q) {
+  std::map<std::string, std::unique_ptr<Group>> groups;
+  std::vector<ok_grid*> grid(count, nullptr);
+  std::vector<int> steps_done(count, 0);
+  std::vector<ok_opts> opts(count);
+  std::vector<std::thread> setups;
+  setups.reserve(count);
+
+  auto finish = [&](int i, int status) {             // request i leaves: handle freed, slot released
+    ok_serve_request& q = reqs[i];
+    if (status != OK_SUCCESS && q.message[0] == 0) {
+      std::strncpy(q.message, ok_last_error(), sizeof(q.message) - 1);
+      q.message[sizeof(q.message) - 1] = 0;
+    }
+    if (grid[i]) ok_grid_destroy(grid[i]);
+    grid[i] = nullptr;
+    q.status = status;
+    q.t_done = now();
     {
       std::lock_guard<std::mutex> lk(mu);
       --inflight;
@@ -2504,15 +2592,79 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
     }
     cv.notify_all();
   };
+
+  auto group_loop = [&](Group* G) {
+    cudaSetDevice(device);
+    cudaStream_t gs = nullptr;
+    if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess) gs = nullptr;
+    while (true) {
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return !G->ready.empty() || !G->active.empty() || closing; });
+        // members join while the cohort has room and shares launches with them
+        for (auto it = G->ready.begin(); it != G->ready.end() && (int)G->active.size() < BATCH_MAX;) {
+          if (G->active.empty() || cohort_compatible(grid[G->active[0]], grid[*it])) {
+            G->active.push_back(*it);
+            it = G->ready.erase(it);
+          } else {
+            ++it;
+          }
+        }
+        if (G->active.empty() && G->ready.empty() && closing) break;
+        if (G->active.empty()) continue;
+      }
+      std::vector<int> act = G->active;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        peak_cohort = std::max(peak_cohort, (int)act.size());
+        if (act.size() > 1) ++cohort_steps;
+      }
+      std::vector<int> status(act.size(), OK_SUCCESS);
+      std::vector<ok_step_info> si(act.size());
+      if (!gs) {
+        for (size_t k = 0; k < act.size(); ++k) status[k] = OK_ERR_CUDA;
+      } else if (act.size() == 1) {
+        status[0] = ok_timestep(grid[act[0]], reqs[act[0]].u, reqs[act[0]].w, &si[0], (ok_stream)gs);
+      } else {
+        std::vector<ok_grid*> Gs;
+        std::vector<double*> u, w;
+        for (int i : act) Gs.push_back(grid[i]), u.push_back(reqs[i].u), w.push_back(reqs[i].w);
+        const int st = guarded([&] {
+          CohortStreams swap(Gs, gs);
+          timestep_b(Gs, u.data(), w.data(), si, status, gs);
+        });
+        if (st != OK_SUCCESS)
+          for (auto& x : status)
+            if (x == OK_SUCCESS) x = st;
+      }
+      std::vector<int> keep;
+      for (size_t k = 0; k < act.size(); ++k) {
+        const int i = act[k];
+        reqs[i].newton_its += si[k].newton_its;
+        reqs[i].gmres_its += si[k].gmres_its;
+        if (status[k] != OK_SUCCESS) {
+          finish(i, status[k]);
+        } else if (++steps_done[i] >= reqs[i].steps) {
+          finish(i, OK_SUCCESS);
+        } else {
+          keep.push_back(i);
+        }
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      G->active = keep;
+    }
+    if (gs) cudaStreamDestroy(gs);
+  };
+
   for (int i : order) {
     ok_serve_request& r = reqs[i];
     r.status = OK_SUCCESS;
     r.newton_its = r.gmres_its = 0;
     r.t_admit = r.t_done = 0.0;
     r.message[0] = 0;
-    ok_opts o;
-    ok_default_opts(&o);
-    if (r.opts) o = *r.opts;
+    ok_default_opts(&opts[i]);
+    if (r.opts) opts[i] = *r.opts;
+    const ok_opts& o = opts[i];
     r.device_bytes = 0;
     if (!r.u || !r.w || r.steps < 0 || r.dim < 2 || r.dim > 3 || r.n < 2 || o.restart < 1 ||
         o.restart >= KRYLOV_MAX || o.coarse_max < 1) {
@@ -2535,39 +2687,65 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
       peak_bytes = std::max(peak_bytes, bytes);
     }
     r.t_admit = now();
+    // the group of (dim, n, options): started on first use
+    std::string key(reinterpret_cast<const char*>(&o), sizeof(ok_opts));
+    key += std::to_string(r.dim) + "/" + std::to_string(r.n);
+    Group* G = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto& slot = groups[key];
+      if (!slot) {
+        slot.reset(new Group());
+        try {
+          slot->th = std::thread(group_loop, slot.get());
+        } catch (const std::exception&) {
+          slot.reset();
+        }
+      }
+      G = slot.get();
+    }
+    if (!G) {
+      std::strncpy(r.message, "could not start a group thread", sizeof(r.message) - 1);
+      std::lock_guard<std::mutex> lk(mu);
+      --inflight;
+      bytes -= r.device_bytes;
+      r.status = OK_ERR_NOMEM;
+      r.t_done = now();
+      groups.erase(key);
+      continue;
+    }
     try {
-      workers.emplace_back([&, i, o] {
+      setups.emplace_back([&, i, G] {                   // handle and w0 on the request's own thread
         ok_serve_request& q = reqs[i];
         cudaSetDevice(device);
         cudaStream_t st = nullptr;
-        ok_grid* g = nullptr;
         int status = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? OK_SUCCESS : OK_ERR_CUDA;
-        if (status == OK_SUCCESS) status = ok_grid_create(q.dim, q.n, &q.params, &o, &g);
-        if (status == OK_SUCCESS && q.init_w) status = ok_init_w(g, q.u, q.w, (ok_stream)st);
-        for (int k = 0; status == OK_SUCCESS && k < q.steps; ++k) {
-          ok_step_info si = {};
-          status = ok_timestep(g, q.u, q.w, &si, (ok_stream)st);
-          q.newton_its += si.newton_its;
-          q.gmres_its += si.gmres_its;
-        }
-        if (status != OK_SUCCESS) {
-          std::strncpy(q.message, ok_last_error(), sizeof(q.message) - 1);
-          q.message[sizeof(q.message) - 1] = 0;
-        }
-        if (g) ok_grid_destroy(g);
+        if (status == OK_SUCCESS) status = ok_grid_create(q.dim, q.n, &q.params, &opts[i], &grid[i]);
+        if (status == OK_SUCCESS && q.init_w) status = ok_init_w(grid[i], q.u, q.w, (ok_stream)st);
         if (st) cudaStreamDestroy(st);
-        q.status = status;
-        q.t_done = now();
-        release(q);
+        if (status != OK_SUCCESS || q.steps == 0) {
+          finish(i, status);
+          return;
+        }
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          G->ready.push_back(i);
+        }
+        cv.notify_all();
       });
-    } catch (const std::exception&) {                // no thread: the request fails, nothing leaks
-      r.status = OK_ERR_NOMEM;
-      std::strncpy(r.message, "could not start a worker thread", sizeof(r.message) - 1);
-      r.t_done = now();
-      release(r);
+    } catch (const std::exception&) {
+      std::strncpy(r.message, "could not start a setup thread", sizeof(r.message) - 1);
+      finish(i, OK_ERR_NOMEM);
     }
   }
-  for (auto& t : workers) t.join();
+  for (auto& t : setups) t.join();
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    closing = true;
+  }
+  cv.notify_all();
+  for (auto& kv : groups)
+    if (kv.second && kv.second->th.joinable()) kv.second->th.join();
   int done = 0, failed = 0;
   for (int i = 0; i < count; ++i) (reqs[i].status == OK_SUCCESS ? done : failed) += 1;
   if (info) {
@@ -2576,6 +2754,8 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
     info->peak_inflight = peak_inflight;
     info->peak_bytes = peak_bytes;
     info->seconds = now();
+    info->peak_cohort = peak_cohort;
+    info->cohort_steps = cohort_steps;
   }
   for (int i = 0; i < count; ++i)
     if (reqs[i].status != OK_SUCCESS) {

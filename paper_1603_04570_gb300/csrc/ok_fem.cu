@@ -485,11 +485,17 @@ __device__ __forceinline__ void apply_j_body(const Geom& g, int kz, const double
   double z1[Tp::NOFF], z2[Tp::NOFF];
   load_nb_d<D, TZ>(z, g, v, z1);
   load_nb_d<D, TZ>(z + g.nv, g, v, z2);
-  double y1 = jc.a11hd * dot_w<D, Tp::NOFF>(sWM, v.cls, z1) + jc.dthhk * dot_w<D, Tp::NAX>(sWK, v.cls, z2);
-  double y2 = jc.hd * dot_w<D, Tp::NOFF>(sWM, v.cls, z2) + capply_from<D, double>(g, v, coef, z1);
+  // every product that feeds a sum is an explicit fma, so each kernel that
+  // inlines this body (one problem or a batch) rounds the same way
+  const double mz1 = dot_w<D, Tp::NOFF>(sWM, v.cls, z1);
+  const double kz2 = dot_w<D, Tp::NAX>(sWK, v.cls, z2);
+  const double mz2 = dot_w<D, Tp::NOFF>(sWM, v.cls, z2);
+  const double cz1 = capply_from<D, double>(g, v, coef, z1);
+  double y1 = fma(jc.a11hd, mz1, jc.dthhk * kz2);
+  double y2 = fma(jc.hd, mz2, cz1);
   if (y0) {
-    y1 = jc.beta * y0[v.idx] + jc.alpha * y1;
-    y2 = jc.beta * y0[v.idx + g.nv] + jc.alpha * y2;
+    y1 = fma(jc.beta, y0[v.idx], jc.alpha * y1);
+    y2 = fma(jc.beta, y0[v.idx + g.nv], jc.alpha * y2);
   }
   y[v.idx] = y1;
   y[v.idx + g.nv] = y2;
@@ -520,7 +526,7 @@ __global__ void __launch_bounds__(128) k_cstep(Geom g, const T* __restrict__ coe
   Vtx<D> v;
   if (!vertex_of_thread<D>(g, v)) return;
   T cy = capply_at<D, T>(g, v, coef, y1, yscale);
-  t[v.idx] = (T)v2[v.idx] * vscale - cy;
+  t[v.idx] = fma((T)v2[v.idx], vscale, -cy);
 }
 template <int D, typename T, typename TV>
 __global__ void __launch_bounds__(128) k_cstep_b(Batch<CStepItem<T, TV>> B, Geom g) {
@@ -529,7 +535,7 @@ __global__ void __launch_bounds__(128) k_cstep_b(Batch<CStepItem<T, TV>> B, Geom
   Vtx<D> v;
   if (!vertex_of_thread_at<D>(g, batch_plane<D>(g), v)) return;
   T cy = capply_at<D, T>(g, v, a.coef, a.y1, a.yscale);
-  a.t[v.idx] = (T)a.v2[v.idx] * a.vscale - cy;
+  a.t[v.idx] = fma((T)a.v2[v.idx], a.vscale, -cy);
 }
 
 // Richardson residual for k_R = 2:  out = t - (M y - C a)   (S y = M y - C A~^{-1} B y)

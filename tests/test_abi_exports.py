@@ -93,7 +93,8 @@ def test_status_codes_match_the_header():
 def test_serving_structs_match_the_header():
     assert ctypes.sizeof(ok.ServeRequest) == 224 and ok.ServeRequest.arrival.offset == 80
     assert ok.ServeRequest.device_bytes.offset == 120
-    assert ctypes.sizeof(ok.ServeInfo) == 32 and ok.ServeInfo.seconds.offset == 24
+    assert ctypes.sizeof(ok.ServeInfo) == 40 and ok.ServeInfo.seconds.offset == 24
+    assert ok.ServeInfo.peak_cohort.offset == 32 and ok.ServeInfo.cohort_steps.offset == 36
 
 
 def test_serve_rejects_invalid_arguments_on_host():

@@ -491,6 +491,28 @@ def test_serving_results_are_the_same_alone_and_in_the_mix():
         assert r.status == 0 and r.newton_its >= r.steps and r.t_done >= r.t_admit >= 0.0
 
 
+def test_serving_cohorts_match_alone():
+    """Requests of the same grids with different parameters, arriving
+    together: ok_serve advances each grid's requests as cohorts (shared
+    launches); every result is bitwise the one the request gets alone."""
+    rng = np.random.default_rng(5)
+    mix = []
+    for k in range(8):
+        dim, n = ((2, 40) if k % 2 else (3, 12))
+        eps = 0.02 + 0.02 * rng.uniform()
+        nv = (n + 1) ** dim
+        m = -0.2 + 0.4 * rng.uniform()
+        mix.append(dict(dim=dim, n=n, eps=eps, sigma=10.0 ** (1 + 2 * rng.uniform()), m=m, theta=0.5 + 0.5 * (k % 3 == 0),
+                        dt=0.25 * eps * eps, steps=2 + k % 3, init_w=True, arrival=0.0,
+                        u0=m + 0.01 * rng.uniform(-1, 1, nv), opts=dict(precision=ok.OK_MIXED, gmres_rtol=1e-8)))
+    alone = [_serve([r], 1, 1 << 34)[0][0] for r in mix]
+    mixed, res, info = _serve(mix, 8, 1 << 34)
+    assert info.completed == len(mix) and info.failed == 0
+    assert info.peak_cohort >= 2 and info.cohort_steps >= 1
+    for k, ((ua, wa), (um, wm)) in enumerate(zip(alone, mixed)):
+        assert np.array_equal(ua, um) and np.array_equal(wa, wm), k
+
+
 def test_serving_admits_by_memory_budget():
     """Three requests of one footprint under a budget of one footprint run one
     at a time; all finish; a request larger than the budget is refused."""
