@@ -1453,9 +1453,11 @@ struct CohortPrec {
   }
 
   // ---- per-level steps (3D, or untiled): Prec::cheb with shared launches ---
+  // (the output scale is per member: the mass solve divides by each member's
+  // own 1 + dt theta sigma)
   template <typename TB, typename TO>
-  void cheb(int l, bool mass, const TB* const* b, bool x_zero, int steps, TO* const* out, T oscale, bool want_r,
-            cudaStream_t s) {
+  void cheb(int l, bool mass, const TB* const* b, bool x_zero, int steps, TO* const* out, const T* oscale,
+            bool want_r, cudaStream_t s) {
     Prec<T>& P0 = p0();
     const int nb = B();
     const Geom& g = P0.lv[l].g;
@@ -1512,14 +1514,14 @@ struct CohortPrec {
         T* d[2] = {D0(i), D1(i)};
         it[i] = {};
         it[i].g = g, it[i].W = W(i), it[i].s = d[cur], it[i].x = X(i), it[i].r = R(i), it[i].first = first ? 1 : 0;
-        it[i].out = (T*)out[i], it[i].oscale = oscale;
+        it[i].out = (T*)out[i], it[i].oscale = oscale[i];
       }
       launch_plane3_b<T, T, T>(PM_LAST, it, nb, shape, s);
     } else {
       ChebLastItem<T, TO> it[BATCH_MAX];
       for (int i = 0; i < nb; ++i) {
         T* d[2] = {D0(i), D1(i)};
-        it[i] = {W(i), X(i), want_r ? R(i) : (T*)nullptr, d[cur], first ? 1 : 0, out[i], oscale};
+        it[i] = {W(i), X(i), want_r ? R(i) : (T*)nullptr, d[cur], first ? 1 : 0, out[i], oscale[i]};
       }
       launch_cheb_last_b<T, TO>(dim, g, it, nb, s);
     }
@@ -1552,8 +1554,9 @@ struct CohortPrec {
     }
     T* none[BATCH_MAX] = {};
     T* bl[BATCH_MAX];
-    for (int i = 0; i < nb; ++i) bl[i] = P[i]->lv[l].b;
-    cheb<T, T>(l, false, bl, x_zero, P0.nu_pre, none, (T)1, true, s);
+    T ones[BATCH_MAX];
+    for (int i = 0; i < nb; ++i) bl[i] = P[i]->lv[l].b, ones[i] = (T)1;
+    cheb<T, T>(l, false, bl, x_zero, P0.nu_pre, none, ones, true, s);
     const Geom& gf = P0.lv[l].g;
     const Geom& gc = P0.lv[l + 1].g;
     TransferItem<T> tr[BATCH_MAX];
@@ -1562,7 +1565,7 @@ struct CohortPrec {
     vcycle<T>(l + 1, true, none, s);
     for (int i = 0; i < nb; ++i) tr[i] = {P[i]->lv[l].x, P[i]->lv[l + 1].x};
     launch_prolong_add_b<T>(dim, gf, gc, tr, nb, s);
-    cheb<T, TO>(l, false, bl, false, P0.nu_post, out, (T)1, false, s);
+    cheb<T, TO>(l, false, bl, false, P0.nu_post, out, ones, false, s);
   }
   template <typename TO>
   void mg_solve(TO* const* out, cudaStream_t s) {
@@ -1599,7 +1602,9 @@ struct CohortPrec {
       return;
     }
     const Geom& g = P0.lv[0].g;
-    cheb<double, TZ>(0, true, v, true, P0.q_A, z, (T)P0.inv_a11, false, s);         // z1 = A~^{-1} r1
+    T ia[BATCH_MAX];
+    for (int i = 0; i < nb; ++i) ia[i] = (T)P[i]->inv_a11;
+    cheb<double, TZ>(0, true, v, true, P0.q_A, z, ia, false, s);                    // z1 = A~^{-1} r1
     CStepItem<T, double> cs[BATCH_MAX];
     for (int i = 0; i < nb; ++i) cs[i] = {P[i]->coef, v[i] + nv, (T)1, P[i]->cx, (T)P[i]->inv_a11, P[i]->lv[0].b};
     launch_cstep_b<T, double>(dim, g, cs, nb, s);                     // t = r2 - C z1

@@ -56,16 +56,22 @@ const double* ks_nsteps_ptr(const KrylovState* ks) { return &ks->nsteps; }
 static constexpr int RT = 256;    // threads per reduction block
 static constexpr int KC = 16;     // vectors per multi-dot launch (register budget)
 
-static int g_blocks = 0;
+// reduction grid per device (4 blocks per SM), looked up once per device
+static constexpr int KB_MAX_DEVICES = 64;
+static std::atomic<int> g_blocks[KB_MAX_DEVICES];
 int krylov_blocks() {
-  if (g_blocks == 0) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= KB_MAX_DEVICES) dev = 0;
+  int b = g_blocks[dev].load(std::memory_order_relaxed);
+  if (b == 0) {
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g_blocks = sms > 0 ? 4 * sms : 512;
-    if (g_blocks > RED_MAX_BLOCKS) g_blocks = RED_MAX_BLOCKS;
+    b = sms > 0 ? 4 * sms : 512;
+    if (b > RED_MAX_BLOCKS) b = RED_MAX_BLOCKS;
+    g_blocks[dev].store(b, std::memory_order_relaxed);
   }
-  return g_blocks;
+  return b;
 }
 
 // Reduce acc[0..K) over the block into partials[blockIdx.x * KRYLOV_MAX + k].

@@ -656,7 +656,8 @@ def _cohort_requests(dim, n, count, precision, seed):
 
 
 @pytest.mark.parametrize("dim,n,precision", [(2, 64, ok.OK_MIXED), (2, 100, ok.OK_FP64), (3, 24, ok.OK_MIXED),
-                                             (3, 32, ok.OK_FP64), (2, 48, ok.OK_MIXED_HALF)])
+                                             (3, 32, ok.OK_FP64), (2, 48, ok.OK_MIXED_HALF), (3, 12, ok.OK_MIXED),
+                                             (2, 40, ok.OK_MIXED)])
 def test_batch_cohort_is_bitwise_the_solo_result(dim, n, precision):
     """ok_solve_batch on requests of one grid with different parameters, states
     and step counts: they run as one cohort (every Arnoldi step's kernels one

@@ -5,7 +5,8 @@ budget, or no room for cudaMalloc's synchronisation on a hot loop).
 It runs the same kernels as ok_apply_jacobian with the coefficient store in a
 static device array, so it must give the same y = J(u_k) z as the handle-based
 entry point, on two calls in a row (the second call overwrites the store the
-first one left behind).  Collected last on purpose: it shares nothing with the
+first one left behind), and the first call's y must match the oracle's
+assembled Jacobian row by row.  Collected last on purpose: it shares nothing with the
 other tests and passes alone in a fresh process as well as after them."""
 import ctypes
 
@@ -44,6 +45,12 @@ def test_noalloc_jacobian_matches_handle_path_twice(dim, n):
             a, b = y.cpu().numpy(), y_ref.cpu().numpy()
             scale = np.abs(b).max()
             assert np.abs(a - b).max() <= 1e-13 * scale, call
+            if call == 0 and nv <= 30000:             # and against the oracle's assembled J (eqn newton)
+                from oracle.fem import Mesh, Params, System
+                sysm = System(Mesh(dim, n), Params(p.eps, p.sigma, p.m, p.theta, p.dt))
+                J = sysm.jacobian(u.cpu().numpy())
+                zh = z.cpu().numpy()
+                assert (np.abs(a - J @ zh) <= 1e-13 * (abs(J) @ np.abs(zh))).all()
 
 
 def test_noalloc_rejects_oversize_and_host_arrays():
