@@ -365,8 +365,11 @@ int ok_apply_jacobian_noalloc(int dim, int n, const ok_params* p, const double* 
 /* Choices of the autotuner (no counterpart in the paper).  With
  * tile_fine = 1, ok_grid_create times the compiled kernel shapes of each
  * multigrid level once per (device, dim, n, precision) in the process and
- * keeps the fastest: in 2D the register-strip window width (32 or 64
- * columns) of every tiled level, in 3D the block shape of the z-marching
+ * keeps the fastest: in 2D the register-strip window shape of every tiled
+ * level (float: 0: 32 x 32 vertices in 2-row strips per thread, 1: 64 x 32 in
+ * 8-row strips, 2: 64 x 32 in 4-row, 3: 64 x 64 in 4-row, 4: 128 x 32 in
+ * 4-row; float64: 0: 32 x 16 by 2, 1: 64 x 32 by 2, 2: 64 x 32 by 4,
+ * 3: 32 x 32 by 4, 4: 64 x 16 by 2), in 3D the block shape of the z-marching
  * stencil kernels (0: 32 x 8 columns by 16 planes, 1: 32 x 4 by 32, 2: 64 x 4
  * by 16, 3: 32 x 8 by 32).  All choices give the same bits.  Writes up to
  * `max` (level cells per side, choice) pairs, finest level first, into the

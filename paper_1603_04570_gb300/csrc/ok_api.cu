@@ -597,7 +597,7 @@ void autotune(ok_grid* G, Prec<T>& P) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[{G->device, G->dim, n, (int)sizeof(T), 0}] = v;
   };
-  if (P.tiled) {                                   // 2D: window width 32 or 64 per tiled level
+  if (P.tiled) {                                   // 2D: strip window shape per tiled level
     const int top = P.fused ? P.Lc : nl - 1;
     for (int l = 0; l < top && l + 1 < nl; ++l) {
       Level<T>& L = P.lv[l];
@@ -609,15 +609,15 @@ void autotune(ok_grid* G, Prec<T>& P) {
         for (T* v : fine) CK(cudaMemset(v, 0, L.g.nv * sizeof(T)));
         for (T* v : coarse) CK(cudaMemset(v, 0, C.g.nv * sizeof(T)));
         float tbest = 0.f;
-        const int widths[] = {32, 64};
-        for (int w : widths) {
+        best = -1;
+        for (int w = 0; w < STRIP_SHAPES; ++w) {
           TileSmooth<T> ts = P.ts[l];
           ts.tile = w;
           const float t = time_launches([&] {
             launch_tile_pre<T>(ts, (const T*)nullptr, L.b, L.xa, C.b, 0);
             launch_tile_post<T, T>(ts, L.xa, C.x, L.b, L.x, (T*)nullptr, (T*)nullptr, (T)1, 0);
           }, 5);
-          if (best == 0 || t < tbest) best = w, tbest = t;
+          if (best < 0 || t < tbest) best = w, tbest = t;
         }
         store(L.n, best);
       }
@@ -862,7 +862,7 @@ void build_prec(ok_grid* G, Prec<T>& P, const std::vector<int>& sizes, const std
       // measured faster from 513^2 down); tile_fine = 2 or 3 forces 32 or 64
       // on every tiled level
       const int tf = G->o.tile_fine;
-      t.tile = tf == 2 ? 32 : (tf == 3 ? 64 : (t.g.n1 >= 1000 ? 64 : 32));
+      t.tile = tf == 2 ? 0 : (tf == 3 ? 1 : (t.g.n1 >= 1000 ? 1 : 0));   // shape (autotuned when tf == 1)
     }
     TileMass<T>& m = P.tm;
     m.g = P.lv[0].g;

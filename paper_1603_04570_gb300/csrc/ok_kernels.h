@@ -180,13 +180,18 @@ template <typename T>
 cudaError_t prepare_coarse_vcycle(int dim, size_t smem);
 
 // ---- register-strip tile kernels, 2D (ok_tile.cu) ------------------------
+// compiled window shapes of the strip kernels (columns x rows, rows per
+// thread): float 0: 32 x 32 by 2, 1: 64 x 32 by 8, 2: 64 x 32 by 4,
+// 3: 64 x 64 by 4, 4: 128 x 32 by 4; float64 0: 32 x 16 by 2, 1: 64 x 32 by
+// 2, 2: 64 x 32 by 4, 3: 32 x 32 by 4, 4: 64 x 16 by 2
+constexpr int STRIP_SHAPES = 5;
 template <typename T> struct TileSmooth {
   Geom g, gc;             // this level and the next coarser one
   const T* W;             // S_hat table of this level
   const T* dinv;
   const T* WM;            // M table of this level (post kernel's optional M x)
   T inv_th, c1, c2;       // smoother: 1/centre, coefficients of the middle step
-  int tile;               // window width: 64 (large levels) or 32 columns
+  int tile;               // window shape (0 .. STRIP_SHAPES-1)
 };
 template <typename T> struct TileMass {
   Geom g;

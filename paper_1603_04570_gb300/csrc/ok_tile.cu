@@ -69,6 +69,10 @@ template <typename T> struct StripCfg;
 template <> struct StripCfg<float> {
   template <int H> using Big = SG<OK_STRIP_F_BIG, H>;
   template <int H> using Small = SG<OK_STRIP_F_SMALL, H>;
+  // further shapes the autotuner may pick per level (shape ids 2, 3, 4)
+  template <int H> using S2 = SG<64, 4, 8, H>;
+  template <int H> using S3 = SG<64, 4, 16, H>;
+  template <int H> using S4 = SG<128, 4, 8, H>;
   using Mass = SG<OK_STRIP_F_MASS, QSPLIT>;
   template <int H> using Low = SG<64, 4, 16, H>;       // one window per block of the cluster kernel
 };
@@ -84,6 +88,9 @@ template <> struct StripCfg<float> {
 template <> struct StripCfg<double> {
   template <int H> using Big = SG<OK_STRIP_D_BIG, H>;
   template <int H> using Small = SG<OK_STRIP_D_SMALL, H>;
+  template <int H> using S2 = SG<64, 4, 8, H>;
+  template <int H> using S3 = SG<32, 4, 8, H>;
+  template <int H> using S4 = SG<64, 2, 8, H>;
   using Mass = SG<OK_STRIP_D_MASS, QSPLIT>;
   template <int H> using Low = SG<64, 2, 16, H>;
 };
@@ -742,27 +749,34 @@ static inline size_t strip_smem(bool with_m) {
   return (2 * (size_t)G::SB + NTAB + Topo<2>::NCLASS + (with_m ? NTAB : 0)) * sizeof(T);
 }
 
+// window shape `shape` (0: Small, 1: Big, 2..4: S2..S4) with halo H
+template <typename T, int H, typename F>
+static void with_shape(int shape, F&& f) {
+  using C = StripCfg<T>;
+  switch (shape) {
+    case 1: f(typename C::template Big<H>{}); break;
+    case 2: f(typename C::template S2<H>{}); break;
+    case 3: f(typename C::template S3<H>{}); break;
+    case 4: f(typename C::template S4<H>{}); break;
+    default: f(typename C::template Small<H>{});
+  }
+}
+
 template <typename T>
 void launch_tile_pre(const TileSmooth<T>& a, const T* x_in, const T* b, T* x_out, T* bc, cudaStream_t s) {
-  using Big = typename StripCfg<T>::template Big<4>;
-  using Small = typename StripCfg<T>::template Small<4>;
-  if (a.tile == 64)
-    launch_k(k_strip_pre<T, Big>, strip_grid<Big>(a.g), Big::NT, strip_smem<Big, T>(false), s, a, x_in, b, x_out, bc);
-  else
-    launch_k(k_strip_pre<T, Small>, strip_grid<Small>(a.g), Small::NT, strip_smem<Small, T>(false), s, a, x_in, b,
-             x_out, bc);
+  with_shape<T, 4>(a.tile, [&](auto G) {
+    using GG = decltype(G);
+    launch_k(k_strip_pre<T, GG>, strip_grid<GG>(a.g), GG::NT, strip_smem<GG, T>(false), s, a, x_in, b, x_out, bc);
+  });
 }
 template <typename T, typename TO>
 void launch_tile_post(const TileSmooth<T>& a, const T* x_in, const T* xc, const T* b, T* x_out, T* mx_out, TO* out,
                       T oscale, cudaStream_t s) {
-  using Big = typename StripCfg<T>::template Big<3>;
-  using Small = typename StripCfg<T>::template Small<3>;
-  if (a.tile == 64)
-    launch_k(k_strip_post<T, TO, Big>, strip_grid<Big>(a.g), Big::NT, strip_smem<Big, T>(true), s, a, x_in, xc, b,
+  with_shape<T, 3>(a.tile, [&](auto G) {
+    using GG = decltype(G);
+    launch_k(k_strip_post<T, TO, GG>, strip_grid<GG>(a.g), GG::NT, strip_smem<GG, T>(true), s, a, x_in, xc, b,
              x_out, mx_out, out, oscale);
-  else
-    launch_k(k_strip_post<T, TO, Small>, strip_grid<Small>(a.g), Small::NT, strip_smem<Small, T>(true), s, a, x_in,
-             xc, b, x_out, mx_out, out, oscale);
+  });
 }
 template <typename T, typename TZ>
 void launch_tile_amass(const TileMass<T>& a, const double* v, TZ* z1, T* t_out, cudaStream_t s) {
@@ -775,37 +789,27 @@ void launch_tile_amass(const TileMass<T>& a, const double* v, TZ* z1, T* t_out, 
 
 template <typename T>
 void launch_tile_pre_b(const StripPreItem<T>* items, int count, cudaStream_t s) {
-  using Big = typename StripCfg<T>::template Big<4>;
-  using Small = typename StripCfg<T>::template Small<4>;
   Batch<StripPreItem<T>> B;
   for (int i = 0; i < count; ++i) B.a[i] = items[i];
   const TileSmooth<T>& a = items[0].a;
-  if (a.tile == 64) {
-    dim3 gr = strip_grid<Big>(a.g);
+  with_shape<T, 4>(a.tile, [&](auto G) {
+    using GG = decltype(G);
+    dim3 gr = strip_grid<GG>(a.g);
     gr.z = count;
-    launch_k(k_strip_pre_b<T, Big>, gr, Big::NT, strip_smem<Big, T>(false), s, B);
-  } else {
-    dim3 gr = strip_grid<Small>(a.g);
-    gr.z = count;
-    launch_k(k_strip_pre_b<T, Small>, gr, Small::NT, strip_smem<Small, T>(false), s, B);
-  }
+    launch_k(k_strip_pre_b<T, GG>, gr, GG::NT, strip_smem<GG, T>(false), s, B);
+  });
 }
 template <typename T, typename TO>
 void launch_tile_post_b(const StripPostItem<T, TO>* items, int count, cudaStream_t s) {
-  using Big = typename StripCfg<T>::template Big<3>;
-  using Small = typename StripCfg<T>::template Small<3>;
   Batch<StripPostItem<T, TO>> B;
   for (int i = 0; i < count; ++i) B.a[i] = items[i];
   const TileSmooth<T>& a = items[0].a;
-  if (a.tile == 64) {
-    dim3 gr = strip_grid<Big>(a.g);
+  with_shape<T, 3>(a.tile, [&](auto G) {
+    using GG = decltype(G);
+    dim3 gr = strip_grid<GG>(a.g);
     gr.z = count;
-    launch_k(k_strip_post_b<T, TO, Big>, gr, Big::NT, strip_smem<Big, T>(true), s, B);
-  } else {
-    dim3 gr = strip_grid<Small>(a.g);
-    gr.z = count;
-    launch_k(k_strip_post_b<T, TO, Small>, gr, Small::NT, strip_smem<Small, T>(true), s, B);
-  }
+    launch_k(k_strip_post_b<T, TO, GG>, gr, GG::NT, strip_smem<GG, T>(true), s, B);
+  });
 }
 template <typename T, typename TZ>
 void launch_tile_amass_b(const AmassItem<T, TZ>* items, int count, cudaStream_t s) {
@@ -822,50 +826,45 @@ void launch_tile_amass_b(const AmassItem<T, TZ>* items, int count, cudaStream_t 
 template <typename T>
 cudaError_t prepare_tiles(int q) {
   (void)q;
-  using Cfg = StripCfg<T>;
-  using BP = typename Cfg::template Big<4>;
-  using SP = typename Cfg::template Small<4>;
-  using BQ = typename Cfg::template Big<3>;
-  using SQ = typename Cfg::template Small<3>;
-  using MA = typename Cfg::Mass;
+  using MA = typename StripCfg<T>::Mass;
   const cudaFuncAttribute attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_strip_pre<T, BP>, attr, (int)strip_smem<BP, T>(false));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_pre<T, SP>, attr, (int)strip_smem<SP, T>(false));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, float, BQ>, attr, (int)strip_smem<BQ, T>(true));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, double, BQ>, attr, (int)strip_smem<BQ, T>(true));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, float, SQ>, attr, (int)strip_smem<SQ, T>(true));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, double, SQ>, attr, (int)strip_smem<SQ, T>(true));
-  const int ms = (int)strip_smem<MA, T>(false);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, float, MA, 0, QSPLIT, true, false>, attr, ms);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, float, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, double, MA, 0, QSPLIT, true, false>, attr, ms);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, double, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_pre_b<T, BP>, attr, (int)strip_smem<BP, T>(false));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_pre_b<T, SP>, attr, (int)strip_smem<SP, T>(false));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, T, BQ>, attr, (int)strip_smem<BQ, T>(true));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, T, SQ>, attr, (int)strip_smem<SQ, T>(true));
-  if constexpr (std::is_same<T, float>::value) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, float, BQ>, attr, (int)strip_smem<BQ, T>(true));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, float, SQ>, attr, (int)strip_smem<SQ, T>(true));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, __half, BQ>, attr, (int)strip_smem<BQ, T>(true));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post_b<T, __half, SQ>, attr, (int)strip_smem<SQ, T>(true));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass_b<T, float, MA, 0, QSPLIT, true, false>, attr, ms);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_strip_amass_b<T, float, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass_b<T, __half, MA, 0, QSPLIT, true, false>, attr, ms);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_strip_amass_b<T, __half, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
-  } else {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass_b<T, double, MA, 0, QSPLIT, true, false>, attr, ms);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_strip_amass_b<T, double, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
+  cudaError_t e = cudaSuccess;
+  auto set = [&](auto kernel, size_t bytes) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, attr, (int)bytes);
+  };
+  for (int sh = 0; sh < STRIP_SHAPES; ++sh) {
+    with_shape<T, 4>(sh, [&](auto G) {
+      using GG = decltype(G);
+      set(k_strip_pre<T, GG>, strip_smem<GG, T>(false));
+      set(k_strip_pre_b<T, GG>, strip_smem<GG, T>(false));
+    });
+    with_shape<T, 3>(sh, [&](auto G) {
+      using GG = decltype(G);
+      const size_t m = strip_smem<GG, T>(true);
+      set(k_strip_post<T, float, GG>, m);
+      set(k_strip_post<T, double, GG>, m);
+      set(k_strip_post_b<T, T, GG>, m);
+      if constexpr (std::is_same<T, float>::value) {
+        set(k_strip_post<T, __half, GG>, m);
+        set(k_strip_post_b<T, __half, GG>, m);
+      }
+    });
   }
+  const size_t ms = strip_smem<MA, T>(false);
+  set(k_strip_amass<T, float, MA, 0, QSPLIT, true, false>, ms);
+  set(k_strip_amass<T, float, MA, QSPLIT, QTILE - 1, false, true>, ms);
+  set(k_strip_amass<T, double, MA, 0, QSPLIT, true, false>, ms);
+  set(k_strip_amass<T, double, MA, QSPLIT, QTILE - 1, false, true>, ms);
   if constexpr (std::is_same<T, float>::value) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, __half, BQ>, attr, (int)strip_smem<BQ, T>(true));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_post<T, __half, SQ>, attr, (int)strip_smem<SQ, T>(true));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip_amass<T, __half, MA, 0, QSPLIT, true, false>, attr, ms);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_strip_amass<T, __half, MA, QSPLIT, QTILE - 1, false, true>, attr, ms);
+    set(k_strip_amass<T, __half, MA, 0, QSPLIT, true, false>, ms);
+    set(k_strip_amass<T, __half, MA, QSPLIT, QTILE - 1, false, true>, ms);
+    set(k_strip_amass_b<T, float, MA, 0, QSPLIT, true, false>, ms);
+    set(k_strip_amass_b<T, float, MA, QSPLIT, QTILE - 1, false, true>, ms);
+    set(k_strip_amass_b<T, __half, MA, 0, QSPLIT, true, false>, ms);
+    set(k_strip_amass_b<T, __half, MA, QSPLIT, QTILE - 1, false, true>, ms);
+  } else {
+    set(k_strip_amass_b<T, double, MA, 0, QSPLIT, true, false>, ms);
+    set(k_strip_amass_b<T, double, MA, QSPLIT, QTILE - 1, false, true>, ms);
   }
   return e;
 }
@@ -873,9 +872,12 @@ cudaError_t prepare_tiles(int q) {
 // blocks of the pre-smoothing kernel on a level with the large (64) or small (32) window
 template <typename T>
 long long strip_blocks(const Geom& g, int tile) {
-  const dim3 d = tile == 64 ? strip_grid<typename StripCfg<T>::template Big<4>>(g)
-                            : strip_grid<typename StripCfg<T>::template Small<4>>(g);
-  return (long long)d.x * d.y;
+  long long n = 0;
+  with_shape<T, 4>(tile, [&](auto G) {
+    const dim3 d = strip_grid<decltype(G)>(g);
+    n = (long long)d.x * d.y;
+  });
+  return n;
 }
 
 #define OK_TILE_INST(T)                                                                                       \
