@@ -371,7 +371,8 @@ int ok_apply_jacobian_noalloc(int dim, int n, const ok_params* p, const double* 
  * 4-row; float64: 0: 32 x 16 by 2, 1: 64 x 32 by 2, 2: 64 x 32 by 4,
  * 3: 32 x 32 by 4, 4: 64 x 16 by 2), in 3D the block shape of the z-marching
  * stencil kernels (0: 32 x 8 columns by 16 planes, 1: 32 x 4 by 32, 2: 64 x 4
- * by 16, 3: 32 x 8 by 32).  All choices give the same bits.  Writes up to
+ * by 16, 3: 32 x 8 by 32) or 4: one thread per vertex instead.  All choices
+ * give the same bits.  Writes up to
  * `max` (level cells per side, choice) pairs, finest level first, into the
  * HOST arrays level_n and choice, their number into *count (0 when nothing
  * was tuned). */

@@ -383,6 +383,9 @@ template <typename T> struct Prec {
       if (lv[l].g.n == g.n) return l < pshape.size() ? pshape[l] : 0;
     return 0;
   }
+  // the z-marching kernels on level g (shape PLANE_SHAPES: the autotuner found
+  // the one-thread-per-vertex kernels faster there)
+  bool on_planes(const Geom& g) const { return plane3 && plane_shape(g) < PLANE_SHAPES; }
 
   // out = n_V V-cycles from zero on the level-0 system with right-hand side rhs
   void solve_mg(const T* rhs, T* out, cudaStream_t s) {
@@ -399,13 +402,13 @@ template <typename T> struct Prec {
             int steps, double th, const std::vector<double>& c1, const std::vector<double>& c2, TO* out,
             T oscale, bool want_r, cudaStream_t s, int tag = -1) {
     if (x_zero) launch_cheb_init<T, TB>(dim, g, dinv, b, (T)1, r, d0, (T)(1.0 / th), s);
-    else if (plane3) launch_resid_init3<T>(g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s, plane_shape(g));
+    else if (on_planes(g)) launch_resid_init3<T>(g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s, plane_shape(g));
     else launch_resid_init<T>(dim, g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s);
     T* d[2] = {d0, d1};
     int cur = 0;
     for (int k = 0; k + 1 < steps; ++k) {
       if (k == 0 && prof) prof->begin(tag, s);
-      if (plane3)
+      if (on_planes(g))
         launch_cheb_step3<T>(g, W, dinv, x, r, d[cur], d[1 - cur], (T)c1[k], (T)c2[k], x_zero && k == 0, s,
                              plane_shape(g));
       else
@@ -413,13 +416,14 @@ template <typename T> struct Prec {
       if (k == 0 && prof) prof->end(tag, s);
       cur ^= 1;
     }
-    if (plane3 && want_r)
+    if (on_planes(g) && want_r)
       launch_cheb_last3<T, TO>(g, W, x, r, d[cur], x_zero && steps == 1, out, oscale, s, plane_shape(g));
     else launch_cheb_last<T, TO>(dim, g, W, x, want_r ? r : nullptr, d[cur], x_zero && steps == 1, out, oscale, s);
   }
   // y = alpha W x on level g (M x, or dt theta K y for k_R = 2)
   void op(const Geom& g, const T* W, bool axis_only, const T* x, T* y, T alpha, cudaStream_t s) {
-    if (plane3) launch_op_apply3<T, T, T>(g, W, axis_only, x, y, alpha, (const T*)nullptr, (T)0, s, plane_shape(g));
+    if (on_planes(g))
+      launch_op_apply3<T, T, T>(g, W, axis_only, x, y, alpha, (const T*)nullptr, (T)0, s, plane_shape(g));
     else launch_op_apply<T, T, T>(dim, g, W, axis_only, x, y, alpha, (const T*)nullptr, (T)0, s);
   }
 
@@ -637,9 +641,12 @@ void autotune(ok_grid* G, Prec<T>& P) {
         T* vs[] = {L.x, L.r, L.d0, L.d1};
         for (T* v : vs) CK(cudaMemset(v, 0, L.g.nv * sizeof(T)));
         float tbest = 0.f;
-        for (int sh = 0; sh < PLANE_SHAPES; ++sh) {
+        for (int sh = 0; sh <= PLANE_SHAPES; ++sh) {   // the last candidate: one thread per vertex
           const float t = time_launches([&] {
-            launch_cheb_step3<T>(L.g, L.WS, L.dinvS, L.x, L.r, L.d0, L.d1, (T)0.5, (T)0.5, false, 0, sh);
+            if (sh < PLANE_SHAPES)
+              launch_cheb_step3<T>(L.g, L.WS, L.dinvS, L.x, L.r, L.d0, L.d1, (T)0.5, (T)0.5, false, 0, sh);
+            else
+              launch_cheb_step<T>(3, L.g, L.WS, L.dinvS, L.x, L.r, L.d0, L.d1, (T)0.5, (T)0.5, false, 0);
           }, 5);
           if (best < 0 || t < tbest) best = sh, tbest = t;
         }
@@ -1475,7 +1482,7 @@ struct CohortPrec {
       ChebInitItem<T, TB> it[BATCH_MAX];
       for (int i = 0; i < nb; ++i) it[i] = {dinv(i), b[i], (T)1, R(i), D0(i), (T)(1.0 / th)};
       launch_cheb_init_b<T, TB>(dim, g, it, nb, s);
-    } else if (P0.plane3) {
+    } else if (P0.on_planes(g)) {
       PlaneArgs<T, T, T> it[BATCH_MAX];
       for (int i = 0; i < nb; ++i) {
         it[i] = {};
@@ -1490,7 +1497,7 @@ struct CohortPrec {
     int cur = 0;
     for (int k = 0; k + 1 < steps; ++k) {
       const bool first = x_zero && k == 0;
-      if (P0.plane3) {
+      if (P0.on_planes(g)) {
         PlaneArgs<T, T, T> it[BATCH_MAX];
         for (int i = 0; i < nb; ++i) {
           T* d[2] = {D0(i), D1(i)};
@@ -1508,7 +1515,7 @@ struct CohortPrec {
       cur ^= 1;
     }
     const bool first = x_zero && steps == 1;
-    if (P0.plane3 && want_r) {
+    if (P0.on_planes(g) && want_r) {
       PlaneArgs<T, T, T> it[BATCH_MAX];
       for (int i = 0; i < nb; ++i) {
         T* d[2] = {D0(i), D1(i)};
@@ -1610,7 +1617,7 @@ struct CohortPrec {
     launch_cstep_b<T, double>(dim, g, cs, nb, s);                     // t = r2 - C z1
     T* none[BATCH_MAX] = {};
     mg_solve<T>(none, s);                                             // S_hat^{-1} t
-    if (P0.plane3) {                                                  // M .
+    if (P0.on_planes(g)) {                                            // M .
       PlaneArgs<T, T, T> it[BATCH_MAX];
       for (int i = 0; i < nb; ++i) {
         it[i] = {};

@@ -402,7 +402,7 @@ def test_plane_kernels_3d_are_bitwise_identical(n, coarse_max, k_R, precision):
             out.append(host(z))
             if tile == 1:
                 tuned = g.tuning()
-                assert tuned and all(0 <= c < 4 for _, c in tuned) and tuned[0][0] == n
+                assert tuned and all(0 <= c <= 4 for _, c in tuned) and tuned[0][0] == n
     for k in range(1, len(out)):
         assert np.array_equal(out[0], out[k]), k
 
