@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--serving", action="store_true",
                     help="instead of the timed workload: the serving stream (Poisson arrivals) through ok_serve")
     ap.add_argument("--requests", type=int, default=256, help="serving: requests of the stream")
-    ap.add_argument("--max-inflight", type=int, default=8, help="serving: requests in flight at once")
+    ap.add_argument("--max-inflight", type=int, default=32, help="serving: requests in flight at once")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="serving: device memory budget")
     return ap.parse_args()
 

@@ -9,6 +9,12 @@ This module runs the same experiments through the library:
     python -m paper_1603_04570_gb300.experiments table2 [--sizes 100 200 400] [--steps 3]
     python -m paper_1603_04570_gb300.experiments refine2d [--sizes 128 256 512 1024] [--steps 2]
     python -m paper_1603_04570_gb300.experiments spectrum [--workloads 2d_n1024 3d_n128] [--steps 2]
+    python -m paper_1603_04570_gb300.experiments energy [--workloads 2d_n1024 3d_n128] [--steps 5]
+
+`energy` monitors the Ohta--Kawasaki free energy (Sec. 1) along the
+trajectory: its interfacial, double-well and nonlocal terms after each
+timestep (ok_energy), with the mean of u; the equations are the H^{-1}
+gradient flow of that energy, so it decreases while the mean relaxes to m.
 
 `spectrum` estimates eig(J P^{-1}) (Sec. 3: 1 and eig(S~^{-1} S)) at full
 size from the Arnoldi matrix of FGMRES cycles: after each timestep, the Ritz
@@ -131,9 +137,33 @@ def spectrum(names, steps, precision=OK_MIXED, restart=60):
                 yield {**rec, **_ritz_record(g, wl, u, "random_rhs", si.gmres_its)}
 
 
+def energy(names, steps, precision=OK_MIXED):
+    """The energy's three terms after each of `steps` timesteps."""
+    import torch
+    for name in names:
+        wl = oi.WORKLOADS[name]
+        o = dict(restart=wl.restart, gmres_rtol=wl.gmres_rtol, precision=precision,
+                 newton_atol=wl.newton_tols[0], newton_rtol=wl.newton_tols[1])
+        if wl.dim == 2 and wl.n >= 128:
+            o["coarse_max"] = 32
+        with Grid(wl.dim, wl.n, wl.eps, wl.sigma, wl.m, wl.theta, wl.dt, **o) as g:
+            u = torch.from_numpy(oi.initial_u(wl)).cuda()
+            w = torch.empty_like(u)
+            g.init_w(u, w)
+            for step in range(steps + 1):
+                if step:
+                    g.timestep(u, w)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                terms, total = g.energy(u)
+                yield dict(workload=wl.name, dofs=wl.dofs, step=step, t=step * wl.dt, energy=total,
+                           interfacial=terms[0], double_well=terms[1], nonlocal=terms[2],
+                           mean_u=float(u.mean()), energy_ms=1e3 * (time.perf_counter() - t0))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("experiment", choices=["table1", "table2", "refine2d", "spectrum"])
+    ap.add_argument("experiment", choices=["table1", "table2", "refine2d", "spectrum", "energy"])
     ap.add_argument("--workloads", nargs="*", default=None, help="spectrum: 2d_n1024, 3d_n128, paper_3d, ...")
     ap.add_argument("--sizes", type=int, nargs="*", default=None)
     ap.add_argument("--steps", type=int, default=3)
@@ -150,6 +180,8 @@ def main(argv=None):
                       gmres_rtol=a.gmres_rtol)
     elif a.experiment == "spectrum":
         rows = spectrum(a.workloads or ["2d_n1024", "paper_3d"], a.steps, precision=prec)
+    elif a.experiment == "energy":
+        rows = energy(a.workloads or ["2d_n1024", "3d_n128"], a.steps, precision=prec)
     else:
         rows = refine2d(a.sizes or [128, 256, 512, 1024], a.steps, a.k_r or 1, precision=prec,
                         gmres_rtol=a.gmres_rtol)
@@ -157,7 +189,13 @@ def main(argv=None):
     for r in rows:
         out.append(r)
         print(json.dumps(r), flush=True)
-    if a.markdown and a.experiment == "spectrum":
+    if a.markdown and a.experiment == "energy":
+        print("\n| workload | step | t | E | interfacial | double well | nonlocal | mean u | ok_energy ms |")
+        print("|---|---|---|---|---|---|---|---|---|")
+        for r in out:
+            print(f"| {r['workload']} | {r['step']} | {r['t']:.2e} | {r['energy']:.9e} | {r['interfacial']:.6e} | "
+                  f"{r['double_well']:.9e} | {r['nonlocal']:.6e} | {r['mean_u']:.9f} | {r['energy_ms']:.1f} |")
+    elif a.markdown and a.experiment == "spectrum":
         print("\n| workload | step | solve | FGMRES its | Ritz Re min | Ritz Re max | max |Im| | dist to 1 | "
               "Lemma 2 enclosure | outside |")
         print("|---|---|---|---|---|---|---|---|---|---|")

@@ -442,6 +442,10 @@ def test_experiments_module_runs():
     # spectral diagnostics on the 32^2 workload: Ritz values of the Newton solve
     # and of a random right-hand side inside Lemma 2's enclosure (widened for
     # the inexact preconditioner), the eigenvalue 1 found
+    # the energy monitor (Sec. 1): decreasing along the 32^2 workload's implicit steps
+    rows = list(experiments.energy(["2d_n32"], steps=3))
+    assert [r["step"] for r in rows] == [0, 1, 2, 3]
+    assert all(b["energy"] < a["energy"] for a, b in zip(rows, rows[1:]))
     rows = list(experiments.spectrum(["2d_n32"], steps=1))
     assert [r["solve"] for r in rows] == ["newton", "random_rhs"]
     for r in rows:
