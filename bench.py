@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer run (short profiling runs)")
+    ap.add_argument("--tuning-file", default=None,
+                    help="autotuner choices: loaded from this file when it exists, saved to it at the end")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the one-pass Gram--Schmidt, nine-level and 3D runs beside the headline")
     ap.add_argument("--profile-out", default=None, help="write per-kernel samples as JSON")
@@ -472,7 +474,8 @@ def workloads_3d(ok, torch, args, rank, flush):
     r = run_precision(ok, torch, wl, "mixed", 1, 1, rank, True, flush, args.opt)
     ms = sum(r["step_ms"])
     out[wl.name] = {"mixed": {"value": wl.dofs * r["its"] / (ms / 1e3), "ms_per_step": ms, "steps": 1,
-                              "gmres_its": r["its"], "newton_its": r["newton"], "mg_levels": r["g"].levels},
+                              "gmres_its": r["its"], "newton_its": r["newton"], "mg_levels": r["g"].levels,
+                              "tuning": [list(t) for t in r["g"].tuning()]},
                     "roofline": roofline_of(r, wl, "mixed", ms),
                     "kernel_samples": {kk: {"samples": n, "avg_ms": (t / n if n else None)}
                                        for kk, (n, t) in r["prof"].items()}}
@@ -491,6 +494,8 @@ def main_ok(args):
     torch.cuda.set_device(local)
     import paper_1603_04570_gb300 as ok
     ok.load()
+    if args.tuning_file and os.path.exists(args.tuning_file):
+        ok.ok_tuning_load(args.tuning_file)
     wl = oi.WORKLOADS[args.workload]
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     clocks = ClockSampler(local)
@@ -524,6 +529,7 @@ def main_ok(args):
                     "newton_solve_p50_ms": pct(mixed["solve_lat"], 0.5),
                     "newton_solve_p99_ms": pct(mixed["solve_lat"], 0.99)},
         "roofline": roof, "e2e": e2e, "gpu_launches": mixed["launches"], "clocks": clk,
+        "tuning": [list(t) for t in mixed["g"].tuning()],
         "kernel_samples": {k: {"samples": n, "avg_ms": (t / n if n else None)} for k, (n, t) in mixed["prof"].items()},
     }
     if fp64 is not None:
@@ -555,6 +561,8 @@ def main_ok(args):
             out["workloads"] = workloads_3d(ok, torch, args, rank, flush)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
+    if args.tuning_file:
+        ok.ok_tuning_save(args.tuning_file)
     if args.profile_out and rank == 0:
         json.dump(out, open(args.profile_out, "w"), indent=1, default=str)
     if rank == 0:

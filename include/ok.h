@@ -378,6 +378,17 @@ int ok_apply_jacobian_noalloc(int dim, int n, const ok_params* p, const double* 
  * was tuned). */
 int ok_grid_tuning(const ok_grid* g, int* level_n, int* choice, int max, int* count);
 
+/* The autotuner's choices made (or loaded) so far in this process, kept per
+ * (dim, level cells per side, value size): ok_tuning_save writes them to the
+ * text file `path` (one "dim n bytes choice" line each); ok_tuning_load reads
+ * such a file into the process's choices for the current device, so that
+ * later ok_grid_create calls of those shapes use them without timing (a
+ * process under a profiler, whose kernel timings differ, then runs the
+ * kernels a plain run chose).  Host only; OK_ERR_INVALID_ARG for a NULL or
+ * unreadable path or malformed lines. */
+int ok_tuning_save(const char* path);
+int ok_tuning_load(const char* path);
+
 /* The Ohta--Kawasaki free energy (Sec. 1, the functional E[u] whose H^{-1}
  * gradient flow eqns oka/okb are) of the P1 function with nodal values u
  * (N_v, host or device):

@@ -114,6 +114,8 @@ def load(build: bool = True):
         "ok_launch_count": (c_longlong, []),
         "ok_energy": (c_int, [P, P, P, P, P]),
         "ok_grid_tuning": (c_int, [P, POINTER(c_int), POINTER(c_int), c_int, POINTER(c_int)]),
+        "ok_tuning_save": (c_int, [c_char_p]),
+        "ok_tuning_load": (c_int, [c_char_p]),
         "ok_apply_jacobian_noalloc": (c_int, [c_int, c_int, POINTER(Params), P, P, P, P]),
         "ok_arnoldi_hessenberg": (c_int, [P, P, c_int, c_int, POINTER(c_int), P]),
         "ok_ritz_values": (c_int, [P, P, P, c_int, POINTER(c_int), P]),
@@ -328,6 +330,14 @@ def ok_grid_tuning(h):
     n, c, k = (c_int * 64)(), (c_int * 64)(), c_int()
     _check(load().ok_grid_tuning(h, n, c, 64, byref(k)))
     return [(n[i], c[i]) for i in range(k.value)]
+
+
+def ok_tuning_save(path: str):
+    _check(load().ok_tuning_save(os.fsencode(path)))
+
+
+def ok_tuning_load(path: str):
+    _check(load().ok_tuning_load(os.fsencode(path)))
 
 
 def ok_launch_count() -> int:

@@ -2370,6 +2370,60 @@ int ok_ritz_values(ok_grid* G, double* re, double* im, int max, int* count, ok_s
   return OK_SUCCESS;
 }
 
+int ok_tuning_save(const char* path) {
+  if (!path) {
+    g_last_error = "NULL path";
+    return OK_ERR_INVALID_ARG;
+  }
+  FILE* f = std::fopen(path, "w");
+  if (!f) {
+    g_last_error = std::string("cannot write ") + path;
+    return OK_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::fprintf(f, "# ok-gb300 autotuner choices: dim n bytes-per-value choice\n");
+  for (const auto& kv : g_tune) std::fprintf(f, "%d %d %d %d\n", kv.first[1], kv.first[2], kv.first[3], kv.second);
+  std::fclose(f);
+  g_last_error.clear();
+  return OK_SUCCESS;
+}
+
+int ok_tuning_load(const char* path) {
+  if (!path) {
+    g_last_error = "NULL path";
+    return OK_ERR_INVALID_ARG;
+  }
+  FILE* f = std::fopen(path, "r");
+  if (!f) {
+    g_last_error = std::string("cannot read ") + path;
+    return OK_ERR_INVALID_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  char line[256];
+  int bad = 0;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  while (std::fgets(line, sizeof(line), f)) {
+    if (line[0] == '#' || line[0] == '\n') continue;
+    int d = 0, n = 0, b = 0, c = 0;
+    if (std::sscanf(line, "%d %d %d %d", &d, &n, &b, &c) == 4 && (d == 2 || d == 3) && n >= 1 &&
+        (b == 4 || b == 8) && c >= 0 && c <= (d == 2 ? STRIP_SHAPES - 1 : PLANE_SHAPES))
+      g_tune[{dev, d, n, b, 0}] = c;
+    else
+      ++bad;
+  }
+  std::fclose(f);
+  if (bad) {
+    g_last_error = std::to_string(bad) + " malformed line(s) in " + path;
+    return OK_ERR_INVALID_ARG;
+  }
+  g_last_error.clear();
+  return OK_SUCCESS;
+}
+
 int ok_grid_tuning(const ok_grid* G, int* level_n, int* choice, int max, int* count) {
   if (!G || !count || max < 0 || (max > 0 && (!level_n || !choice))) {
     g_last_error = "NULL argument or max < 0";

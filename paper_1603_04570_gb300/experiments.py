@@ -156,9 +156,9 @@ def energy(names, steps, precision=OK_MIXED):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 terms, total = g.energy(u)
-                yield dict(workload=wl.name, dofs=wl.dofs, step=step, t=step * wl.dt, energy=total,
-                           interfacial=terms[0], double_well=terms[1], nonlocal=terms[2],
-                           mean_u=float(u.mean()), energy_ms=1e3 * (time.perf_counter() - t0))
+                yield {"workload": wl.name, "dofs": wl.dofs, "step": step, "t": step * wl.dt, "energy": total,
+                       "interfacial": terms[0], "double_well": terms[1], "nonlocal": terms[2],
+                       "mean_u": float(u.mean()), "energy_ms": 1e3 * (time.perf_counter() - t0)}
 
 
 def main(argv=None):

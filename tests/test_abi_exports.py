@@ -132,3 +132,25 @@ def test_host_diagnostic_wrappers_validate_shapes():
     with pytest.raises(ValueError):
         ok.ok_givens_unrotate(np.zeros((3, 3)), np.zeros(3), np.zeros(3))   # R must be (k+1) x k
     assert ok.ok_givens_unrotate(np.zeros((1, 0)), np.zeros(0), np.zeros(0)).shape == (1, 0)
+
+
+def test_tuning_file_roundtrip(tmp_path):
+    """Autotuner choices written by one process are read back by another
+    (host only): loading a file and saving it again gives the same entries;
+    malformed lines are rejected."""
+    src = tmp_path / "in.txt"
+    src.write_text("# comment\n2 1024 4 1\n2 512 4 0\n3 128 8 4\n")
+    ok.ok_tuning_load(str(src))
+    out = tmp_path / "out.txt"
+    ok.ok_tuning_save(str(out))
+    lines = {l for l in out.read_text().splitlines() if not l.startswith("#")}
+    assert {"2 1024 4 1", "2 512 4 0", "3 128 8 4"} <= lines
+    bad = tmp_path / "bad.txt"
+    bad.write_text("2 64 4 9\n")                     # shape 9 does not exist
+    with pytest.raises(ok.OkError):
+        ok.ok_tuning_load(str(bad))
+
+
+def test_experiment_driver_imports():
+    import paper_1603_04570_gb300.experiments as ex
+    assert callable(ex.energy) and callable(ex.table1)
