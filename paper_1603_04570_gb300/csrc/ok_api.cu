@@ -400,9 +400,14 @@ template <typename T> struct Prec {
   template <typename TB, typename TO>
   void cheb(const Geom& g, const T* W, const T* dinv, const TB* b, bool x_zero, T* x, T* r, T* d0, T* d1,
             int steps, double th, const std::vector<double>& c1, const std::vector<double>& c2, TO* out,
-            T oscale, bool want_r, cudaStream_t s, int tag = -1) {
-    if (x_zero) launch_cheb_init<T, TB>(dim, g, dinv, b, (T)1, r, d0, (T)(1.0 / th), s);
-    else if (on_planes(g)) launch_resid_init3<T>(g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s, plane_shape(g));
+            T oscale, bool want_r, cudaStream_t s, int tag = -1, bool inited = false,
+            const T** defer_last = nullptr) {
+    // inited: the start from zero (r, d0) was written by the restriction
+    // launch; defer_last: the last step (x += d, no residual, no output) is
+    // left to the prolongation that reads x next, which gets d here
+    if (x_zero) {
+      if (!inited) launch_cheb_init<T, TB>(dim, g, dinv, b, (T)1, r, d0, (T)(1.0 / th), s);
+    } else if (on_planes(g)) launch_resid_init3<T>(g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s, plane_shape(g));
     else launch_resid_init<T>(dim, g, W, dinv, (const T*)b, x, r, d0, (T)(1.0 / th), s);
     T* d[2] = {d0, d1};
     int cur = 0;
@@ -416,6 +421,10 @@ template <typename T> struct Prec {
       if (k == 0 && prof) prof->end(tag, s);
       cur ^= 1;
     }
+    if (defer_last && !want_r && out == nullptr && !(x_zero && steps == 1)) {
+      *defer_last = d[cur];
+      return;
+    }
     if (on_planes(g) && want_r)
       launch_cheb_last3<T, TO>(g, W, x, r, d[cur], x_zero && steps == 1, out, oscale, s, plane_shape(g));
     else launch_cheb_last<T, TO>(dim, g, W, x, want_r ? r : nullptr, d[cur], x_zero && steps == 1, out, oscale, s);
@@ -427,8 +436,11 @@ template <typename T> struct Prec {
     else launch_op_apply<T, T, T>(dim, g, W, axis_only, x, y, alpha, (const T*)nullptr, (T)0, s);
   }
 
+  // inited / defer: see cheb (level l's start from zero was written by the
+  // restriction above it; its last post-smoothing step goes to the caller's
+  // prolongation)
   template <typename TO>
-  void vcycle(int l, bool x_zero, TO* out, cudaStream_t s) {
+  void vcycle(int l, bool x_zero, TO* out, cudaStream_t s, bool inited = false, const T** defer = nullptr) {
     Level<T>& L = lv[l];
     const bool coarsest = (l + 1 == (int)lv.size());
     if (fused && l == Lc) {                 // levels Lc..L in one thread block
@@ -442,12 +454,18 @@ template <typename T> struct Prec {
       return;
     }
     cheb<T, T>(L.g, L.WS, L.dinvS, L.b, x_zero, L.x, L.r, L.d0, L.d1, nu_pre, thS, cS1, cS2, (T*)nullptr,
-               (T)1, true, s, l == 0 ? PT_SMOOTH0 : -1);
+               (T)1, true, s, l == 0 ? PT_SMOOTH0 : -1, inited);
     Level<T>& C = lv[l + 1];
-    launch_restrict<T>(dim, L.g, C.g, L.r, C.b, s);
-    vcycle<T>(l + 1, true, (T*)nullptr, s);
-    launch_prolong_add<T>(dim, L.g, C.g, L.x, C.x, s);
-    cheb<T, TO>(L.g, L.WS, L.dinvS, L.b, false, L.x, L.r, L.d0, L.d1, nu_post, thS, cS1, cS2, out, (T)1, false, s);
+    // a coarse level that smooths (neither the fused part nor the coarsest)
+    // starts inside the restriction launch and ends inside the prolongation
+    const bool c_smooths = !(fused && l + 1 == Lc) && l + 2 < (int)lv.size();
+    if (c_smooths) launch_restrict<T>(dim, L.g, C.g, L.r, C.b, s, C.dinvS, C.r, C.d0, (T)(1.0 / thS));
+    else launch_restrict<T>(dim, L.g, C.g, L.r, C.b, s);
+    const T* dc = nullptr;
+    vcycle<T>(l + 1, true, (T*)nullptr, s, c_smooths, c_smooths ? &dc : nullptr);
+    launch_prolong_add<T>(dim, L.g, C.g, L.x, C.x, s, dc);
+    cheb<T, TO>(L.g, L.WS, L.dinvS, L.b, false, L.x, L.r, L.d0, L.d1, nu_post, thS, cS1, cS2, out, (T)1, false, s,
+                -1, false, defer);
   }
 
   // x_0 = S_hat^{-1} b_0 by n_V V-cycles from zero; optional cast to out
@@ -1464,7 +1482,7 @@ struct CohortPrec {
   // own 1 + dt theta sigma)
   template <typename TB, typename TO>
   void cheb(int l, bool mass, const TB* const* b, bool x_zero, int steps, TO* const* out, const T* oscale,
-            bool want_r, cudaStream_t s) {
+            bool want_r, cudaStream_t s, bool inited = false, const T** defer_last = nullptr) {
     Prec<T>& P0 = p0();
     const int nb = B();
     const Geom& g = P0.lv[l].g;
@@ -1478,7 +1496,9 @@ struct CohortPrec {
     auto D0 = [&](int i) { return mass ? P[i]->cd0 : P[i]->lv[l].d0; };
     auto D1 = [&](int i) { return mass ? P[i]->cd1 : P[i]->lv[l].d1; };
     const int shape = P0.plane_shape(g);
-    if (x_zero) {
+    if (x_zero && inited) {
+      // r and d0 written by the restriction launch
+    } else if (x_zero) {
       ChebInitItem<T, TB> it[BATCH_MAX];
       for (int i = 0; i < nb; ++i) it[i] = {dinv(i), b[i], (T)1, R(i), D0(i), (T)(1.0 / th)};
       launch_cheb_init_b<T, TB>(dim, g, it, nb, s);
@@ -1515,6 +1535,15 @@ struct CohortPrec {
       cur ^= 1;
     }
     const bool first = x_zero && steps == 1;
+    bool no_out = true;
+    for (int i = 0; i < nb; ++i) no_out = no_out && out[i] == nullptr;
+    if (defer_last && !want_r && no_out && !first) {
+      for (int i = 0; i < nb; ++i) {
+        T* d[2] = {D0(i), D1(i)};
+        defer_last[i] = d[cur];
+      }
+      return;
+    }
     if (P0.on_planes(g) && want_r) {
       PlaneArgs<T, T, T> it[BATCH_MAX];
       for (int i = 0; i < nb; ++i) {
@@ -1535,7 +1564,7 @@ struct CohortPrec {
   }
 
   template <typename TO>
-  void vcycle(int l, bool x_zero, TO* const* out, cudaStream_t s) {
+  void vcycle(int l, bool x_zero, TO* const* out, cudaStream_t s, bool inited = false, const T** defer = nullptr) {
     Prec<T>& P0 = p0();
     const int nb = B();
     const bool coarsest = l + 1 == (int)P0.lv.size();
@@ -1563,16 +1592,25 @@ struct CohortPrec {
     T* bl[BATCH_MAX];
     T ones[BATCH_MAX];
     for (int i = 0; i < nb; ++i) bl[i] = P[i]->lv[l].b, ones[i] = (T)1;
-    cheb<T, T>(l, false, bl, x_zero, P0.nu_pre, none, ones, true, s);
+    cheb<T, T>(l, false, bl, x_zero, P0.nu_pre, none, ones, true, s, inited);
     const Geom& gf = P0.lv[l].g;
     const Geom& gc = P0.lv[l + 1].g;
+    const bool c_smooths = !(P0.fused && l + 1 == P0.Lc) && l + 2 < (int)P0.lv.size();   // as Prec::vcycle
     TransferItem<T> tr[BATCH_MAX];
-    for (int i = 0; i < nb; ++i) tr[i] = {P[i]->lv[l].r, P[i]->lv[l + 1].b};
+    for (int i = 0; i < nb; ++i) {
+      Level<T>& C = P[i]->lv[l + 1];
+      tr[i] = {P[i]->lv[l].r, C.b};
+      if (c_smooths) tr[i].dinv = C.dinvS, tr[i].r = C.r, tr[i].d = C.d0, tr[i].inv_th = (T)(1.0 / P0.thS);
+    }
     launch_restrict_b<T>(dim, gf, gc, tr, nb, s);
-    vcycle<T>(l + 1, true, none, s);
-    for (int i = 0; i < nb; ++i) tr[i] = {P[i]->lv[l].x, P[i]->lv[l + 1].x};
+    const T* dc[BATCH_MAX] = {};
+    vcycle<T>(l + 1, true, none, s, c_smooths, c_smooths ? dc : nullptr);
+    for (int i = 0; i < nb; ++i) {
+      tr[i] = {P[i]->lv[l].x, P[i]->lv[l + 1].x};
+      tr[i].dc = dc[i];
+    }
     launch_prolong_add_b<T>(dim, gf, gc, tr, nb, s);
-    cheb<T, TO>(l, false, bl, false, P0.nu_post, out, ones, false, s);
+    cheb<T, TO>(l, false, bl, false, P0.nu_post, out, ones, false, s, false, defer);
   }
   template <typename TO>
   void mg_solve(TO* const* out, cudaStream_t s) {

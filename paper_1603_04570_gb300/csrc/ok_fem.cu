@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(128) k_schur_resid(Geom g, const T* __restrict
 // launchers
 // ---------------------------------------------------------------------------
 static inline dim3 grid_of(int dim, const Geom& g, int bx) {
-  return dim3((g.n1 + bx - 1) / bx, g.n1, dim == 3 ? g.n1 : 1);
+  return dim3((unsigned)(((long long)g.n1 * g.n1 + bx - 1) / bx), 1, dim == 3 ? g.n1 : 1);
 }
 
 void launch_residual(int dim, const Geom& g, const double* WM, const double* WK, const ResidualCoefs& rc,

@@ -146,6 +146,7 @@ struct Geom {
   long long nv;    // vertices
   long long sy;    // stride of y
   long long sz;    // stride of z (0 in 2D)
+  unsigned rmul;   // ceil(2^32 / n1): t / n1 = umulhi(t, rmul) for 0 <= t < n1^2 while n1^3 < 2^32
 };
 
 inline Geom make_geom(int dim, int n) {
@@ -155,6 +156,7 @@ inline Geom make_geom(int dim, int n) {
   g.sy = n + 1;
   g.sz = dim == 3 ? (long long)(n + 1) * (n + 1) : 0;
   g.nv = dim == 3 ? g.sz * (n + 1) : g.sy * (n + 1);
+  g.rmul = (unsigned)((0x100000000ull + (unsigned long long)g.n1 - 1) / (unsigned long long)g.n1);
   return g;
 }
 
@@ -168,13 +170,18 @@ template <int D> struct Vtx {
   int cls;
 };
 
-// thread -> vertex for the launch shape grid(ceil(n1/bx), n1, D==3 ? n1 : 1)
-// (kz: the z-plane; batched launches fold the problem index into blockIdx.z)
+// thread -> vertex for the launch shape grid(ceil(n1^2 / bx), 1, D==3 ? n1 : 1)
+// (kz: the z-plane; batched launches fold the problem index into blockIdx.z).
+// The threads of a block take consecutive vertices of one (x, y) plane, rows
+// back to back, so that no warp idles at the end of a row of 2^k + 1 vertices.
 template <int D>
 __device__ __forceinline__ bool vertex_of_thread_at(const Geom& g, int kz, Vtx<D>& v) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n1) return false;
-  int j = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.n1 * g.n1) return false;
+  // t / n1 by a multiply where that is exact (t n1 < n1^3 < 2^32: the
+  // quotient's error t (rmul n1 - 2^32) / 2^32 n1 stays below 1 / n1)
+  const int j = g.n1 <= 1625 ? (int)__umulhi((unsigned)t, g.rmul) : t / g.n1;
+  const int i = t - j * g.n1;
   int k = D == 3 ? kz : 0;
   v.p[0] = i;
   v.p[1] = j;
@@ -190,7 +197,7 @@ template <int D>
 __device__ __forceinline__ bool vertex_of_thread(const Geom& g, Vtx<D>& v) {
   return vertex_of_thread_at<D>(g, D == 3 ? (int)blockIdx.z : 0, v);
 }
-// batched grid (x, n1, (D == 3 ? n1 : 1) * count): problem index and z-plane
+// batched grid (x, 1, (D == 3 ? n1 : 1) * count): problem index and z-plane
 template <int D>
 __device__ __forceinline__ int batch_problem(const Geom& g) {
   return D == 3 ? (int)blockIdx.z / g.n1 : (int)blockIdx.z;

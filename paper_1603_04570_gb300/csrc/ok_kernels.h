@@ -90,12 +90,16 @@ void launch_cheb_step(int dim, const Geom& g, const T* W, const T* dinv, T* x, T
 template <typename T, typename TO>
 void launch_cheb_last(int dim, const Geom& g, const T* W, T* x, T* r, const T* d_in, bool first, TO* out,
                       T oscale, cudaStream_t s);
-// b_c = P^T r_f
+// b_c = P^T r_f; with dinv also r = b_c, d = dinv b_c inv_th on the coarse
+// level (launch_cheb_init from zero, folded into the same launch)
 template <typename T>
-void launch_restrict(int dim, const Geom& gf, const Geom& gc, const T* rf, T* bc, cudaStream_t s);
-// x_f += P x_c
+void launch_restrict(int dim, const Geom& gf, const Geom& gc, const T* rf, T* bc, cudaStream_t s,
+                     const T* dinv = nullptr, T* r = nullptr, T* d = nullptr, T inv_th = (T)0);
+// x_f += P x_c (with dc: x_f += P (x_c + d_c), the coarse level's last
+// smoothing step x_c += d_c folded in)
 template <typename T>
-void launch_prolong_add(int dim, const Geom& gf, const Geom& gc, T* xf, const T* xc, cudaStream_t s);
+void launch_prolong_add(int dim, const Geom& gf, const Geom& gc, T* xf, const T* xc, cudaStream_t s,
+                        const T* dc = nullptr);
 // x = Ainv b on the coarsest level (dense, row stride nc), one thread block
 template <typename T>
 void launch_coarse_solve(long long nc, const T* Ainv, const T* b, T* x, cudaStream_t s);
@@ -293,6 +297,11 @@ template <typename T, typename TO> struct ChebLastItem {
 template <typename T> struct TransferItem {
   T* fine;          // restrict: fine residual (read); prolong: fine iterate (updated)
   T* coarse;        // restrict: coarse right-hand side (written); prolong: coarse correction (read)
+  const T* dinv;    // restrict, optional: also start the coarse smoothing from zero (r, d below)
+  T* r;
+  T* d;
+  T inv_th;
+  const T* dc;      // prolong, optional: the coarse level's last step folded in (P (coarse + dc))
 };
 template <typename T> struct GemvItem {
   const T* A;

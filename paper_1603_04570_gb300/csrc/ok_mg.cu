@@ -28,7 +28,7 @@ namespace okg {
 static constexpr int BX = 128;
 
 static inline dim3 grid_of(int dim, const Geom& g) {
-  return dim3((g.n1 + BX - 1) / BX, g.n1, dim == 3 ? g.n1 : 1);
+  return dim3((unsigned)(((long long)g.n1 * g.n1 + BX - 1) / BX), 1, dim == 3 ? g.n1 : 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -94,20 +94,29 @@ __global__ void __launch_bounds__(BX) k_cheb_last(Geom g, const T* __restrict__ 
   cheb_last_at<D, T, TO>(g, v, sW, x, r, din, first != 0, out, oscale);
 }
 
+// restriction bc = P^T rf; with dinv, also the coarse level's first
+// smoothing start from zero (cheb_init_at on bc: r = bc, d = D^{-1} bc / th),
+// which would otherwise be the next launch
 template <int D, typename T>
-__global__ void __launch_bounds__(BX) k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ bc) {
-  pdl_entry();
+__global__ void __launch_bounds__(BX) k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* bc,
+                                                 const T* __restrict__ dinv, T* __restrict__ r, T* __restrict__ d,
+                                                 T inv_th) {
+  OK_LEVEL_SMEM(D, T);
+  stage_level<D, T>(sW, sD, (const T*)nullptr, dinv);
   Vtx<D> v;                               // coarse vertex
   if (!vertex_of_thread<D>(gc, v)) return;
   restrict_at<D, T>(gf, v, rf, bc);
+  if (dinv) cheb_init_at<D, T, T>(v, sD, bc, (T)1, r, d, inv_th);
 }
 
+// prolongation xf += P xc (with dc: P (xc + dc), see prolong_add_at)
 template <int D, typename T>
-__global__ void __launch_bounds__(BX) k_prolong_add(Geom gf, Geom gc, T* __restrict__ xf, const T* __restrict__ xc) {
+__global__ void __launch_bounds__(BX) k_prolong_add(Geom gf, Geom gc, T* __restrict__ xf, const T* __restrict__ xc,
+                                                    const T* __restrict__ dc) {
   pdl_entry();
   Vtx<D> v;                               // fine vertex
   if (!vertex_of_thread<D>(gf, v)) return;
-  prolong_add_at<D, T>(gc, v, xf, xc);
+  prolong_add_at<D, T>(gc, v, xf, xc, dc);
 }
 
 // one block; warp per row
@@ -139,11 +148,13 @@ __global__ void __launch_bounds__(BX) k_cheb_last_b(Batch<ChebLastItem<T, TO>> B
 }
 template <int D, typename T>
 __global__ void __launch_bounds__(BX) k_restrict_b(Batch<TransferItem<T>> B, Geom gf, Geom gc) {
-  pdl_entry();
+  OK_LEVEL_SMEM(D, T);
   const TransferItem<T>& a = B.a[batch_problem<D>(gc)];
+  stage_level<D, T>(sW, sD, (const T*)nullptr, a.dinv);
   Vtx<D> v;
   if (!vertex_of_thread_at<D>(gc, batch_plane<D>(gc), v)) return;
   restrict_at<D, T>(gf, v, a.fine, a.coarse);
+  if (a.dinv) cheb_init_at<D, T, T>(v, sD, a.coarse, (T)1, a.r, a.d, a.inv_th);
 }
 template <int D, typename T>
 __global__ void __launch_bounds__(BX) k_prolong_add_b(Batch<TransferItem<T>> B, Geom gf, Geom gc) {
@@ -151,7 +162,7 @@ __global__ void __launch_bounds__(BX) k_prolong_add_b(Batch<TransferItem<T>> B, 
   const TransferItem<T>& a = B.a[batch_problem<D>(gf)];
   Vtx<D> v;
   if (!vertex_of_thread_at<D>(gf, batch_plane<D>(gf), v)) return;
-  prolong_add_at<D, T>(gc, v, a.fine, a.coarse);
+  prolong_add_at<D, T>(gc, v, a.fine, a.coarse, (const T*)a.dc);
 }
 template <typename T>
 __global__ void __launch_bounds__(512) k_coarse_solve_b(Batch<GemvItem<T>> B, long long nc) {
@@ -471,14 +482,15 @@ void launch_cheb_last(int dim, const Geom& g, const T* W, T* x, T* r, const T* d
   else launch_k(k_cheb_last<3, T, TO>, grid_of(3, g), BX, 0, s, g, W, x, r, d_in, first, out, oscale);
 }
 template <typename T>
-void launch_restrict(int dim, const Geom& gf, const Geom& gc, const T* rf, T* bc, cudaStream_t s) {
-  if (dim == 2) launch_k(k_restrict<2, T>, grid_of(2, gc), BX, 0, s, gf, gc, rf, bc);
-  else launch_k(k_restrict<3, T>, grid_of(3, gc), BX, 0, s, gf, gc, rf, bc);
+void launch_restrict(int dim, const Geom& gf, const Geom& gc, const T* rf, T* bc, cudaStream_t s,
+                     const T* dinv, T* r, T* d, T inv_th) {
+  if (dim == 2) launch_k(k_restrict<2, T>, grid_of(2, gc), BX, 0, s, gf, gc, rf, bc, dinv, r, d, inv_th);
+  else launch_k(k_restrict<3, T>, grid_of(3, gc), BX, 0, s, gf, gc, rf, bc, dinv, r, d, inv_th);
 }
 template <typename T>
-void launch_prolong_add(int dim, const Geom& gf, const Geom& gc, T* xf, const T* xc, cudaStream_t s) {
-  if (dim == 2) launch_k(k_prolong_add<2, T>, grid_of(2, gf), BX, 0, s, gf, gc, xf, xc);
-  else launch_k(k_prolong_add<3, T>, grid_of(3, gf), BX, 0, s, gf, gc, xf, xc);
+void launch_prolong_add(int dim, const Geom& gf, const Geom& gc, T* xf, const T* xc, cudaStream_t s, const T* dc) {
+  if (dim == 2) launch_k(k_prolong_add<2, T>, grid_of(2, gf), BX, 0, s, gf, gc, xf, xc, dc);
+  else launch_k(k_prolong_add<3, T>, grid_of(3, gf), BX, 0, s, gf, gc, xf, xc, dc);
 }
 template <typename T>
 void launch_coarse_solve(long long nc, const T* Ainv, const T* b, T* x, cudaStream_t s) {
@@ -554,7 +566,7 @@ void launch_gauss_jordan(long long n, const double* A, double* work, double* Ain
 // ---- batched launchers ----------------------------------------------------
 template <int D>
 static inline dim3 grid_b(const Geom& g, int count) {
-  return dim3((g.n1 + BX - 1) / BX, g.n1, (D == 3 ? g.n1 : 1) * count);
+  return dim3((unsigned)(((long long)g.n1 * g.n1 + BX - 1) / BX), 1, (D == 3 ? g.n1 : 1) * count);
 }
 template <typename I>
 static inline Batch<I> pack(const I* items, int count) {
@@ -625,8 +637,9 @@ template void launch_cheb_last_b<float, __half>(int, const Geom&, const ChebLast
                                      cudaStream_t);                                                            \
   template void launch_cheb_step<T>(int, const Geom&, const T*, const T*, T*, T*, const T*, T*, T, T, bool,    \
                                     cudaStream_t);                                                             \
-  template void launch_restrict<T>(int, const Geom&, const Geom&, const T*, T*, cudaStream_t);                 \
-  template void launch_prolong_add<T>(int, const Geom&, const Geom&, T*, const T*, cudaStream_t);              \
+  template void launch_restrict<T>(int, const Geom&, const Geom&, const T*, T*, cudaStream_t, const T*, T*, T*, \
+                                   T);                                                                        \
+  template void launch_prolong_add<T>(int, const Geom&, const Geom&, T*, const T*, cudaStream_t, const T*);    \
   template void launch_coarse_solve<T>(long long, const T*, const T*, T*, cudaStream_t);                  \
   template void launch_coarse_gemv<T>(long long, long long, const T*, const T*, T*, cudaStream_t);        \
   template cudaError_t prepare_coarse_gemv<T>(long long);

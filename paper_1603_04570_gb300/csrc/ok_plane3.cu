@@ -1,8 +1,9 @@
 // ok_plane3.cu -- 3D stencil steps by z-marching thread blocks.
 //
 // A thread block owns a PX x PY tile of (x, y) columns, one thread per column,
-// and walks a chunk of PZ z-planes (four compiled shapes, chosen per level by
-// timing at setup).  The vector the stencil reads is staged
+// and walks a chunk of pz consecutive z-planes (four compiled tile shapes,
+// chosen per level by timing at setup; pz is chosen at launch so that the
+// blocks fill whole waves of the SMs, see plane_chunk).  The vector the stencil reads is staged
 // plane by plane into a ring of four shared-memory planes of (PY + 2) x
 // (PX + 2) values (the tile and a one-vertex ring around it, zero outside the
 // domain, which is the value load_nb gives an absent neighbour).  The 15
@@ -25,10 +26,15 @@
 #include "ok_kernels.h"
 #include "ok_stencil.cuh"
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 namespace okg {
 
-// Block shapes (PX x PY columns, PZ planes); the autotuner of the multigrid
-// setup picks one per level by timing (all give the same bits).
+// Block shapes (PX x PY columns; PZ is the plane count the shape was first
+// tuned with, kept as its name); the autotuner of the multigrid setup picks
+// one per level by timing (all give the same bits).
 template <int PX_, int PY_, int PZ_> struct PShape {
   static constexpr int PX = PX_, PY = PY_, PZ = PZ_;
   static constexpr int PW = PX + 2, PH = PY + 2;            // padded plane
@@ -90,9 +96,9 @@ __device__ __forceinline__ void plane_update(const PlaneArgs<T, TS, TO>& a, cons
 }
 
 template <typename T, typename TS, typename TO, int MODE, class C>
-__device__ __forceinline__ void plane3_body(const PlaneArgs<T, TS, TO>& a, int zchunk) {
+__device__ __forceinline__ void plane3_body(const PlaneArgs<T, TS, TO>& a, int zchunk, int pz) {
   using Tp = Topo<3>;
-  constexpr int PX = C::PX, PY = C::PY, PZ = C::PZ, PW = C::PW, PH = C::PH, PNT = C::PNT, PSLOT = C::PSLOT;
+  constexpr int PX = C::PX, PY = C::PY, PW = C::PW, PH = C::PH, PNT = C::PNT, PSLOT = C::PSLOT;
   __shared__ T sW[NTAB3];
   __shared__ T sD[Tp::NCLASS];
   __shared__ T ring[4][PH][PW];
@@ -104,8 +110,8 @@ __device__ __forceinline__ void plane3_body(const PlaneArgs<T, TS, TO>& a, int z
   const int n = g.n;
   const int tx = threadIdx.x % PX, ty = threadIdx.x / PX;
   const int gx = blockIdx.x * PX + tx, gy = blockIdx.y * PY + ty;
-  const int z0 = zchunk * PZ;
-  const int z1 = min(z0 + PZ, n + 1);
+  const int z0 = zchunk * pz;
+  const int z1 = min(z0 + pz, n + 1);
   // padded-plane elements this thread stages: (ey, ex) -> global (x0 + ex - 1, y0 + ey - 1)
   long long eoff[PSLOT];
   bool ein[PSLOT];
@@ -198,36 +204,84 @@ __device__ __forceinline__ void plane3_body(const PlaneArgs<T, TS, TO>& a, int z
   }
 }
 template <typename T, typename TS, typename TO, int MODE, class C>
-__global__ void __launch_bounds__(C::PNT) k_plane3(PlaneArgs<T, TS, TO> a) {
-  plane3_body<T, TS, TO, MODE, C>(a, blockIdx.z);
+__global__ void __launch_bounds__(C::PNT) k_plane3(PlaneArgs<T, TS, TO> a, int pz) {
+  plane3_body<T, TS, TO, MODE, C>(a, blockIdx.z, pz);
 }
 // batched: blockIdx.z = problem * (z-chunks) + chunk
 template <typename T, typename TS, typename TO, int MODE, class C>
-__global__ void __launch_bounds__(C::PNT) k_plane3_b(Batch<PlaneArgs<T, TS, TO>> B, int nzc) {
-  plane3_body<T, TS, TO, MODE, C>(B.a[blockIdx.z / nzc], blockIdx.z % nzc);
+__global__ void __launch_bounds__(C::PNT) k_plane3_b(Batch<PlaneArgs<T, TS, TO>> B, int nzc, int pz) {
+  plane3_body<T, TS, TO, MODE, C>(B.a[blockIdx.z / nzc], blockIdx.z % nzc, pz);
+}
+
+// Planes per block.  A launch of T column tiles split into c z-chunks runs in
+// ceil(T c / R) waves of R = (resident blocks per SM) x (SMs) blocks, each
+// block walking ceil(n1 / c) planes after staging two; c is chosen to
+// minimise waves x (planes + 2).  (At 129^3 with 32 x 8 tiles and four
+// resident blocks per SM this gives 7 chunks of 19 planes, one wave, where
+// fixed 16-plane chunks need 765 blocks: 1.26 waves.)  Every plane is
+// computed once whatever c is, so the results do not depend on it.
+static int plane_chunk(const void* kern, int pnt, int n1, long long tiles) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, long long, int>, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple(kern, n1, tiles, dev);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int nsm = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, pnt, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const long long R = (long long)(nsm > 0 ? nsm : 1) * (per_sm > 0 ? per_sm : 1);
+  int best_pz = n1;
+  long long best = -1;
+  for (int c = 1; c <= n1; ++c) {
+    const int pz = (n1 + c - 1) / c;
+    const int chunks = (n1 + pz - 1) / pz;
+    if (chunks != c) continue;                       // same pz as a smaller c
+    const long long cost = ((tiles * chunks + R - 1) / R) * (pz + 2);
+    if (best < 0 || cost < best) {
+      best = cost;
+      best_pz = pz;
+    }
+  }
+  cache[key] = best_pz;
+  return best_pz;
 }
 
 template <class C>
-static inline dim3 plane_grid(const Geom& g) {
-  return dim3((g.n1 + C::PX - 1) / C::PX, (g.n1 + C::PY - 1) / C::PY, (g.n1 + C::PZ - 1) / C::PZ);
+static inline long long plane_tiles(const Geom& g) {
+  return (long long)((g.n1 + C::PX - 1) / C::PX) * ((g.n1 + C::PY - 1) / C::PY);
+}
+
+template <typename T, typename TS, typename TO, int MODE, class C>
+static void launch_plane1(const PlaneArgs<T, TS, TO>& a, cudaStream_t s) {
+  auto kern = k_plane3<T, TS, TO, MODE, C>;
+  const int pz = plane_chunk((const void*)kern, C::PNT, a.g.n1, plane_tiles<C>(a.g));
+  const dim3 gr((a.g.n1 + C::PX - 1) / C::PX, (a.g.n1 + C::PY - 1) / C::PY, (a.g.n1 + pz - 1) / pz);
+  launch_k(kern, gr, C::PNT, 0, s, a, pz);
 }
 
 template <typename T, typename TS, typename TO, int MODE>
 static void launch_plane(const PlaneArgs<T, TS, TO>& a, int shape, cudaStream_t s) {
   switch (shape) {
-    case 1: launch_k(k_plane3<T, TS, TO, MODE, PShape1>, plane_grid<PShape1>(a.g), PShape1::PNT, 0, s, a); break;
-    case 2: launch_k(k_plane3<T, TS, TO, MODE, PShape2>, plane_grid<PShape2>(a.g), PShape2::PNT, 0, s, a); break;
-    case 3: launch_k(k_plane3<T, TS, TO, MODE, PShape3>, plane_grid<PShape3>(a.g), PShape3::PNT, 0, s, a); break;
-    default: launch_k(k_plane3<T, TS, TO, MODE, PShape0>, plane_grid<PShape0>(a.g), PShape0::PNT, 0, s, a);
+    case 1: launch_plane1<T, TS, TO, MODE, PShape1>(a, s); break;
+    case 2: launch_plane1<T, TS, TO, MODE, PShape2>(a, s); break;
+    case 3: launch_plane1<T, TS, TO, MODE, PShape3>(a, s); break;
+    default: launch_plane1<T, TS, TO, MODE, PShape0>(a, s);
   }
 }
 
 template <typename T, typename TS, typename TO, int MODE, class C>
 static void launch_plane_b1(const Batch<PlaneArgs<T, TS, TO>>& B, const Geom& g, int count, cudaStream_t s) {
-  dim3 gr = plane_grid<C>(g);
-  const int nzc = (int)gr.z;
-  gr.z = nzc * count;
-  launch_k(k_plane3_b<T, TS, TO, MODE, C>, gr, C::PNT, 0, s, B, nzc);
+  auto kern = k_plane3_b<T, TS, TO, MODE, C>;
+  const int pz = plane_chunk((const void*)kern, C::PNT, g.n1, plane_tiles<C>(g) * count);
+  const int nzc = (g.n1 + pz - 1) / pz;
+  const dim3 gr((g.n1 + C::PX - 1) / C::PX, (g.n1 + C::PY - 1) / C::PY, nzc * count);
+  launch_k(kern, gr, C::PNT, 0, s, B, nzc, pz);
 }
 template <typename T, typename TS, typename TO>
 void launch_plane3_b(int mode, const PlaneArgs<T, TS, TO>* items, int count, int shape, cudaStream_t s) {

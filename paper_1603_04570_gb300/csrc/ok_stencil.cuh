@@ -66,9 +66,12 @@ __device__ __forceinline__ void restrict_at(const Geom& gf, const Vtx<D>& v, con
   bc[v.idx] = fma((T)0.5, acc, rf[fc]);
 }
 
-// v: fine vertex, gc: coarse geometry
+// v: fine vertex, gc: coarse geometry.  With dc, the coarse iterate is
+// xc + dc, rounded as the last smoothing step (cheb_last_at without r) rounds
+// it: the coarse level's last step is folded into this launch.
 template <int D, typename T>
-__device__ __forceinline__ void prolong_add_at(const Geom& gc, const Vtx<D>& v, T* xf, const T* xc) {
+__device__ __forceinline__ void prolong_add_at(const Geom& gc, const Vtx<D>& v, T* xf, const T* xc,
+                                               const T* dc = nullptr) {
   long long ci = 0, cj = 0;
   bool mid = false;
   const long long st[3] = {1, gc.sy, gc.sz};
@@ -78,7 +81,13 @@ __device__ __forceinline__ void prolong_add_at(const Geom& gc, const Vtx<D>& v, 
     cj += (long long)((v.p[a] >> 1) + (v.p[a] & 1)) * st[a];
     mid = mid || (v.p[a] & 1);
   }
-  xf[v.idx] = mid ? fma((T)0.5, xc[ci] + xc[cj], xf[v.idx]) : xf[v.idx] + xc[ci];
+  const T ai = dc ? xc[ci] + dc[ci] : xc[ci];
+  if (mid) {
+    const T aj = dc ? xc[cj] + dc[cj] : xc[cj];
+    xf[v.idx] = fma((T)0.5, ai + aj, xf[v.idx]);
+  } else {
+    xf[v.idx] = xf[v.idx] + ai;
+  }
 }
 
 // x[r] = sum_c A[r][c] b[c] for the rows of this warp, xor-reduced.  Lane l
