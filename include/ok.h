@@ -236,10 +236,13 @@ typedef struct ok_batch_info {
 int ok_solve_batch(ok_request* reqs, int count, ok_batch_info* out, ok_stream stream);
 
 /* Serving (no counterpart in the paper): whole simulations admitted
- * continuously.  Requests are taken in order of `arrival` (seconds after the
- * call starts); one is admitted when it has arrived, fewer than
- * `max_inflight` are in flight and its estimated device footprint (Krylov
- * basis dominant) fits in `mem_budget` bytes beside those in flight.  An
+ * continuously.  A request is admitted when it has arrived (`arrival`,
+ * seconds after the call starts), fewer than `max_inflight` are in flight and
+ * its estimated device footprint (Krylov basis dominant) fits in
+ * `mem_budget` bytes beside those in flight.  Arrived requests are
+ * considered oldest first; a younger one that fits may pass an older one
+ * that waits for memory, until the oldest waiting request has waited one
+ * second (from then on it alone may enter, so it is not starved).  An
  * admitted request's handle (ok_grid_create) and w0 (ok_init_w when
  * init_w != 0) are set up on a thread of its own; it then joins the group of
  * requests with its (dim, n, options), whose host thread and non-blocking

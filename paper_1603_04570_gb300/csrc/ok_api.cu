@@ -2760,6 +2760,8 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
     if (gs) cudaStreamDestroy(gs);
   };
 
+  // validation; the valid requests in arrival order
+  std::vector<int> valid;
   for (int i : order) {
     ok_serve_request& r = reqs[i];
     r.status = OK_SUCCESS;
@@ -2780,16 +2782,17 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
       r.status = OK_ERR_NOMEM;
       continue;
     }
-    const double wait = r.arrival - now();
-    if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(wait));
-    {
-      std::unique_lock<std::mutex> lk(mu);
-      cv.wait(lk, [&] { return inflight < max_inflight && bytes + r.device_bytes <= mem_budget; });
-      ++inflight;
-      bytes += r.device_bytes;
-      peak_inflight = std::max(peak_inflight, inflight);
-      peak_bytes = std::max(peak_bytes, bytes);
-    }
+    valid.push_back(i);
+  }
+  // Admission.  A request is admitted once fewer than max_inflight are in
+  // flight and its estimate fits the budget beside theirs; a younger request
+  // that fits may pass an older one that waits for memory, unless the oldest
+  // waiting request has waited HOL_WAIT seconds (then it alone may enter, so
+  // it cannot starve while small requests keep arriving).
+  constexpr double HOL_WAIT = 1.0;
+  auto admit = [&](int i) {
+    ok_serve_request& r = reqs[i];
+    const ok_opts& o = opts[i];
     r.t_admit = now();
     // the group of (dim, n, options): started on first use
     std::string key(reinterpret_cast<const char*>(&o), sizeof(ok_opts));
@@ -2816,7 +2819,7 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
       r.status = OK_ERR_NOMEM;
       r.t_done = now();
       groups.erase(key);
-      continue;
+      return;
     }
     try {
       setups.emplace_back([&, i, G] {                   // handle and w0 on the request's own thread
@@ -2841,6 +2844,40 @@ extern "C" int ok_serve(ok_serve_request* reqs, int count, int max_inflight, lon
       std::strncpy(r.message, "could not start a setup thread", sizeof(r.message) - 1);
       finish(i, OK_ERR_NOMEM);
     }
+  };
+  std::deque<int> waiting;                            // arrived, not yet admitted, in arrival order
+  size_t next = 0;                                    // next valid request still to arrive
+  while (next < valid.size() || !waiting.empty()) {
+    int pick = -1;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      const double t = now();
+      while (next < valid.size() && reqs[valid[next]].arrival <= t) waiting.push_back(valid[next++]);
+      if (inflight < max_inflight && !waiting.empty()) {
+        const bool head_may_be_passed = t - reqs[waiting.front()].arrival < HOL_WAIT;
+        for (size_t k = 0; k < waiting.size(); ++k) {
+          if (bytes + reqs[waiting[k]].device_bytes <= mem_budget) {
+            pick = (int)k;
+            break;
+          }
+          if (!head_may_be_passed) break;
+        }
+      }
+      if (pick < 0) {                                 // wait for a request to finish or to arrive
+        double dt = 0.05;
+        if (next < valid.size()) dt = std::min(dt, std::max(0.0, reqs[valid[next]].arrival - t));
+        cv.wait_for(lk, std::chrono::duration<double>(dt));
+        continue;
+      }
+      const int i = waiting[pick];
+      waiting.erase(waiting.begin() + pick);
+      ++inflight;
+      bytes += reqs[i].device_bytes;
+      peak_inflight = std::max(peak_inflight, inflight);
+      peak_bytes = std::max(peak_bytes, bytes);
+      pick = i;
+    }
+    admit(pick);
   }
   for (auto& t : setups) t.join();
   {

@@ -530,6 +530,28 @@ def test_serving_admits_by_memory_budget():
     assert st == ok.OK_ERR_NOMEM and res[0].status == ok.OK_ERR_NOMEM and info.failed == 1
 
 
+def test_serving_small_request_passes_one_waiting_for_memory():
+    """Admission is not strictly in arrival order: while the second of two large
+    requests waits for the first one's memory, a younger small request that
+    fits beside the first is admitted ahead of it; every result is still the
+    one the request gets alone."""
+    base = _serve_mix()[0]
+    rng = np.random.default_rng(3)
+    big = [dict(base, n=96, steps=5, arrival=0.001 * k, u0=0.01 * rng.uniform(-1, 1, 97 ** 2)) for k in range(2)]
+    small = dict(base, n=16, steps=1, arrival=0.002, u0=0.01 * rng.uniform(-1, 1, 17 ** 2))
+    fp_big = _serve(big[:1], 1, 1 << 34)[1][0].device_bytes
+    fp_small = _serve([small], 1, 1 << 34)[1][0].device_bytes
+    assert fp_big > fp_small
+    mix = [big[0], big[1], small]
+    alone = [_serve([r], 1, 1 << 34)[0][0] for r in mix]
+    got, res, info = _serve(mix, 4, fp_big + fp_small + 1)
+    assert info.completed == 3 and info.failed == 0
+    assert res[2].t_admit < res[1].t_admit                  # the small one passed the waiting big one
+    assert res[1].t_admit >= res[0].t_done - 1e-3          # which entered when the first one left
+    for k, ((ua, wa), (um, wm)) in enumerate(zip(alone, got)):
+        assert np.array_equal(ua, um) and np.array_equal(wa, wm), k
+
+
 def _match(a, b):
     """Largest distance of an optimal one-to-one pairing of two eigenvalue sets."""
     from scipy.optimize import linear_sum_assignment
